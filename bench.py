@@ -1,0 +1,286 @@
+#!/usr/bin/env python3
+"""Benchmark: k-point eigensolves per second for a photonic-crystal band path (kernel-compensated MFD + LOBPCG).
+
+Workload (one "step"): the FCC conventional cubic cell with four eps = 13 spheres (r = 0.25 a) in air, N = 32^3,
+the lowest 10 bands at 40 Bloch vectors on Gamma-X-W-K-Gamma-L, LOBPCG to a relative residual of 1e-6 -- every
+k-point solved together by one pc_solve call (all hot-path kernels). Synthetic, seeded input; the working set
+(~9 GB of search blocks) is larger than L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0). Multi-GPU: one process per GPU, each rank solves its own copy of the path
+(independent problems, no collective on the data path; weak scaling).
+
+``--impl reference`` times the FP64 CPU oracle (oracle/) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as wl  # noqa: E402
+
+METRIC = "k-point eigensolves/sec at 1e-6 residual (chosen vs plain FP64); stencil GB/s vs HBM"
+UNIT = "k-points/s"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, ws, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(x, dist):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.idx = device_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = [r.split(",") for r in open(self.tmp.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(w, max_iters: int, kidx: int = 3):
+    """Times the oracle on one k-point for a bounded number of LOBPCG iterations; returns (seconds, iterations)."""
+    from oracle import eigs, geometry
+    m0 = 1.0 / geometry.eps_edges(w.N, w.structure.as_array(), w.structure.eps_bg)
+    t = time.perf_counter()
+    out = eigs.solve_kpoint(w.N, w.kpts[kidx], m0, w.nbands, w.tol, maxiter=max_iters, max_doublings=0)
+    return time.perf_counter() - t, max(1, out["iters"])
+
+
+def cpu_baseline(w, iters_per_kpoint: float, max_iters: int = 12):
+    secs, its = oracle_sample(w, max_iters)
+    per_it = secs / its
+    value = 1.0 / (per_it * iters_per_kpoint)
+    return {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"oracle LOBPCG (numpy/scipy FP64) on k-point 3 of the path for {its} iterations "
+                       f"({secs:.1f} s, {per_it:.2f} s/iteration), scaled to {iters_per_kpoint:.1f} iterations per "
+                       f"k-point (the mean the GPU solve needed); BLAS on all cores, sparse matvec and FFT "
+                       f"single-threaded")}
+
+
+def run_reference(args, rank, ws, dist):
+    if rank != 0:
+        return
+    w = wl.workload_fcc_32()
+    # iterations per k-point of this workload for the extrapolation (measured by the GPU solve; 90 if unknown)
+    ipk = float(os.environ.get("PC_BENCH_ITERS_PER_KPOINT", "90"))
+    times = []
+    for s in range(args.warmup + args.steps):
+        secs, its = oracle_sample(w, args.ref_iters)
+        if s >= args.warmup:
+            times.append(secs / its * ipk)
+    t = statistics.mean(times)
+    value = 1.0 / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "N": w.N, "nbands": w.nbands, "tol": w.tol, "nk_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": (f"each step: oracle LOBPCG on k-point 3 for {args.ref_iters} iterations, "
+                                        f"scaled to {ipk:.0f} iterations per k-point")},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-iters", type=int, default=12)
+    args = ap.parse_args()
+    rank, ws, dist = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, ws, dist)
+        return
+
+    import torch
+
+    import paper_2503_19379_gb300 as pc
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    w = wl.workload_fcc_32()
+    prec = pc.pc.PC_PREC_MIXED if args.precision == "mixed" else pc.pc.PC_PREC_FP64
+    eps = pc.eps_spheres(w.N, w.structure.as_array(), w.structure.eps_bg)
+    stream = torch.cuda.current_stream()
+    solver = pc.Solver(w.N, eps, stream=stream.cuda_stream, precision=prec)
+    nk = len(w.kpts)
+
+    for _ in range(args.warmup):
+        out = solver.solve(w.kpts, w.nbands, w.tol)
+    torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs)
+    solver.reset_stats()
+    solver.set_timing(True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    barrier(dist)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters, statuses = [], []
+    for _ in range(args.steps):
+        out = solver.solve(w.kpts, w.nbands, w.tol)
+        iters.append(out["iters"].copy())
+        statuses.append(out["status"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clk = clocks.stop()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    st = solver.stats()
+    solver.set_timing(False)
+    ms_step_max = max_over_ranks(ms_step, dist)
+    value = nk * ws / (ms_step_max / 1e3)
+    mean_iters = float(np.mean(np.concatenate(iters)))
+
+    # ---- end to end through the public API with host buffers: setup (eps H2D) + solve (evals D2H)
+    barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s2 = pc.Solver(w.N, eps, stream=stream.cuda_stream, precision=prec)
+        o2 = s2.solve(w.kpts, w.nbands, w.tol)
+        s2.close()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) / args.steps * 1e3, dist)
+    h2d = eps.nbytes + w.kpts.nbytes
+    d2h = o2["evals"].nbytes + o2["iters"].nbytes + o2["resid"].nbytes
+
+    # ---- roofline of the dominant stage
+    peaks, src = load_peaks()
+    dom = max(st, key=lambda k: st[k]["ms"])
+    d = st[dom]
+    per_launch_ms = d["ms"] / max(d["calls"], 1)
+    if args.precision == "fp64" or dom in ("gram", "update", "rr"):
+        achieved = d["flops"] / max(d["calls"], 1) / (per_launch_ms / 1e3) / 1e12
+        peak = FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x FP64 FMA/clk x 2 x 2.07 GHz (FP64 CUDA-core, the path's unit)"}
+    else:
+        achieved = d["bytes"] / max(d["calls"], 1) / (per_launch_ms / 1e3) / 1e9
+        peak = float(peaks["hbm_gbs"])
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": src}
+    sten = st["stencil"]
+    sten_gbs = sten["bytes"] / max(sten["ms"], 1e-9) / 1e6
+    stages = {k: {"ms_per_step": v["ms"] / args.steps, "calls_per_step": v["calls"] / args.steps,
+                  "share": v["ms"] / max(sum(x["ms"] for x in st.values()), 1e-9)} for k, v in st.items()}
+    launches = int(sum(v["kernels"] for v in st.values()))
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128" if args.precision == "fp64" else "c64+f64", "data": "synthetic",
+            "config": {"workload": ("fcc-spheres-N32: FCC conventional cell, 4 spheres eps=13 r=0.25a in air, N=32, "
+                                    "10 bands, 40 k-points Gamma-X-W-K-Gamma-L, tol 1e-6, all k-points in one "
+                                    "batched solve"),
+                       "precision": args.precision, "nk_per_gpu": nk, "nbands": w.nbands, "tol": w.tol,
+                       "mean_lobpcg_iterations": mean_iters, "status": max(statuses),
+                       "cache": "inputs larger than L2 (search blocks ~9 GB per GPU), no flush"},
+            "roofline": roof,
+            "stencil": {"achieved_gbs": sten_gbs, "peak_gbs": float(peaks["hbm_gbs"]),
+                        "frac": sten_gbs / float(peaks["hbm_gbs"]),
+                        "note": "algorithmic bytes (read X, write Op X, M0 once per launch) / event time"},
+            "stages": stages,
+            "e2e": {"value": nk * ws / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
+            "gpu_launches": launches, "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, mean_iters)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * pc.h -- C ABI of libpc, a GB300 (sm_103a) solver for the kernel-compensated MFD Maxwell eigenproblem of
+ * photonic crystals (Jin, Xia, Xu, "Kernel compensation method for Maxwell eigenproblem in photonic crystals with
+ * mimetic finite difference discretizations").
+ *
+ * The library computes, for Bloch vectors k, the lowest eigenpairs of the compensated operator
+ *     Op = A M0 A' + gamma B'B                                            (eq. Ker_comp, Section 3.2)
+ * on the periodic N^3 grid, where A = CURL_k (edges -> faces), B = DIV_k (faces -> cells) are the shifted MFD
+ * operators of eq. discrete_2nd_block built from D_i = K_i + i L_i (eqs. discre, blocks), M0 = diag(1/eps) on edges
+ * (Section 4.4), and gamma = 2 max{1/h, |k|^-2} (eq. pnt_number). The eigensolver is block LOBPCG (Section 5.1)
+ * preconditioned by P = A A' + gamma B'B solved with FFTs (Section 5.2, Algorithm 5.1), followed by the recompute
+ * check of Algorithm 4.1.
+ *
+ * Conventions common to every entry point
+ * - Grid: N a power of two, 8 <= N <= 256; lattice constant a = 1 (h = 1/N); cubic cell only.
+ * - A face (or edge) field is complex [3][N][N][N] = (component, z, y, x), x fastest, so that D_1 acts on x.
+ *   A cell field is complex [N][N][N]. A "block" of m fields stores field j at offset j * 3 N^3 (column-major
+ *   tall-skinny matrix with L = 3 N^3 rows); a batch of blocks for nb k-points stores block b at offset
+ *   b * stride elements.
+ * - Complex numbers are interleaved (re, im): dtype PC_C128 = two doubles, PC_C64 = two floats.
+ * - "device" pointers are CUDA device memory owned by the caller; "host" pointers are ordinary host memory owned by
+ *   the caller. The library never frees caller memory. Pointers must be 16-byte aligned.
+ * - All device work is issued on the stream given at pc_setup (or the stream argument); calls return after
+ *   enqueueing unless stated otherwise. Host outputs are valid on return.
+ * - Return value: 0 on success; negative on error (PC_EINVAL bad argument, PC_EUNSUPPORTED valid but not
+ *   implemented, PC_ENOMEM allocation failure, PC_ECUDA CUDA error); positive warnings PC_NOT_CONVERGED and
+ *   PC_SPURIOUS. pc_last_error() returns a thread-local description of the last failure.
+ * - There is no CPU fallback: every numerical step runs in this library's CUDA kernels.
+ */
+#ifndef PC_H
+#define PC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PC_OK 0
+#define PC_EINVAL (-1)
+#define PC_EUNSUPPORTED (-2)
+#define PC_ENOMEM (-3)
+#define PC_ECUDA (-4)
+#define PC_NOT_CONVERGED 1
+#define PC_SPURIOUS 2
+
+#define PC_C128 0
+#define PC_C64 1
+
+/* Preconditioner variants (Section 5.1 and Corollary discrete_vec_lap_mat). */
+#define PC_PRECOND_GAMMA 0     /* P = A A' + gamma B'B, eq. penalised_marix (default) */
+#define PC_PRECOND_LAPLACIAN 1 /* vector Laplacian A A' + B'B, the scalar symbol of Algorithm 5.1 */
+
+/* Solver precision. */
+#define PC_PREC_FP64 0  /* every step in FP64 / complex128 */
+#define PC_PREC_MIXED 1 /* search directions in complex64, X, residual and Rayleigh-Ritz in FP64 */
+
+typedef struct pc_ctx pc_ctx;
+
+typedef struct {
+    int order;             /* k of Table 1: 1 -> 2nd-order stencils (the only order the CUDA kernels implement) */
+    double gamma_override; /* > 0: use this penalty instead of eq. pnt_number */
+    int precond;           /* PC_PRECOND_GAMMA or PC_PRECOND_LAPLACIAN */
+    int precision;         /* PC_PREC_FP64 or PC_PREC_MIXED */
+    int guard;             /* block columns beyond nbands; < 0 (default): nbands/2 + 1, capped so 3(nbands+guard) <= 64 */
+    int maxiter;           /* LOBPCG iteration cap per k-point and gamma-doubling round (default 400) */
+    int max_doublings;     /* Algorithm 4.1 gamma doublings cap (default 8) */
+    uint64_t seed;         /* seed of the counter-based initial blocks */
+} pc_opts;
+
+/* Fill *opts with the defaults listed above. */
+int pc_opts_default(pc_opts *opts);
+
+/* pc_setup -- create a context for one structure (Section 4.4).
+ *   out:       receives the new context (library-owned; release with pc_destroy).
+ *   N:         grid points per axis (power of two, 8..256).
+ *   eps_edges: host [3][N][N][N] permittivity at the edge DoFs (x-edges at ((i+1/2)h, jh, kh), etc.), all > 0.
+ *              M0 = diag(1/eps_edges).
+ *   lattice:   host double[9], columns a1, a2, a3; must be the identity (cubic cell, a = 1) -> else PC_EUNSUPPORTED.
+ *   opts:      options (NULL -> defaults).
+ *   stream:    cudaStream_t to use for all work of this context (NULL -> the legacy default stream).
+ * Uploads M0 and the FFT tables once (one host-to-device copy). */
+int pc_setup(pc_ctx **out, int N, const double *eps_edges, const double *lattice, const pc_opts *opts,
+             void *stream);
+
+/* pc_solve -- lowest nbands eigenpairs for each of nk Bloch vectors (Sections 3.2, 4.5, 5; Algorithm 4.1).
+ *   kpts:   host [nk][3] Bloch vectors in units 1/a (reduced into [-pi, pi]^3 internally; a vector equivalent to 0
+ *           is treated as k = 0: its 3 constant kernel fields are projected out and the lowest nonzero eigenvalues
+ *           are returned).
+ *   nbands: eigenpairs per k-point, 1 <= nbands <= 21 (nbands + guard <= 21).
+ *   tol:    column j converged when |Op x - lambda x| <= tol |lambda| |x|.
+ *   evals:  host [nk][nbands] ascending omega^2 (units (1/a)^2).
+ *   evecs:  device [nk][nbands][3][N][N][N] complex128, unit 2-norm, or NULL.
+ *   iters:  host [nk] LOBPCG iterations (summed over gamma doublings), or NULL.
+ *   resid:  host [nk][nbands] final relative residuals, or NULL.
+ * All k-points are solved together (batched kernels). Returns PC_NOT_CONVERGED if some k-point hit maxiter and
+ * PC_SPURIOUS if Algorithm 4.1 still saw a spurious eigenvalue after max_doublings (results are filled in both
+ * cases). Synchronises the context stream before returning. */
+int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, double tol, double *evals, void *evecs,
+             int *iters, double *resid);
+
+/* Release a context and its device memory (never caller memory). NULL is allowed. */
+void pc_destroy(pc_ctx *ctx);
+
+/* Thread-local description of the last error ("" if none). */
+const char *pc_last_error(void);
+
+/* ---------------- per-stage timing and launch counts (tracing) ---------------- */
+
+/* Stages of a solve, in pc_stage_stat arrays. */
+#define PC_STAGE_STENCIL 0   /* a1: Op X (fused stencil) */
+#define PC_STAGE_PRECOND 1   /* a2: FFT preconditioner (5 kernels per call) */
+#define PC_STAGE_GRAM 2      /* a3: Gram products S^H S, S^H AS */
+#define PC_STAGE_RR 3        /* a4: Rayleigh-Ritz (small dense, one block per k-point) */
+#define PC_STAGE_UPDATE 4    /* a5: block updates S C */
+#define PC_STAGE_RESIDUAL 5  /* a5: residual and column norms */
+#define PC_STAGE_RECOMPUTE 6 /* a6: Algorithm 4.1 norms */
+#define PC_STAGE_OTHER 7     /* initial block, k = 0 projection */
+#define PC_NSTAGES 8
+
+typedef struct {
+    long calls;    /* stage invocations */
+    long kernels;  /* kernel launches */
+    double ms;     /* summed device time between CUDA events around each invocation (0 unless timing is on) */
+    double flops;  /* algorithmic floating-point operations (real), summed */
+    double bytes;  /* algorithmic global-memory bytes (each operand read once, each result written once) */
+} pc_stage_stat;
+
+/* Enable (1) or disable (0) event timing of every stage invocation of pc_solve on the context stream. Counts and
+ * algorithmic work are always accumulated. */
+int pc_set_timing(pc_ctx *ctx, int enable);
+/* Copy the accumulated statistics (PC_NSTAGES entries) into out (host). */
+int pc_get_stats(pc_ctx *ctx, pc_stage_stat *out);
+/* Zero the accumulated statistics. */
+int pc_reset_stats(pc_ctx *ctx);
+
+/* ---------------- step-level entry points (the individual kernels of the solve) ---------------- */
+
+/* a0: permittivity at the edge DoFs from a list of dielectric spheres (Section 4.4).
+ *   spheres: host [nsph][5] = (cx, cy, cz, r, eps_in) in cell fractions; a point belongs to a sphere when its
+ *            distance to a periodic image of the centre is <= r; later spheres take precedence.
+ *   eps_bg:  permittivity outside all spheres.
+ *   eps_out: host [3][N][N][N]. An edge midpoint within 1e-12 of a sphere surface takes the interface rule of
+ *            Section 4.4: eps = (sum of eps at the 4 adjacent cell centres) / 4, so that M0 = 4 / sum.
+ * Runs a device kernel; synchronous. */
+int pc_eps_spheres(int N, int nsph, const double *spheres, double eps_bg, double *eps_out);
+
+/* a1: Y = Op X = A M0 A' X + gamma B'B X for nb k-points x m fields (eq. Ker_comp; stencils of Section 4.1.2).
+ *   kpts: host [nb][3] (used as given, no zone reduction); gammas: host [nb].
+ *   X, Y: device blocks, dtype PC_C128 or PC_C64, batch stride m*3N^3 elements. X and Y must not overlap. */
+int pc_apply_op(pc_ctx *ctx, int nb, const double *kpts, const double *gammas, int m, int dtype, const void *X,
+                void *Y);
+
+/* a1h: E = A' X (faces -> edges, [m][3][N^3]) and C = B X (faces -> cells, [m][N^3]) per k-point (Section 4.3,
+ * eq. derived_uniform_grid). dtype PC_C128 only. Batch strides m*3N^3 (E) and m*N^3 (C). Either output may be NULL. */
+int pc_apply_half(pc_ctx *ctx, int nb, const double *kpts, int m, const void *X, void *E, void *C);
+
+/* a6: the norms of Algorithm 4.1 for each field x of the blocks (PC_C128):
+ *   out (device double [nb][m][3]) = (|M0^{1/2} A' x|^2, |B x|^2, |x|^2).
+ * lambda_re = out[0]/out[2]; the symmetric Rayleigh quotient is (out[0] + gamma out[1]) / out[2]. */
+int pc_recompute_norms(pc_ctx *ctx, int nb, const double *kpts, int m, const void *X, double *out);
+
+/* a2: W = P^{-1} R with P = A A' + gamma B'B (or the vector Laplacian, per opts.precond): forward 3D FFT, the exact
+ * inverse of the 3x3 symbol sigma I + (gamma-1) conj(d) d^T per mode, inverse 3D FFT (Algorithm 5.1,
+ * eq. penalised_marix). At k = 0 the singular mode 0 is mapped to 0. R and W may be the same buffer (in place). */
+int pc_apply_precond(pc_ctx *ctx, int nb, const double *kpts, const double *gammas, int m, int dtype,
+                     const void *R, void *W);
+
+/* a3: G_b = A_b^H B_b for tall-skinny blocks (L rows; p and q columns, column stride L; batch strides sa, sb in
+ * elements). G: device complex128 [nb][p][q] row-major. p, q <= 64. dtype applies to A and B; accumulation is
+ * FP64. */
+int pc_gram(int nb, long L, int p, int q, int dtype, const void *A, long sa, const void *B, long sb, void *G,
+            void *stream);
+
+/* a3: the Rayleigh-Ritz pencil of one panel: G_b = S_b^H S_b and H_b = S_b^H AS_b, with S_b and AS_b of p columns
+ * (length L, column stride L, the same batch stride ss for both). Op is Hermitian, so both outputs are Hermitian:
+ * only the upper triangle is accumulated (FP64) and the lower triangle is its conjugate mirror. G, H: device
+ * complex128 [nb][p][p]. p <= 64; dtype applies to S and AS. */
+int pc_gram_pair(int nb, long L, int p, int dtype, const void *S, long ss, const void *AS, void *G, void *H,
+                 void *stream);
+
+/* a5: Y_b = S_b C_b: S_b has p columns of length L (batch stride ss), C_b device complex128 [p][q] row-major
+ * (batch stride p*q), Y_b has q columns (batch stride sy). p <= 64, q <= 64. dtype applies to S and Y. */
+int pc_block_update(int nb, long L, int p, int q, int dtype, const void *S, long ss, const void *C, void *Y,
+                    long sy, void *stream);
+
+/* a4: batched Hermitian eigensolver (cyclic Jacobi, FP64) of device complex128 A [nb][n][n] (row-major, only the
+ * Hermitian part is used); w: device double [nb][n] ascending; V: device complex128 [nb][n][n], column j is the
+ * eigenvector of w[j]. n <= 64. */
+int pc_eigh_batched(int nb, int n, const void *A, double *w, void *V, void *stream);
+
+/* a4: Rayleigh-Ritz on span(S) for nb pencils (H, G) = (S^H Op S, S^H S), each n x n (device complex128, batch
+ * stride n*n): scale to unit diagonal, orthonormalise through the eigenvectors of G (dropping directions with
+ * eigenvalue < drop * max), solve the projected problem and return the lowest m Ritz values theta (device double
+ * [nb][m]) and coefficients coef (device complex128 [nb][n][m], so that S coef are the Ritz vectors; unit-norm
+ * and mutually orthogonal). rank (device int [nb], or NULL) receives the retained dimension. */
+int pc_rayleigh_ritz(int nb, int n, int m, const void *G, const void *H, double drop, double *theta, void *coef,
+                     int *rank, void *stream);
+
+/* a5: R = AX - X diag(theta) and column norms norms (device double [nb][m][2]) = (|r_j|, |x_j|). Blocks of m
+ * columns, batch stride m*L, dtype PC_C128. theta device double [nb][m]. */
+int pc_residual(int nb, long L, int m, const void *X, const void *AX, const double *theta, void *R,
+                double *norms, void *stream);
+
+/* Initial block: field j of k-point b is the counter-based complex normal stream (seed, (kidx0+b)*4096 + j)
+ * (splitmix64 output function + Box-Muller; see the oracle's rng module for the definition). Device PC_C128. */
+int pc_init_block(int nb, long L, int m, uint64_t seed, int kidx0, void *X, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -11,6 +11,7 @@
 Readings (where the paper is silent):
 * Convergence: column j is converged when |A x_j - theta_j x_j| <= tol * |theta_j| * |x_j|.
 * Algorithm 4.1's equality test: |lambda - lambda_re| <= 10 * tol * lambda; at most ``max_doublings`` doublings.
+  Its "goto line 1" re-solve starts from the current block with the spurious columns replaced by fresh random ones.
 * k = 0 (Remark after eq. penalised_marix): instead of a shift, the 3 constant fields spanning the kernel are
   projected out of every block (exact, since the kernel is an invariant subspace), and the lowest nonzero
   eigenvalues are reported.
@@ -132,6 +133,14 @@ def recompute_check(X: np.ndarray, theta: np.ndarray, m0: np.ndarray, Ah, tol: f
     return lam_re, spurious
 
 
+def spurious_columns(lam_re: np.ndarray, theta: np.ndarray, nbands: int, tol: float) -> np.ndarray:
+    """Columns to discard before the re-solve of Algorithm 4.1: the first nbands by the equality test, the guard
+    columns (not converged to tol) when lambda_re < lambda / 2, i.e. when the compensation part dominates."""
+    strict = np.abs(lam_re - theta) > 10.0 * tol * np.abs(theta)
+    loose = lam_re < 0.5 * theta
+    return np.where(np.arange(theta.size) < nbands, strict, loose)
+
+
 def solve_kpoint(N: int, kvec, m0: np.ndarray, nbands: int, tol: float, guard: int = 2, korder: int = 1,
                  gamma: float | None = None, variant: str = "gamma", X0: np.ndarray | None = None,
                  maxiter: int = 500, max_doublings: int = 8, seed: int = 0):
@@ -163,6 +172,13 @@ def solve_kpoint(N: int, kvec, m0: np.ndarray, nbands: int, tol: float, guard: i
         if doubling == max_doublings:
             break
         g *= 2.0
-        X0 = X
+        # "goto line 1" (Algorithm 4.1), warm-started: the physical eigenvectors are kept; the spurious ones are
+        # gamma-independent exact eigenvectors of B'B that LOBPCG would never leave, so they are replaced by fresh
+        # random columns (stream shifted by the doubling count)
+        lam_all, _ = recompute_check(X, theta, m0, Ah, tol)
+        bad = spurious_columns(lam_all, theta, nbands, tol)
+        X0 = X.copy()
+        fresh = initial_block(seed + 7919 * (doubling + 1), 0, X.shape[0], m)
+        X0[:, bad] = fresh[:, bad]
     return {"evals": theta[:nbands], "evecs": X[:, :nbands], "iters": total_it, "resid": res[:nbands],
             "gamma": g, "doublings": doubling, "spurious": spurious, "lam_re": lam_re}

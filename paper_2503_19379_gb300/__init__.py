@@ -1,0 +1,12 @@
+"""GB300-native kernel-compensated MFD Maxwell eigensolver for photonic crystals.
+
+The numerical work runs in ``libpc.so`` (hand-written CUDA for sm_103a, C ABI declared in ``include/pc.h``). This
+package is the thin Python binding over it: ``pc`` marshals arguments (numpy arrays for host buffers, torch CUDA
+tensors for device buffers) and raises on any library error. There is no CPU fallback: importing the binding
+without a built library raises.
+"""
+from .pc import (PCError, Solver, block_update, eigh_batched, eps_spheres, gram, gram_pair, init_block, lib,
+                 rayleigh_ritz, residual)
+
+__all__ = ["PCError", "Solver", "block_update", "eigh_batched", "eps_spheres", "gram", "gram_pair", "init_block",
+           "lib", "rayleigh_ritz", "residual"]

@@ -1,0 +1,245 @@
+// FFT-diagonalised preconditioner solve W = P^{-1} R (Section 5.2, Algorithm 5.1) with the 3x3 mode symbol of
+// eq. penalised_marix, for batches of k-points x fields.
+//
+// Every circulant K_i, L_i is diagonal in the DFT basis (eq. diag_of_circ), so per mode m the preconditioner
+// P = A A' + gamma B'B is the 3x3 matrix sigma I + (gamma - 1) conj(d) d^T with d_i = symbol of D_i on mode m_i and
+// sigma = |d|^2. Its exact inverse (Sherman-Morrison) is (1/sigma) [I - (gamma-1)/(gamma sigma) conj(d) d^T]; with
+// the vector-Laplacian variant (gamma -> 1 in P) it is the scalar 1/sigma of Algorithm 5.1.
+//
+// Passes (each a read and a write of the block):
+//   1. forward FFT along x (decimation in frequency: natural order in, bit-reversed mode order out)
+//   2. forward FFT along y (same)
+//   3. along z, for all three components of a column at once: forward DIF FFT, the 3x3 symbol inverse at the mode
+//      (bitrev x, bitrev y, bitrev z) times 1/N^3, inverse FFT (decimation in time: bit-reversed in, natural out)
+//   4. inverse FFT along y (DIT), 5. inverse FFT along x (DIT).
+// The frequency data never needs reordering: the DIT inverse consumes the DIF output order directly.
+// Each line is transformed in shared memory with radix-2 butterflies; twiddles exp(-2 pi i t / N) come from a
+// table computed once on the host.
+#include <cmath>
+
+#include "pc_internal.cuh"
+
+namespace pc {
+
+__device__ __forceinline__ int bitrev(int p, int logN) { return (int)(__brev((unsigned)p) >> (32 - logN)); }
+
+// In-place radix-2 FFTs of `lines` lines of length N held in shared memory. Line l = g * lpg + u (group g, member
+// u) starts at g * gs + u * ls and its element t sits t * es further. Forward = DIF with exp(-), inverse = DIT with
+// exp(+).
+template <typename C, bool FWD>
+__device__ __forceinline__ void fft_lines(C *a, int lines, int lpg, int gs, int ls, int es, int logN, const C *tw) {
+  const int N = 1 << logN, halfN = N >> 1;
+  const int total = lines * halfN;
+  if (FWD) {
+    for (int lh = logN - 1; lh >= 0; --lh) {
+      const int half = 1 << lh;
+      for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        const int l = q / halfN, r = q - l * halfN;
+        const int g = r >> lh, jj = r & (half - 1);
+        const int lg = l / lpg, lu = l - lg * lpg;
+        const int i0 = lg * gs + lu * ls + ((g << (lh + 1)) + jj) * es, i1 = i0 + half * es;
+        const C x0 = a[i0], x1 = a[i1];
+        a[i0] = cadd(x0, x1);
+        a[i1] = cmul(csub(x0, x1), tw[jj << (logN - 1 - lh)]);
+      }
+      __syncthreads();
+    }
+  } else {
+    for (int lh = 0; lh < logN; ++lh) {
+      const int half = 1 << lh;
+      for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        const int l = q / halfN, r = q - l * halfN;
+        const int g = r >> lh, jj = r & (half - 1);
+        const int lg = l / lpg, lu = l - lg * lpg;
+        const int i0 = lg * gs + lu * ls + ((g << (lh + 1)) + jj) * es, i1 = i0 + half * es;
+        const C w = tw[jj << (logN - 1 - lh)];
+        const C t = cmulc(w, a[i1]);  // conj(w) * a[i1]
+        const C x0 = a[i0];
+        a[i1] = csub(x0, t);
+        a[i0] = cadd(x0, t);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename C> __device__ __forceinline__ void load_tw(C *s_tw, const C *tw, int halfN) {
+  for (int i = threadIdx.x; i < halfN; i += blockDim.x) s_tw[i] = tw[i];
+}
+
+// Pass along x: R rows of N contiguous elements per CTA. grid (3N^2/R, m, nb).
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(256) fft_x_kernel(const cplx<T> *__restrict__ in, long si, cplx<T> *__restrict__ out,
+                                                    long so, const cplx<T> *__restrict__ tw, const int *act, int logN,
+                                                    int R) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = 1 << logN;
+  C *s_tw = reinterpret_cast<C *>(smem_raw);
+  C *a = s_tw + N / 2;
+  const long n = 1L << (3 * logN);
+  const int b = act ? act[blockIdx.z] : (int)blockIdx.z;
+  const long base_i = (long)b * si + (long)blockIdx.y * 3 * n + (long)blockIdx.x * R * N;
+  const long base_o = (long)b * so + (long)blockIdx.y * 3 * n + (long)blockIdx.x * R * N;
+  load_tw(s_tw, tw, N / 2);
+  for (int i = threadIdx.x; i < R * N; i += blockDim.x) a[i] = in[base_i + i];
+  __syncthreads();
+  fft_lines<C, FWD>(a, R, R, 0, N, 1, logN, s_tw);
+  for (int i = threadIdx.x; i < R * N; i += blockDim.x) out[base_o + i] = a[i];
+}
+
+// Pass along y: a tile of U contiguous x values by N y values, for one (component, z). grid (3*N*(N/U), m, nb).
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(256) fft_y_kernel(const cplx<T> *__restrict__ in, long si, cplx<T> *__restrict__ out,
+                                                    long so, const cplx<T> *__restrict__ tw, const int *act, int logN,
+                                                    int U) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = 1 << logN;
+  C *s_tw = reinterpret_cast<C *>(smem_raw);
+  C *a = s_tw + N / 2;  // [y][u]
+  const long n = 1L << (3 * logN);
+  const int b = act ? act[blockIdx.z] : (int)blockIdx.z;
+  const int tilesX = N / U;
+  const int xt = blockIdx.x % tilesX, plane = blockIdx.x / tilesX;  // plane = comp * N + z
+  const long off = (long)blockIdx.y * 3 * n + (long)plane * N * N + (long)xt * U;
+  const long base_i = (long)b * si + off, base_o = (long)b * so + off;
+  load_tw(s_tw, tw, N / 2);
+  for (int i = threadIdx.x; i < N * U; i += blockDim.x) {
+    const int y = i / U, u = i - y * U;
+    a[i] = in[base_i + (long)y * N + u];
+  }
+  __syncthreads();
+  fft_lines<C, FWD>(a, U, U, 0, 1, U, logN, s_tw);
+  for (int i = threadIdx.x; i < N * U; i += blockDim.x) {
+    const int y = i / U, u = i - y * U;
+    out[base_o + (long)y * N + u] = a[i];
+  }
+}
+
+// Pass along z with the symbol: all 3 components of U contiguous x values at one y. grid (N*(N/U), m, nb).
+template <typename T>
+__global__ void __launch_bounds__(256) fft_z_symbol_kernel(const cplx<T> *__restrict__ in, long si,
+                                                           cplx<T> *__restrict__ out, long so,
+                                                           const cplx<T> *__restrict__ tw,
+                                                           const double2 *__restrict__ sym,
+                                                           const KParam *__restrict__ kp, const int *act, int logN,
+                                                           int U, int laplacian) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = 1 << logN;
+  C *s_tw = reinterpret_cast<C *>(smem_raw);
+  C *a = s_tw + N / 2;  // [comp][z][u]
+  const long n = 1L << (3 * logN);
+  const int b = act ? act[blockIdx.z] : (int)blockIdx.z;
+  const int tilesX = N / U;
+  const int xt = blockIdx.x % tilesX, y = blockIdx.x / tilesX;
+  const long off = (long)blockIdx.y * 3 * n + (long)y * N + (long)xt * U;
+  const long base_i = (long)b * si + off, base_o = (long)b * so + off;
+  load_tw(s_tw, tw, N / 2);
+  for (int i = threadIdx.x; i < 3 * N * U; i += blockDim.x) {
+    const int u = i % U, z = (i / U) % N, comp = i / (U * N);
+    a[i] = in[base_i + comp * n + (long)z * N * N + u];
+  }
+  __syncthreads();
+  fft_lines<C, true>(a, 3 * U, U, N * U, 1, U, logN, s_tw);  // lines (comp, u); z stride U
+  // symbol inverse per mode
+  const double2 *symb = sym + (long)b * 3 * N;
+  const double gam = kp[b].gamma;
+  const T scale = (T)(1.0 / (double)n);
+  const int my = bitrev(y, logN);
+  const double2 d2d = symb[N + my];
+  for (int i = threadIdx.x; i < N * U; i += blockDim.x) {
+    const int u = i % U, z = i / U;
+    const int mx = bitrev(xt * U + u, logN), mz = bitrev(z, logN);
+    const double2 d1d = symb[mx], d3d = symb[2 * N + mz];
+    const C d1 = cmake<C>((T)d1d.x, (T)d1d.y), d2 = cmake<C>((T)d2d.x, (T)d2d.y), d3 = cmake<C>((T)d3d.x, (T)d3d.y);
+    const T sigma = d1.x * d1.x + d1.y * d1.y + d2.x * d2.x + d2.y * d2.y + d3.x * d3.x + d3.y * d3.y;
+    C r1 = a[i], r2 = a[N * U + i], r3 = a[2 * N * U + i];
+    if (!(sigma > (T)0)) {
+      r1 = r2 = r3 = cmake<C>((T)0, (T)0);
+    } else {
+      const T inv = scale / sigma;
+      if (!laplacian) {
+        const C s = cadd(cadd(cmul(d1, r1), cmul(d2, r2)), cmul(d3, r3));  // d^T r
+        const T f = (T)((gam - 1.0) / gam) / sigma;
+        r1 = csub(r1, cscale(cmulc(d1, s), f));  // conj(d1) * s
+        r2 = csub(r2, cscale(cmulc(d2, s), f));
+        r3 = csub(r3, cscale(cmulc(d3, s), f));
+      }
+      r1 = cscale(r1, inv);
+      r2 = cscale(r2, inv);
+      r3 = cscale(r3, inv);
+    }
+    a[i] = r1;
+    a[N * U + i] = r2;
+    a[2 * N * U + i] = r3;
+  }
+  __syncthreads();
+  fft_lines<C, false>(a, 3 * U, U, N * U, 1, U, logN, s_tw);
+  for (int i = threadIdx.x; i < 3 * N * U; i += blockDim.x) {
+    const int u = i % U, z = (i / U) % N, comp = i / (U * N);
+    out[base_o + comp * n + (long)z * N * N + u] = a[i];
+  }
+}
+
+template <typename T>
+static int launch_precond_t(pc_ctx *ctx, int nb, int m, const void *R, long sr, void *W, long sw, const int *act) {
+  using C = cplx<T>;
+  const int N = ctx->N, logN = ctx->logN;
+  const C *tw = std::is_same<T, double>::value ? ctx->twd.as<C>() : ctx->twf.as<C>();
+  const int elems = 2048;
+  const int Rr = std::min(elems / N, N * N);          // rows per CTA along x
+  const int Uy = std::min(N, std::max(1, elems / N));  // x values per CTA along y
+  int Uz = 1;
+  while (Uz * 2 <= N && 3 * N * Uz * 2 <= 3 * elems / 2) Uz *= 2;
+  const size_t tw_b = sizeof(C) * (N / 2);
+  const size_t sx = tw_b + sizeof(C) * Rr * N, sy = tw_b + sizeof(C) * Uy * N, sz = tw_b + sizeof(C) * 3 * N * Uz;
+  static bool configured = false;
+  if (!configured) {
+    PC_CK(cudaFuncSetAttribute(fft_x_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    PC_CK(cudaFuncSetAttribute(fft_x_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    PC_CK(cudaFuncSetAttribute(fft_y_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    PC_CK(cudaFuncSetAttribute(fft_y_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    PC_CK(cudaFuncSetAttribute(fft_z_symbol_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    configured = true;
+  }
+  const C *Rc = static_cast<const C *>(R);
+  C *Wc = static_cast<C *>(W);
+  const unsigned gx = (unsigned)(3 * N * N / Rr), gy = (unsigned)(3 * N * (N / Uy)), gz = (unsigned)(N * (N / Uz));
+  fft_x_kernel<T, true><<<dim3(gx, m, nb), 256, sx, ctx->stream>>>(Rc, sr, Wc, sw, tw, act, logN, Rr);
+  PC_CK_LAUNCH();
+  fft_y_kernel<T, true><<<dim3(gy, m, nb), 256, sy, ctx->stream>>>(Wc, sw, Wc, sw, tw, act, logN, Uy);
+  PC_CK_LAUNCH();
+  fft_z_symbol_kernel<T><<<dim3(gz, m, nb), 256, sz, ctx->stream>>>(Wc, sw, Wc, sw, tw, ctx->symd.as<double2>(),
+                                                                    ctx->kparam.as<KParam>(), act, logN, Uz,
+                                                                    ctx->opts.precond == PC_PRECOND_LAPLACIAN);
+  PC_CK_LAUNCH();
+  fft_y_kernel<T, false><<<dim3(gy, m, nb), 256, sy, ctx->stream>>>(Wc, sw, Wc, sw, tw, act, logN, Uy);
+  PC_CK_LAUNCH();
+  fft_x_kernel<T, false><<<dim3(gx, m, nb), 256, sx, ctx->stream>>>(Wc, sw, Wc, sw, tw, act, logN, Rr);
+  PC_CK_LAUNCH();
+  return PC_OK;
+}
+
+int launch_precond(pc_ctx *ctx, int nb, int m, int dtype, const void *R, long sr, void *W, long sw,
+                   const int *act) {
+  if (nb == 0 || m == 0) return PC_OK;
+  if (dtype == PC_C128) return launch_precond_t<double>(ctx, nb, m, R, sr, W, sw, act);
+  return launch_precond_t<float>(ctx, nb, m, R, sr, W, sw, act);
+}
+
+}  // namespace pc
+
+using namespace pc;
+
+extern "C" int pc_apply_precond(pc_ctx *ctx, int nb, const double *kpts, const double *gammas, int m, int dtype,
+                                const void *R, void *W) {
+  PC_REQUIRE(ctx && kpts && gammas && R && W, "pc_apply_precond: null argument");
+  PC_REQUIRE(nb >= 0 && m >= 0, "pc_apply_precond: negative size");
+  PC_REQUIRE(dtype == PC_C128 || dtype == PC_C64, "pc_apply_precond: bad dtype %d", dtype);
+  int rc = upload_kpoints(ctx, nb, kpts, gammas);
+  if (rc) return rc;
+  const long blk = (long)m * 3 * ctx->n;
+  return launch_precond(ctx, nb, m, dtype, R, blk, W, blk, nullptr);
+}

@@ -1,0 +1,90 @@
+// Permittivity at the edge DoFs from a list of dielectric spheres (Section 4.4), one thread per edge.
+// x-edge (i,j,k) sits at ((i+1/2)h, jh, kh), y-edge at (ih, (j+1/2)h, kh), z-edge at (ih, jh, (k+1/2)h); cells at
+// ((i+1/2)h, (j+1/2)h, (k+1/2)h). A point is inside a sphere when its distance to the nearest periodic image of the
+// centre is <= r; later spheres take precedence. An edge within 1e-12 of a sphere surface takes the interface rule
+// eps = (sum of eps at the 4 cell centres sharing the edge) / 4, i.e. M0 = 4 / sum (harmonic rule of Section 4.4).
+// Arithmetic uses explicit round-to-nearest intrinsics (no fused multiply-add) so that the classification of a
+// point does not depend on instruction selection.
+#include <vector>
+
+#include "pc_internal.cuh"
+
+namespace pc {
+
+constexpr double IFACE_TOL = 1e-12;
+
+__device__ double sphere_dist(double px, double py, double pz, const double *s) {
+  double dx = __dsub_rn(px, s[0]), dy = __dsub_rn(py, s[1]), dz = __dsub_rn(pz, s[2]);
+  dx = __dsub_rn(dx, rint(dx));
+  dy = __dsub_rn(dy, rint(dy));
+  dz = __dsub_rn(dz, rint(dz));
+  return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+}
+
+__device__ double eps_point(double px, double py, double pz, const double *sph, int nsph, double eps_bg,
+                            bool *iface) {
+  double e = eps_bg;
+  bool on = false;
+  for (int s = 0; s < nsph; ++s) {
+    const double *sp = sph + 5 * s;
+    const double d = sphere_dist(px, py, pz, sp);
+    if (d <= sp[3]) e = sp[4];
+    if (fabs(__dsub_rn(d, sp[3])) < IFACE_TOL) on = true;
+  }
+  if (iface) *iface = on;
+  return e;
+}
+
+__global__ void eps_edges_kernel(const double *__restrict__ sph, int nsph, double eps_bg, int N, double *out) {
+  const long n = (long)N * N * N;
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= 3 * n) return;
+  const int axis = (int)(gid / n);
+  const long r = gid - (long)axis * n;
+  const int ix = (int)(r % N), iy = (int)((r / N) % N), iz = (int)(r / ((long)N * N));
+  const double h = 1.0 / (double)N;
+  double p[3] = {__dmul_rn((double)ix, h), __dmul_rn((double)iy, h), __dmul_rn((double)iz, h)};
+  p[axis] = __dadd_rn(p[axis], __dmul_rn(0.5, h));
+  bool on = false;
+  double e = eps_point(p[0], p[1], p[2], sph, nsph, eps_bg, &on);
+  if (on) {
+    int o1 = (axis + 1) % 3, o2 = (axis + 2) % 3;
+    if (o1 > o2) {
+      const int t = o1;
+      o1 = o2;
+      o2 = t;
+    }
+    double total = 0.0;
+    for (int a = -1; a <= 0; ++a)
+      for (int c = -1; c <= 0; ++c) {
+        int idx[3] = {ix, iy, iz};
+        idx[o1] += a;
+        idx[o2] += c;
+        double q[3];
+        for (int d = 0; d < 3; ++d) q[d] = __dmul_rn(__dadd_rn((double)idx[d], 0.5), h);
+        total = __dadd_rn(total, eps_point(q[0], q[1], q[2], sph, nsph, eps_bg, nullptr));
+      }
+    e = total / 4.0;
+  }
+  out[gid] = e;
+}
+
+}  // namespace pc
+
+using namespace pc;
+
+extern "C" int pc_eps_spheres(int N, int nsph, const double *spheres, double eps_bg, double *eps_out) {
+  PC_REQUIRE(eps_out && (nsph == 0 || spheres), "pc_eps_spheres: null argument");
+  PC_REQUIRE(N >= 2 && N <= 1024 && nsph >= 0 && nsph <= 4096, "pc_eps_spheres: bad sizes");
+  PC_REQUIRE(eps_bg > 0.0, "pc_eps_spheres: eps_bg must be > 0");
+  for (int s = 0; s < nsph; ++s) PC_REQUIRE(spheres[5 * s + 4] > 0.0 && spheres[5 * s + 3] >= 0.0, "pc_eps_spheres: bad sphere %d", s);
+  const long total = 3L * N * N * N;
+  DevBuf ds, dout;
+  PC_CK(ds.reserve(sizeof(double) * 5 * std::max(nsph, 1)));
+  PC_CK(dout.reserve(sizeof(double) * total));
+  if (nsph) PC_CK(cudaMemcpy(ds.p, spheres, sizeof(double) * 5 * nsph, cudaMemcpyHostToDevice));
+  eps_edges_kernel<<<(unsigned)((total + 255) / 256), 256>>>(ds.as<double>(), nsph, eps_bg, N, dout.as<double>());
+  PC_CK_LAUNCH();
+  PC_CK(cudaMemcpy(eps_out, dout.p, sizeof(double) * total, cudaMemcpyDeviceToHost));
+  return PC_OK;
+}

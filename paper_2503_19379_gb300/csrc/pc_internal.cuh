@@ -1,0 +1,204 @@
+// Internal helpers shared by the libpc translation units: complex arithmetic on interleaved pairs, error state,
+// per-k-point parameters and the context layout.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "pc.h"
+
+namespace pc {
+
+// ---------------------------------------------------------------- complex on (x = re, y = im) pairs
+template <typename T> struct cplx_of;
+template <> struct cplx_of<double> { using type = double2; };
+template <> struct cplx_of<float> { using type = float2; };
+template <typename T> using cplx = typename cplx_of<T>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C cmake(decltype(C{}.x) re, decltype(C{}.x) im) {
+  C r;
+  r.x = re;
+  r.y = im;
+  return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return cmake<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return cmake<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+  return cmake<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {
+  return cmake<C>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+template <typename C, typename T> __host__ __device__ __forceinline__ C cscale(C a, T s) {
+  return cmake<C>(a.x * s, a.y * s);
+}
+
+// ---------------------------------------------------------------- per-k-point parameters
+struct KParam {
+  double k[3];   // Bloch vector (units 1/a)
+  double gamma;  // penalty of eq. pnt_number
+};
+
+// ---------------------------------------------------------------- error state
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define PC_CK(call)                                                   \
+  do {                                                                \
+    cudaError_t e_ = (call);                                          \
+    if (e_ != cudaSuccess) return pc::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+#define PC_CK_LAUNCH() PC_CK(cudaGetLastError())
+#define PC_REQUIRE(cond, ...)       \
+  do {                              \
+    if (!(cond)) {                  \
+      pc::set_error(__VA_ARGS__);   \
+      return PC_EINVAL;             \
+    }                               \
+  } while (0)
+
+inline int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+inline bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// ---------------------------------------------------------------- device buffer that frees itself
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  // grows (never shrinks) to at least nbytes; returns cudaSuccess or the allocation error
+  cudaError_t reserve(size_t nbytes) {
+    if (nbytes <= bytes) return cudaSuccess;
+    release();
+    cudaError_t e = cudaMalloc(&p, nbytes);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    bytes = nbytes;
+    return cudaSuccess;
+  }
+  template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
+}  // namespace pc
+
+// ---------------------------------------------------------------- the context
+struct pc_ctx {
+  int N = 0, logN = 0;
+  long n = 0;  // N^3
+  pc_opts opts{};
+  cudaStream_t stream = nullptr;
+  pc::DevBuf m0d, m0f;      // M0 diagonal, double and float copies, [3][N^3]
+  pc::DevBuf twd, twf;      // FFT twiddles exp(-2 pi i t / N), t < N/2
+  pc::DevBuf kparam;        // KParam [nb]
+  pc::DevBuf symd;          // per-k axis symbols d_i(m) complex128 [nb][3][N]
+  pc::DevBuf scratch;       // general scratch (partial sums)
+  int kcap = 0;             // capacity (k-points) of kparam / symd
+  // solver buffers
+  pc::DevBuf S[2], AS[2], Gm, Hm, coef, theta, norms, rnorm, rank, flag;
+  // mixed-precision solve: FP64 block X and AX, complex64 residual copy, coupling and FP64 X-X products, phases
+  pc::DevBuf X64[2], AX64, R32, RQ, GX, HX, phase, mask;
+  // tracing: per-stage statistics and event pairs awaiting harvest
+  bool timing = false;
+  pc_stage_stat stats[PC_NSTAGES] = {};
+  struct Pending {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  ~pc_ctx() {
+    for (auto &p : pending) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    for (auto e : event_pool) cudaEventDestroy(e);
+  }
+};
+
+namespace pc {
+// Runs one stage invocation: counts it, adds its algorithmic work, and brackets it with events when timing is on.
+template <typename F> int run_stage(pc_ctx *ctx, int stage, int kernels, double flops, double bytes, F &&launch);
+// Accumulates the elapsed times of finished event pairs (call after a stream synchronisation).
+int harvest_timing(pc_ctx *ctx);
+// uploads kparams (and symbol tables) for nb k-points into the context; returns 0 or an error code
+int upload_kpoints(pc_ctx *ctx, int nb, const double *kpts, const double *gammas);
+// kernels launched by the solver (all on ctx->stream)
+int launch_apply_op(pc_ctx *ctx, int nb, int m, int dtype, const void *X, long sx, void *Y, long sy,
+                    const int *act);
+int launch_precond(pc_ctx *ctx, int nb, int m, int dtype, const void *R, long sr, void *W, long sw,
+                   const int *act);
+int launch_gram(int nb, long L, int p, int q, int dtype, const void *A, long sa, const void *B, long sb, void *G,
+                void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act);
+size_t gram_scratch_bytes(int nb, long L, int p, int q);
+int launch_gram_pair(int nb, long L, int p, int dtype, const void *S, const void *AS, long ss, void *G, void *H,
+                     void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act);
+size_t gram_pair_scratch_bytes(int nb, long L, int p);
+// Y = S C (+ Z, a complex64 addend, if Z is not null); arithmetic in the precision of dtype
+int launch_block_update(int nb, long L, int p, int q, int dtype, const void *S, long ss, const void *C, long sc,
+                        void *Y, long sy, cudaStream_t st, const int *act, const void *Z = nullptr, long sz = 0);
+int launch_rr(int nb, int n, int m, const void *G, const void *H, double drop, double *theta, void *coef,
+              int *rank, cudaStream_t st, const int *act);
+int launch_residual(int nb, long L, int m, const void *X, long sx, const void *AX, long sax, const double *theta,
+                    void *R, long sr, double *norms, void *scratch, size_t scratch_bytes, cudaStream_t st,
+                    const int *act);
+size_t residual_scratch_bytes(int nb, long L, int m);
+int launch_recompute(pc_ctx *ctx, int nb, int m, const void *X, long sx, double *out, const int *act);
+int launch_deflate(int nb, long n, int m, void *X, long sx, const int *flags, void *scratch, cudaStream_t st,
+                   const int *act, int dtype = PC_C128);
+int launch_residual_mixed(int nb, long L, int m, int dtype_x, const void *X, long sx, const void *AX, long sax,
+                          const double *theta, void *R1, long sr1, void *R2, long sr2, void *X32, long sx32,
+                          void *AX32, long sax32, double *norms, void *scratch, size_t scratch_bytes,
+                          cudaStream_t st, const int *act);
+int launch_rr_patch(int nb, int n, int m, void *G, void *H, const void *RQ, const double *theta, const void *GX,
+                    const void *HX, const int *phase, cudaStream_t st, const int *act);
+int launch_widen(int nb, long L, int m, const void *X, long sx, void *Y, long sy, cudaStream_t st, const int *act);
+int launch_narrow(int nb, long L, int m, const void *X, long sx, void *Y, long sy, cudaStream_t st, const int *act);
+// the mixed-precision LOBPCG driver (solver_mixed.cu); k-points already reduced, gammas per k-point
+int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam, const std::vector<int> &zero,
+                int nbands, int m, double tol, double *evals, void *evecs, int *iters, double *resid);
+// counter-based initial columns; with mask (int [nb][m]) only the flagged columns of the act k-points are written
+int launch_init_block(int nb, long L, int m, uint64_t seed, int kidx0, void *X, long sx, cudaStream_t st,
+                      const int *mask = nullptr, const int *act = nullptr);
+// Algorithm 4.1 restart: flags (host, [nb][m]) the columns of the redo k-points to replace before the re-solve
+void spurious_mask(const std::vector<int> &redo, int m, int nbands, double tol, const std::vector<double> &theta,
+                   const std::vector<double> &rn, std::vector<int> &mask);
+}  // namespace pc
+
+namespace pc {
+cudaError_t get_event(pc_ctx *ctx, cudaEvent_t *e);
+
+template <typename F> int run_stage(pc_ctx *ctx, int stage, int kernels, double flops, double bytes, F &&launch) {
+  pc_stage_stat &st = ctx->stats[stage];
+  st.calls += 1;
+  st.kernels += kernels;
+  st.flops += flops;
+  st.bytes += bytes;
+  if (!ctx->timing) return launch();
+  cudaEvent_t a, b;
+  PC_CK(get_event(ctx, &a));
+  PC_CK(get_event(ctx, &b));
+  PC_CK(cudaEventRecord(a, ctx->stream));
+  int rc = launch();
+  PC_CK(cudaEventRecord(b, ctx->stream));
+  ctx->pending.push_back({stage, a, b});
+  return rc;
+}
+}  // namespace pc

@@ -1,0 +1,303 @@
+// Matrix-free compensated operator Op = A M0 A' + gamma B'B (eq. Ker_comp) on the staggered MFD grid, second-order
+// stencils (Section 4.1.2, eqs. stencils, blocks, discrete_2nd_block, derived_uniform_grid), and the half applies
+// A' x, B x used by Algorithm 4.1.
+//
+// Along axis i the shifted differences are, with kh = k_i / 2 and ih = 1/h,
+//   (D_i f)_r  = ih (f_{r+1} - f_r) + i kh (f_r + f_{r+1})          faces -> cells, edges -> faces (forward)
+//   (D_i' g)_r = ih (g_{r-1} - g_r) - i kh (g_{r-1} + g_r)          the conjugate transpose (backward)
+// A = [[0,-D3,D2],[D3,0,-D1],[-D2,D1,0]], A' = [[0,D3',-D2'],[-D3',0,D1'],[D2',-D1',0]], B = [D1 D2 D3],
+// B' = [D1'; D2'; D3'].
+//
+// The fused kernel stages a face tile with a one-point halo in shared memory, forms e = M0 A' v on the tile grown by
+// one point upward and c = B v on the tile grown by one point downward, then writes y = A e + gamma B' c. Every
+// input face value is read from global memory once per tile (plus halo).
+#include <cstdio>
+
+#include "pc_internal.cuh"
+
+namespace pc {
+
+template <typename C, typename T> __device__ __forceinline__ C dfwd(C f0, C f1, T ih, T kh) {
+  T ar = f1.x - f0.x, ai = f1.y - f0.y;
+  T sr = f0.x + f1.x, si = f0.y + f1.y;
+  return cmake<C>(ih * ar - kh * si, ih * ai + kh * sr);
+}
+template <typename C, typename T> __device__ __forceinline__ C dbwd(C gm, C g0, T ih, T kh) {
+  T ar = gm.x - g0.x, ai = gm.y - g0.y;
+  T sr = gm.x + g0.x, si = gm.y + g0.y;
+  return cmake<C>(ih * ar + kh * si, ih * ai - kh * sr);
+}
+
+template <typename T, int TX, int TY, int TZ> constexpr size_t op_smem_bytes() {
+  return sizeof(cplx<T>) * (size_t)(3 * (TZ + 2) * (TY + 2) * (TX + 2) + 3 * (TZ + 1) * (TY + 1) * (TX + 1) +
+                                    (TZ + 1) * (TY + 1) * (TX + 1));
+}
+
+template <typename T, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(256) op_kernel(const cplx<T> *__restrict__ X, long sx, cplx<T> *__restrict__ Y,
+                                                 long sy, const T *__restrict__ m0, const KParam *__restrict__ kp,
+                                                 const int *__restrict__ act, int logN, T ih) {
+  using C = cplx<T>;
+  constexpr int VX = TX + 2, VY = TY + 2, VZ = TZ + 2;
+  constexpr int EX = TX + 1, EY = TY + 1, EZ = TZ + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *v = reinterpret_cast<C *>(smem_raw);  // [3][VZ][VY][VX], global [o-1, o+T]
+  C *e = v + 3 * VZ * VY * VX;             // [3][EZ][EY][EX], global [o, o+T]
+  C *c = e + 3 * EZ * EY * EX;             // [EZ][EY][EX],    global [o-1, o+T-1]
+
+  const int N = 1 << logN, mask = N - 1;
+  const long n = 1L << (3 * logN);
+  const int b = act ? act[blockIdx.z] : (int)blockIdx.z;
+  const int j = blockIdx.y;
+  const int tilesX = N / TX, tilesY = N / TY;
+  int t = blockIdx.x;
+  const int x0 = (t % tilesX) * TX;
+  t /= tilesX;
+  const int y0 = (t % tilesY) * TY;
+  const int z0 = (t / tilesY) * TZ;
+  const C *Xb = X + (long)b * sx + (long)j * 3 * n;
+  C *Yb = Y + (long)b * sy + (long)j * 3 * n;
+  const KParam p = kp[b];
+  const T kh0 = (T)(0.5 * p.k[0]), kh1 = (T)(0.5 * p.k[1]), kh2 = (T)(0.5 * p.k[2]);
+  const T gam = (T)p.gamma;
+
+  for (int i = threadIdx.x; i < 3 * VZ * VY * VX; i += blockDim.x) {
+    int lx = i % VX, r = i / VX;
+    int ly = r % VY;
+    r /= VY;
+    int lz = r % VZ, comp = r / VZ;
+    int gx = (x0 + lx - 1) & mask, gy = (y0 + ly - 1) & mask, gz = (z0 + lz - 1) & mask;
+    v[i] = Xb[comp * n + ((long)gz << (2 * logN)) + ((long)gy << logN) + gx];
+  }
+  __syncthreads();
+
+  for (int i = threadIdx.x; i < EZ * EY * EX; i += blockDim.x) {
+    const int ex = i % EX, ey = (i / EX) % EY, ez = i / (EX * EY);
+    // e at global o + (ez,ey,ex): v local index + 1; its backward neighbours are local + 0
+#define VV(comp, dz, dy, dx) v[(((comp) * VZ + ez + 1 + (dz)) * VY + ey + 1 + (dy)) * VX + ex + 1 + (dx)]
+    const C v1 = VV(0, 0, 0, 0), v2 = VV(1, 0, 0, 0), v3 = VV(2, 0, 0, 0);
+    const C d3v2 = dbwd(VV(1, -1, 0, 0), v2, ih, kh2);
+    const C d2v3 = dbwd(VV(2, 0, -1, 0), v3, ih, kh1);
+    const C d3v1 = dbwd(VV(0, -1, 0, 0), v1, ih, kh2);
+    const C d1v3 = dbwd(VV(2, 0, 0, -1), v3, ih, kh0);
+    const C d2v1 = dbwd(VV(0, 0, -1, 0), v1, ih, kh1);
+    const C d1v2 = dbwd(VV(1, 0, 0, -1), v2, ih, kh0);
+#undef VV
+    const int gx = (x0 + ex) & mask, gy = (y0 + ey) & mask, gz = (z0 + ez) & mask;
+    const long gi = ((long)gz << (2 * logN)) + ((long)gy << logN) + gx;
+    const int eo = (ez * EY + ey) * EX + ex;
+    e[eo] = cscale(csub(d3v2, d2v3), m0[gi]);
+    e[EZ * EY * EX + eo] = cscale(csub(d1v3, d3v1), m0[n + gi]);
+    e[2 * EZ * EY * EX + eo] = cscale(csub(d2v1, d1v2), m0[2 * n + gi]);
+    // c at global o - 1 + (ez,ey,ex): v local index + 0; its forward neighbours are local + 1
+#define WW(comp, dz, dy, dx) v[(((comp) * VZ + ez + (dz)) * VY + ey + (dy)) * VX + ex + (dx)]
+    C cc = dfwd(WW(0, 0, 0, 0), WW(0, 0, 0, 1), ih, kh0);
+    cc = cadd(cc, dfwd(WW(1, 0, 0, 0), WW(1, 0, 1, 0), ih, kh1));
+    cc = cadd(cc, dfwd(WW(2, 0, 0, 0), WW(2, 1, 0, 0), ih, kh2));
+#undef WW
+    c[eo] = cc;
+  }
+  __syncthreads();
+
+  for (int i = threadIdx.x; i < TZ * TY * TX; i += blockDim.x) {
+    const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
+#define EE(comp, dz, dy, dx) e[(((comp) * EZ + lz + (dz)) * EY + ly + (dy)) * EX + lx + (dx)]
+#define CC(dz, dy, dx) c[((lz + 1 + (dz)) * EY + ly + 1 + (dy)) * EX + lx + 1 + (dx)]
+    const C c0 = CC(0, 0, 0);
+    const C e1 = EE(0, 0, 0, 0), e2 = EE(1, 0, 0, 0), e3 = EE(2, 0, 0, 0);
+    C y1 = csub(dfwd(e3, EE(2, 0, 1, 0), ih, kh1), dfwd(e2, EE(1, 1, 0, 0), ih, kh2));
+    y1 = cadd(y1, cscale(dbwd(CC(0, 0, -1), c0, ih, kh0), gam));
+    C y2 = csub(dfwd(e1, EE(0, 1, 0, 0), ih, kh2), dfwd(e3, EE(2, 0, 0, 1), ih, kh0));
+    y2 = cadd(y2, cscale(dbwd(CC(0, -1, 0), c0, ih, kh1), gam));
+    C y3 = csub(dfwd(e2, EE(1, 0, 0, 1), ih, kh0), dfwd(e1, EE(0, 0, 1, 0), ih, kh1));
+    y3 = cadd(y3, cscale(dbwd(CC(-1, 0, 0), c0, ih, kh2), gam));
+#undef EE
+#undef CC
+    const long gi = ((long)(z0 + lz) << (2 * logN)) + ((long)(y0 + ly) << logN) + x0 + lx;
+    Yb[gi] = y1;
+    Yb[n + gi] = y2;
+    Yb[2 * n + gi] = y3;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------ half applies
+// A' x at edge point r and B x at cell point r, read straight from global memory (not on the per-iteration path).
+struct HalfOut {
+  double2 e[3];
+  double2 c;
+};
+__device__ __forceinline__ HalfOut half_at(const double2 *__restrict__ x, long n, int logN, int gx, int gy, int gz,
+                                           double ih, double kh0, double kh1, double kh2) {
+  const int mask = (1 << logN) - 1;
+  auto at = [&](int comp, int z, int y, int xx) {
+    return x[comp * n + ((long)(z & mask) << (2 * logN)) + ((long)(y & mask) << logN) + (xx & mask)];
+  };
+  const double2 v1 = at(0, gz, gy, gx), v2 = at(1, gz, gy, gx), v3 = at(2, gz, gy, gx);
+  HalfOut o;
+  o.e[0] = csub(dbwd(at(1, gz - 1, gy, gx), v2, ih, kh2), dbwd(at(2, gz, gy - 1, gx), v3, ih, kh1));
+  o.e[1] = csub(dbwd(at(2, gz, gy, gx - 1), v3, ih, kh0), dbwd(at(0, gz - 1, gy, gx), v1, ih, kh2));
+  o.e[2] = csub(dbwd(at(0, gz, gy - 1, gx), v1, ih, kh1), dbwd(at(1, gz, gy, gx - 1), v2, ih, kh0));
+  o.c = cadd(cadd(dfwd(v1, at(0, gz, gy, gx + 1), ih, kh0), dfwd(v2, at(1, gz, gy + 1, gx), ih, kh1)),
+             dfwd(v3, at(2, gz + 1, gy, gx), ih, kh2));
+  return o;
+}
+
+__global__ void half_kernel(const double2 *__restrict__ X, double2 *__restrict__ E, double2 *__restrict__ Cc,
+                            const KParam *__restrict__ kp, int logN, int m, double ih) {
+  const long n = 1L << (3 * logN);
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = blockIdx.z, j = blockIdx.y;
+  const int N = 1 << logN;
+  const int gx = (int)(i & (N - 1)), gy = (int)((i >> logN) & (N - 1)), gz = (int)(i >> (2 * logN));
+  const KParam p = kp[b];
+  const double2 *x = X + ((long)b * m + j) * 3 * n;
+  HalfOut o = half_at(x, n, logN, gx, gy, gz, ih, 0.5 * p.k[0], 0.5 * p.k[1], 0.5 * p.k[2]);
+  if (E) {
+    double2 *eb = E + ((long)b * m + j) * 3 * n;
+    eb[i] = o.e[0];
+    eb[n + i] = o.e[1];
+    eb[2 * n + i] = o.e[2];
+  }
+  if (Cc) Cc[((long)b * m + j) * n + i] = o.c;
+}
+
+// per-block partial sums of (sum M0 |A'x|^2, sum |Bx|^2, sum |x|^2); grid (nchunk, m, nb)
+__global__ void recompute_partial_kernel(const double2 *__restrict__ X, long sx, const double *__restrict__ m0,
+                                         const KParam *__restrict__ kp, const int *__restrict__ act, int logN,
+                                         double ih, long chunk, double *__restrict__ part) {
+  const long n = 1L << (3 * logN);
+  const int N = 1 << logN;
+  const int bi = blockIdx.z;
+  const int b = act ? act[bi] : bi;
+  const int j = blockIdx.y;
+  const KParam p = kp[b];
+  const double2 *x = X + (long)b * sx + (long)j * 3 * n;
+  double s0 = 0, s1 = 0, s2 = 0;
+  const long beg = blockIdx.x * chunk, end = min(n, beg + chunk);
+  for (long i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    const int gx = (int)(i & (N - 1)), gy = (int)((i >> logN) & (N - 1)), gz = (int)(i >> (2 * logN));
+    HalfOut o = half_at(x, n, logN, gx, gy, gz, ih, 0.5 * p.k[0], 0.5 * p.k[1], 0.5 * p.k[2]);
+    for (int c = 0; c < 3; ++c) {
+      s0 += m0[c * n + i] * (o.e[c].x * o.e[c].x + o.e[c].y * o.e[c].y);
+      const double2 xv = x[c * n + i];
+      s2 += xv.x * xv.x + xv.y * xv.y;
+    }
+    s1 += o.c.x * o.c.x + o.c.y * o.c.y;
+  }
+  __shared__ double red[3][256];
+  red[0][threadIdx.x] = s0;
+  red[1][threadIdx.x] = s1;
+  red[2][threadIdx.x] = s2;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double *o = part + (((long)bi * gridDim.y + j) * gridDim.x + blockIdx.x) * 3;
+    o[0] = red[0][0];
+    o[1] = red[1][0];
+    o[2] = red[2][0];
+  }
+}
+
+__global__ void recompute_reduce_kernel(const double *__restrict__ part, int nchunk, int m,
+                                        const int *__restrict__ act, double *__restrict__ out) {
+  const int bi = blockIdx.x, j = threadIdx.x;
+  if (j >= m) return;
+  const int b = act ? act[bi] : bi;
+  double s[3] = {0, 0, 0};
+  for (int c = 0; c < nchunk; ++c)
+    for (int q = 0; q < 3; ++q) s[q] += part[(((long)bi * m + j) * nchunk + c) * 3 + q];
+  for (int q = 0; q < 3; ++q) out[((long)b * m + j) * 3 + q] = s[q];
+}
+
+// ------------------------------------------------------------------------------------------------ launchers
+template <typename T, int TX, int TY, int TZ>
+static int launch_op_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act) {
+  constexpr size_t smem = op_smem_bytes<T, TX, TY, TZ>();
+  static bool configured = false;  // attribute is per function; set once per process
+  if (!configured) {
+    PC_CK(cudaFuncSetAttribute(op_kernel<T, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = true;
+  }
+  const int N = ctx->N;
+  dim3 grid((N / TX) * (N / TY) * (N / TZ), m, nb);
+  const T *m0 = std::is_same<T, double>::value ? ctx->m0d.as<T>() : ctx->m0f.as<T>();
+  op_kernel<T, TX, TY, TZ><<<grid, 256, smem, ctx->stream>>>(
+      static_cast<const cplx<T> *>(X), sx, static_cast<cplx<T> *>(Y), sy, m0, ctx->kparam.as<KParam>(), act,
+      ctx->logN, (T)ctx->N);
+  PC_CK_LAUNCH();
+  return PC_OK;
+}
+
+int launch_apply_op(pc_ctx *ctx, int nb, int m, int dtype, const void *X, long sx, void *Y, long sy,
+                    const int *act) {
+  if (nb == 0 || m == 0) return PC_OK;
+  const int N = ctx->N;
+  if (dtype == PC_C128) {
+    if (N >= 32) return launch_op_t<double, 32, 4, 4>(ctx, nb, m, X, sx, Y, sy, act);
+    if (N == 16) return launch_op_t<double, 16, 4, 4>(ctx, nb, m, X, sx, Y, sy, act);
+    return launch_op_t<double, 8, 4, 4>(ctx, nb, m, X, sx, Y, sy, act);
+  }
+  if (N >= 32) return launch_op_t<float, 32, 4, 4>(ctx, nb, m, X, sx, Y, sy, act);
+  if (N == 16) return launch_op_t<float, 16, 4, 4>(ctx, nb, m, X, sx, Y, sy, act);
+  return launch_op_t<float, 8, 4, 4>(ctx, nb, m, X, sx, Y, sy, act);
+}
+
+int launch_recompute(pc_ctx *ctx, int nb, int m, const void *X, long sx, double *out, const int *act) {
+  if (nb == 0 || m == 0) return PC_OK;
+  const long n = ctx->n;
+  const int nchunk = (int)std::min<long>(64, (n + 4095) / 4096);
+  const long chunk = (n + nchunk - 1) / nchunk;
+  const size_t need = sizeof(double) * 3 * (size_t)nb * m * nchunk;
+  PC_CK(ctx->scratch.reserve(need));
+  recompute_partial_kernel<<<dim3(nchunk, m, nb), 256, 0, ctx->stream>>>(
+      static_cast<const double2 *>(X), sx, ctx->m0d.as<double>(), ctx->kparam.as<KParam>(), act, ctx->logN,
+      (double)ctx->N, chunk, ctx->scratch.as<double>());
+  PC_CK_LAUNCH();
+  recompute_reduce_kernel<<<nb, 64, 0, ctx->stream>>>(ctx->scratch.as<double>(), nchunk, m, act, out);
+  PC_CK_LAUNCH();
+  return PC_OK;
+}
+
+}  // namespace pc
+
+using namespace pc;
+
+extern "C" int pc_apply_op(pc_ctx *ctx, int nb, const double *kpts, const double *gammas, int m, int dtype,
+                           const void *X, void *Y) {
+  PC_REQUIRE(ctx && kpts && gammas && X && Y, "pc_apply_op: null argument");
+  PC_REQUIRE(nb >= 0 && m >= 0, "pc_apply_op: negative size");
+  PC_REQUIRE(dtype == PC_C128 || dtype == PC_C64, "pc_apply_op: bad dtype %d", dtype);
+  int rc = upload_kpoints(ctx, nb, kpts, gammas);
+  if (rc) return rc;
+  const long blk = (long)m * 3 * ctx->n;
+  return launch_apply_op(ctx, nb, m, dtype, X, blk, Y, blk, nullptr);
+}
+
+extern "C" int pc_apply_half(pc_ctx *ctx, int nb, const double *kpts, int m, const void *X, void *E, void *C) {
+  PC_REQUIRE(ctx && kpts && X, "pc_apply_half: null argument");
+  PC_REQUIRE(nb >= 0 && m >= 0, "pc_apply_half: negative size");
+  if (nb == 0 || m == 0) return PC_OK;
+  std::vector<double> g(nb, 1.0);
+  int rc = upload_kpoints(ctx, nb, kpts, g.data());
+  if (rc) return rc;
+  dim3 grid((unsigned)((ctx->n + 255) / 256), m, nb);
+  half_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const double2 *>(X), static_cast<double2 *>(E),
+                                              static_cast<double2 *>(C), ctx->kparam.as<KParam>(), ctx->logN, m,
+                                              (double)ctx->N);
+  PC_CK_LAUNCH();
+  return PC_OK;
+}
+
+extern "C" int pc_recompute_norms(pc_ctx *ctx, int nb, const double *kpts, int m, const void *X, double *out) {
+  PC_REQUIRE(ctx && kpts && X && out, "pc_recompute_norms: null argument");
+  PC_REQUIRE(nb >= 0 && m >= 0 && m <= 64, "pc_recompute_norms: bad size");
+  std::vector<double> g(nb, 1.0);
+  int rc = upload_kpoints(ctx, nb, kpts, g.data());
+  if (rc) return rc;
+  return launch_recompute(ctx, nb, m, X, (long)m * 3 * ctx->n, out, nullptr);
+}

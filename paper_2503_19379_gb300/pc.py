@@ -1,0 +1,307 @@
+"""ctypes binding of libpc (include/pc.h): same entry points, argument marshalling only.
+
+Host buffers are numpy arrays; device buffers are torch CUDA tensors (complex128 / complex64 / float64), used only
+as device memory. Work is issued on torch's current CUDA stream unless a stream is given.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libpc.so")
+
+PC_C128, PC_C64 = 0, 1
+PC_PRECOND_GAMMA, PC_PRECOND_LAPLACIAN = 0, 1
+PC_PREC_FP64, PC_PREC_MIXED = 0, 1
+PC_NOT_CONVERGED, PC_SPURIOUS = 1, 2
+
+
+class PCError(RuntimeError):
+    pass
+
+
+STAGES = ("stencil", "precond", "gram", "rr", "update", "residual", "recompute", "other")
+
+
+class StageStat(C.Structure):
+    _fields_ = [("calls", C.c_long), ("kernels", C.c_long), ("ms", C.c_double), ("flops", C.c_double),
+                ("bytes", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("order", C.c_int), ("gamma_override", C.c_double), ("precond", C.c_int), ("precision", C.c_int),
+                ("guard", C.c_int), ("maxiter", C.c_int), ("max_doublings", C.c_int), ("seed", C.c_uint64)]
+
+
+_LIB = None
+_vp, _i, _l, _d, _u64 = C.c_void_p, C.c_int, C.c_long, C.c_double, C.c_uint64
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+SIGNATURES = {
+    "pc_opts_default": (_i, [C.POINTER(Opts)]),
+    "pc_setup": (_i, [C.POINTER(_vp), _i, _dp, _dp, C.POINTER(Opts), _vp]),
+    "pc_solve": (_i, [_vp, _i, _dp, _i, _d, _dp, _vp, _ip, _dp]),
+    "pc_destroy": (None, [_vp]),
+    "pc_last_error": (C.c_char_p, []),
+    "pc_eps_spheres": (_i, [_i, _i, _dp, _d, _dp]),
+    "pc_apply_op": (_i, [_vp, _i, _dp, _dp, _i, _i, _vp, _vp]),
+    "pc_apply_half": (_i, [_vp, _i, _dp, _i, _vp, _vp, _vp]),
+    "pc_recompute_norms": (_i, [_vp, _i, _dp, _i, _vp, _vp]),
+    "pc_apply_precond": (_i, [_vp, _i, _dp, _dp, _i, _i, _vp, _vp]),
+    "pc_gram": (_i, [_i, _l, _i, _i, _i, _vp, _l, _vp, _l, _vp, _vp]),
+    "pc_gram_pair": (_i, [_i, _l, _i, _i, _vp, _l, _vp, _vp, _vp, _vp]),
+    "pc_block_update": (_i, [_i, _l, _i, _i, _i, _vp, _l, _vp, _vp, _l, _vp]),
+    "pc_eigh_batched": (_i, [_i, _i, _vp, _vp, _vp, _vp]),
+    "pc_rayleigh_ritz": (_i, [_i, _i, _i, _vp, _vp, _d, _vp, _vp, _vp, _vp]),
+    "pc_residual": (_i, [_i, _l, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pc_init_block": (_i, [_i, _l, _i, _u64, _i, _vp, _vp]),
+    "pc_set_timing": (_i, [_vp, _i]),
+    "pc_get_stats": (_i, [_vp, C.POINTER(StageStat)]),
+    "pc_reset_stats": (_i, [_vp]),
+}
+
+
+def lib():
+    """Load libpc.so (built in-tree); raises if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIBPATH):
+            raise PCError(f"{LIBPATH} is missing: build it with paper_2503_19379_gb300.build.build()")
+        L = C.CDLL(LIBPATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(rc, what, warn_ok=False):
+    if rc < 0 or (rc > 0 and not warn_ok):
+        raise PCError(f"{what} failed ({rc}): {lib().pc_last_error().decode()}")
+    return rc
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    torch = _torch()
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, dtypes=None):
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise PCError("expected a contiguous CUDA tensor")
+    if dtypes is not None and t.dtype not in dtypes:
+        raise PCError(f"unexpected dtype {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _dtype_code(t):
+    torch = _torch()
+    if t.dtype == torch.complex128:
+        return PC_C128
+    if t.dtype == torch.complex64:
+        return PC_C64
+    raise PCError(f"unsupported dtype {t.dtype}")
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    _check(lib().pc_opts_default(C.byref(o)), "pc_opts_default")
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def eps_spheres(N: int, spheres, eps_bg: float) -> np.ndarray:
+    """Permittivity at the edge DoFs, host array (3, N, N, N) (pc_eps_spheres)."""
+    sph = np.ascontiguousarray(np.asarray(spheres, dtype=np.float64).reshape(-1, 5))
+    out = np.empty((3, N, N, N), dtype=np.float64)
+    _check(lib().pc_eps_spheres(N, sph.shape[0], _dptr(sph) if sph.size else None, float(eps_bg), _dptr(out)),
+           "pc_eps_spheres")
+    return out
+
+
+class Solver:
+    """One structure on one grid: pc_setup / pc_solve / pc_destroy and the step-level kernels."""
+
+    def __init__(self, N: int, eps_edges: np.ndarray, stream=None, **opts):
+        self.N = int(N)
+        self.n = self.N ** 3
+        eps = np.ascontiguousarray(np.asarray(eps_edges, dtype=np.float64).reshape(3, N, N, N))
+        self.opts = default_opts(**opts)
+        self._stream = _stream(stream)
+        h = C.c_void_p()
+        lat = np.eye(3).ravel()
+        _check(lib().pc_setup(C.byref(h), self.N, _dptr(eps), _dptr(lat), C.byref(self.opts), self._stream),
+               "pc_setup")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, kpts, nbands: int, tol: float, want_vectors: bool = False):
+        """pc_solve; returns dict(evals, iters, resid, status[, evecs (torch complex128 on the device)])."""
+        k = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
+        nk = k.shape[0]
+        evals = np.zeros((nk, nbands))
+        resid = np.zeros((nk, nbands))
+        iters = np.zeros(nk, dtype=np.int32)
+        evecs = None
+        if want_vectors:
+            torch = _torch()
+            evecs = torch.empty((nk, nbands, 3, self.N, self.N, self.N), dtype=torch.complex128, device="cuda")
+        rc = lib().pc_solve(self._h, nk, _dptr(k), nbands, float(tol), _dptr(evals),
+                            _dev(evecs) if evecs is not None else None, iters.ctypes.data_as(_ip), _dptr(resid))
+        _check(rc, "pc_solve", warn_ok=True)
+        out = {"evals": evals, "iters": iters, "resid": resid, "status": rc}
+        if evecs is not None:
+            out["evecs"] = evecs
+        return out
+
+    # ---- tracing
+    def set_timing(self, enable: bool):
+        _check(lib().pc_set_timing(self._h, int(bool(enable))), "pc_set_timing")
+
+    def reset_stats(self):
+        _check(lib().pc_reset_stats(self._h), "pc_reset_stats")
+
+    def stats(self) -> dict:
+        arr = (StageStat * len(STAGES))()
+        _check(lib().pc_get_stats(self._h, arr), "pc_get_stats")
+        return {name: {"calls": a.calls, "kernels": a.kernels, "ms": a.ms, "flops": a.flops, "bytes": a.bytes}
+                for name, a in zip(STAGES, arr)}
+
+    # ---- step-level kernels (device tensors shaped (nb, m, 3, N, N, N))
+    def apply_op(self, kpts, gammas, X):
+        k = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
+        g = np.ascontiguousarray(np.asarray(gammas, dtype=np.float64).reshape(-1))
+        Y = _torch().empty_like(X)
+        nb, m = X.shape[0], X.shape[1]
+        _check(lib().pc_apply_op(self._h, nb, _dptr(k), _dptr(g), m, _dtype_code(X), _dev(X), _dev(Y)),
+               "pc_apply_op")
+        return Y
+
+    def apply_half(self, kpts, X):
+        torch = _torch()
+        k = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
+        nb, m = X.shape[0], X.shape[1]
+        E = torch.empty_like(X)
+        Cc = torch.empty((nb, m, self.N, self.N, self.N), dtype=X.dtype, device=X.device)
+        _check(lib().pc_apply_half(self._h, nb, _dptr(k), m, _dev(X, [torch.complex128]), _dev(E), _dev(Cc)),
+               "pc_apply_half")
+        return E, Cc
+
+    def recompute_norms(self, kpts, X):
+        torch = _torch()
+        k = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
+        nb, m = X.shape[0], X.shape[1]
+        out = torch.empty((nb, m, 3), dtype=torch.float64, device=X.device)
+        _check(lib().pc_recompute_norms(self._h, nb, _dptr(k), m, _dev(X, [torch.complex128]), _dev(out)),
+               "pc_recompute_norms")
+        return out
+
+    def apply_precond(self, kpts, gammas, R, out=None):
+        k = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
+        g = np.ascontiguousarray(np.asarray(gammas, dtype=np.float64).reshape(-1))
+        W = _torch().empty_like(R) if out is None else out
+        nb, m = R.shape[0], R.shape[1]
+        _check(lib().pc_apply_precond(self._h, nb, _dptr(k), _dptr(g), m, _dtype_code(R), _dev(R), _dev(W)),
+               "pc_apply_precond")
+        return W
+
+
+def gram(A, B, stream=None):
+    """G_b = A_b^H B_b for A (nb, p, L), B (nb, q, L) device tensors (columns contiguous)."""
+    torch = _torch()
+    nb, p, L = A.shape
+    q = B.shape[1]
+    G = torch.empty((nb, p, q), dtype=torch.complex128, device=A.device)
+    _check(lib().pc_gram(nb, L, p, q, _dtype_code(A), _dev(A), p * L, _dev(B), q * L, _dev(G), _stream(stream)),
+           "pc_gram")
+    return G
+
+
+def gram_pair(S, AS, stream=None):
+    """(G, H) = (S^H S, S^H AS) for panels S, AS (nb, p, L), Hermitian (upper triangle computed, mirrored)."""
+    torch = _torch()
+    nb, p, L = S.shape
+    G = torch.empty((nb, p, p), dtype=torch.complex128, device=S.device)
+    H = torch.empty_like(G)
+    _check(lib().pc_gram_pair(nb, L, p, _dtype_code(S), _dev(S), p * L, _dev(AS), _dev(G), _dev(H),
+                              _stream(stream)), "pc_gram_pair")
+    return G, H
+
+
+def block_update(S, Cm, stream=None):
+    """Y_b = S_b C_b for S (nb, p, L) (columns contiguous) and C (nb, p, q) complex128; returns (nb, q, L)."""
+    torch = _torch()
+    nb, p, L = S.shape
+    q = Cm.shape[2]
+    Y = torch.empty((nb, q, L), dtype=S.dtype, device=S.device)
+    _check(lib().pc_block_update(nb, L, p, q, _dtype_code(S), _dev(S), p * L, _dev(Cm, [torch.complex128]), _dev(Y),
+                                 q * L, _stream(stream)), "pc_block_update")
+    return Y
+
+
+def eigh_batched(A, stream=None):
+    torch = _torch()
+    nb, n, _ = A.shape
+    w = torch.empty((nb, n), dtype=torch.float64, device=A.device)
+    V = torch.empty_like(A)
+    _check(lib().pc_eigh_batched(nb, n, _dev(A, [torch.complex128]), _dev(w), _dev(V), _stream(stream)),
+           "pc_eigh_batched")
+    return w, V
+
+
+def rayleigh_ritz(G, H, m: int, drop: float = 1e-12, stream=None):
+    torch = _torch()
+    nb, n, _ = G.shape
+    theta = torch.empty((nb, m), dtype=torch.float64, device=G.device)
+    coef = torch.empty((nb, n, m), dtype=torch.complex128, device=G.device)
+    rank = torch.empty((nb,), dtype=torch.int32, device=G.device)
+    _check(lib().pc_rayleigh_ritz(nb, n, m, _dev(G, [torch.complex128]), _dev(H, [torch.complex128]), float(drop),
+                                  _dev(theta), _dev(coef), _dev(rank), _stream(stream)), "pc_rayleigh_ritz")
+    return theta, coef, rank
+
+
+def residual(X, AX, theta, stream=None):
+    """R = AX - X diag(theta) and column norms (|r|, |x|) for X, AX (nb, m, L) complex128."""
+    torch = _torch()
+    nb, m, L = X.shape
+    R = torch.empty_like(X)
+    norms = torch.empty((nb, m, 2), dtype=torch.float64, device=X.device)
+    _check(lib().pc_residual(nb, L, m, _dev(X, [torch.complex128]), _dev(AX, [torch.complex128]),
+                             _dev(theta, [torch.float64]), _dev(R), _dev(norms), _stream(stream)), "pc_residual")
+    return R, norms
+
+
+def init_block(nb: int, L: int, m: int, seed: int, kidx0: int = 0, stream=None):
+    torch = _torch()
+    X = torch.empty((nb, m, L), dtype=torch.complex128, device="cuda")
+    _check(lib().pc_init_block(nb, L, m, seed, kidx0, _dev(X), _stream(stream)), "pc_init_block")
+    return X

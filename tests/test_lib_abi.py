@@ -1,0 +1,68 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point that include/pc.h declares
+(no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pc.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*(pc_\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2503_19379_gb300 import build as b
+    if not os.path.exists(b.LIB):
+        b.build()
+    return b.LIB
+
+
+def test_header_declares_entry_points():
+    syms = declared_symbols()
+    for s in ("pc_setup", "pc_solve", "pc_destroy", "pc_last_error", "pc_apply_op", "pc_apply_precond", "pc_gram",
+              "pc_rayleigh_ritz", "pc_block_update", "pc_residual", "pc_recompute_norms", "pc_eps_spheres"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    missing = [s for s in declared_symbols() if not hasattr(L, s)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2503_19379_gb300 import pc
+    assert set(declared_symbols()) <= set(pc.SIGNATURES)
+
+
+def test_opts_default_and_errors_without_gpu(libpath):
+    """Host-side validation runs without a device: bad arguments are rejected before any CUDA call."""
+    from paper_2503_19379_gb300 import pc
+    o = pc.default_opts()
+    assert (o.order, o.guard, o.maxiter, o.precision) == (1, -1, 400, 0)
+    import numpy as np
+    h = ctypes.c_void_p()
+    eps = np.ones(3 * 6 ** 3)
+    rc = pc.lib().pc_setup(ctypes.byref(h), 6, pc._dptr(eps), None, None, None)  # N not a power of two >= 8
+    assert rc == -1 and b"power of two" in pc.lib().pc_last_error()
+    eps = np.ones(3 * 8 ** 3)
+    eps[5] = -1.0
+    rc = pc.lib().pc_setup(ctypes.byref(h), 8, pc._dptr(eps), None, None, None)
+    assert rc == -1 and b"eps_edges" in pc.lib().pc_last_error()
+    lat = np.diag([1.0, 2.0, 1.0]).ravel()
+    rc = pc.lib().pc_setup(ctypes.byref(h), 8, pc._dptr(np.ones(3 * 8 ** 3)), pc._dptr(lat), None, None)
+    assert rc == -2
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_2503_19379_gb300 import pc
+    monkeypatch.setattr(pc, "_LIB", None)
+    monkeypatch.setattr(pc, "LIBPATH", str(tmp_path / "nope.so"))
+    with pytest.raises(pc.PCError):
+        pc.lib()

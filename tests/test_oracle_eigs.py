@@ -64,7 +64,7 @@ def test_algorithm_4_1_doubles_gamma_until_clean():
     h = 1.0 / N
     k = np.array([0.3, 0.1, 0.2])
     m0 = sphere_m0(N)
-    out = eigs.solve_kpoint(N, k, m0, 6, 1e-11, guard=3, gamma=0.5)
+    out = eigs.solve_kpoint(N, k, m0, 6, 1e-11, guard=3, gamma=1.0)
     assert out["doublings"] >= 1 and not out["spurious"].any()
     wa = np.linalg.eigvalsh(mfd.curl_part(N, k, h, m0).toarray())
     phys = np.sort(wa[wa > 1e-10 * wa.max()])[:6]
