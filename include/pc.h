@@ -180,6 +180,21 @@ int pc_gram(int nb, long L, int p, int q, int dtype, const void *A, long sa, con
 int pc_gram_pair(int nb, long L, int p, int dtype, const void *S, long ss, const void *AS, void *G, void *H,
                  void *stream);
 
+/* pc_gram_pair_noalloc -- the same products as pc_gram_pair, for callers that cannot allocate device memory:
+ * code that runs under a fixed device-memory budget, inside an application whose own allocator must own every
+ * allocation, or in latency-critical loops where cudaMalloc/cudaFree would synchronise the device. It calls no
+ * cudaMalloc, cudaFree or other allocating routine; its partial sums live in a 4 MiB array that is part of the
+ * library image, so every GPU that loads the library holds those 4 MiB until the process exits.
+ * This entry point has no counterpart in the paper; it is an interface convenience.
+ *   Limit: 2 * 16 * nb * p * p <= 4 MiB, i.e. nb * p * p <= 131072 (for example 32 k-points of 64 columns);
+ *   larger requests return PC_EINVAL with a message. Arguments, layout and results are those of pc_gram_pair.
+ *   The first call on each device looks up the array's device address (cudaGetSymbolAddress) with that device
+ *   current; make that first call before any stream capture. Every call reuses the same array and only reads
+ *   entries it has written itself, so no state carries over between calls, but calls whose work overlaps on the
+ *   GPU (other streams, other host threads) race on the array and must be serialised by the caller. */
+int pc_gram_pair_noalloc(int nb, long L, int p, int dtype, const void *S, long ss, const void *AS, void *G, void *H,
+                         void *stream);
+
 /* a5: Y_b = S_b C_b: S_b has p columns of length L (batch stride ss), C_b device complex128 [p][q] row-major
  * (batch stride p*q), Y_b has q columns (batch stride sy). p <= 64, q <= 64. dtype applies to S and Y. */
 int pc_block_update(int nb, long L, int p, int q, int dtype, const void *S, long ss, const void *C, void *Y,

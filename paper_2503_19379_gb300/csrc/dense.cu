@@ -2,6 +2,7 @@
 // R = AX - X Theta with column norms, the k = 0 projection of the constant fields, and the counter-based initial
 // blocks. Blocks are column-major: column j of a block with L rows starts at j * L.
 #include <cmath>
+#include <mutex>
 
 #include "pc_internal.cuh"
 
@@ -747,4 +748,68 @@ extern "C" int pc_init_block(int nb, long L, int m, uint64_t seed, int kidx0, vo
   PC_REQUIRE(X, "pc_init_block: null argument");
   PC_REQUIRE(nb >= 0 && L >= 0 && m >= 0 && m < 4096, "pc_init_block: bad sizes");
   return launch_init_block(nb, L, m, seed, kidx0, X, (long)m * L, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------------------------------------ no-allocation
+// pc_gram_pair_noalloc: the Gram pair of pc_gram_pair for callers that must not allocate device memory. Its
+// per-chunk partial sums live in this fixed array instead of a cudaMalloc'd buffer. The array is part of the
+// library image, so every GPU that loads the library holds these bytes until the process exits.
+namespace pc {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = 4u << 20;  // 4 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch, looked up once per device. In host code the symbol names a host-side
+// stand-in, not device memory, so kernels must be given the address returned by cudaGetSymbolAddress.
+static int noalloc_scratch_address(void **out) {
+  static std::mutex mu;
+  static void *addr[64] = {};
+  int dev = 0;
+  PC_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("pc_gram_pair_noalloc: device index %d out of range", dev);
+    return PC_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    PC_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    addr[dev] = p;
+  }
+  *out = addr[dev];
+  return PC_OK;
+}
+
+}  // namespace pc
+
+extern "C" int pc_gram_pair_noalloc(int nb, long L, int p, int dtype, const void *S, long ss, const void *AS, void *G,
+                                    void *H, void *stream) {
+  PC_REQUIRE(S && AS && G && H, "pc_gram_pair_noalloc: null argument");
+  PC_REQUIRE(nb >= 0 && L >= 0 && p >= 1 && p <= 64, "pc_gram_pair_noalloc: bad sizes");
+  PC_REQUIRE(dtype == PC_C128 || dtype == PC_C64, "pc_gram_pair_noalloc: bad dtype");
+  if (nb == 0) return PC_OK;
+  // two partial panels (G and H) of nb * nchunk * p * p complex128 must fit in the fixed array
+  const size_t per_chunk = 2 * sizeof(double2) * (size_t)nb * p * p;
+  const size_t fit = NOALLOC_SCRATCH_BYTES / per_chunk;
+  if (fit < 1) {
+    set_error("pc_gram_pair_noalloc: nb * p * p = %zu exceeds the fixed scratch (at most %zu, i.e. 2*16*nb*p*p <= %zu "
+              "bytes)", (size_t)nb * p * p, NOALLOC_SCRATCH_BYTES / (2 * sizeof(double2)), NOALLOC_SCRATCH_BYTES);
+    return PC_EINVAL;
+  }
+  void *scratch = nullptr;
+  int rc = noalloc_scratch_address(&scratch);
+  if (rc) return rc;
+  const int nchunk = (int)std::min<size_t>((size_t)gram_chunks(nb, L), fit);
+  long chunk = (L + nchunk - 1) / nchunk;
+  chunk = (chunk + GRAM_TL - 1) / GRAM_TL * GRAM_TL;
+  double2 *part = static_cast<double2 *>(scratch);
+  cudaStream_t st = (cudaStream_t)stream;
+  // every partial entry the reduction reads (i <= j of each chunk) is written first in this call: nothing to clear
+  rc = dtype == PC_C128 ? launch_gram_pair_t<double>(nb, L, p, S, AS, ss, part, nchunk, chunk, st, nullptr)
+                        : launch_gram_pair_t<float>(nb, L, p, S, AS, ss, part, nchunk, chunk, st, nullptr);
+  if (rc) return rc;
+  gram_pair_reduce_kernel<<<nb, 256, 0, st>>>(part, part + (size_t)nb * nchunk * p * p, nchunk, p, nullptr,
+                                              static_cast<double2 *>(G), static_cast<double2 *>(H));
+  PC_CK_LAUNCH();
+  return PC_OK;
 }

@@ -54,6 +54,7 @@ SIGNATURES = {
     "pc_apply_precond": (_i, [_vp, _i, _dp, _dp, _i, _i, _vp, _vp]),
     "pc_gram": (_i, [_i, _l, _i, _i, _i, _vp, _l, _vp, _l, _vp, _vp]),
     "pc_gram_pair": (_i, [_i, _l, _i, _i, _vp, _l, _vp, _vp, _vp, _vp]),
+    "pc_gram_pair_noalloc": (_i, [_i, _l, _i, _i, _vp, _l, _vp, _vp, _vp, _vp]),
     "pc_block_update": (_i, [_i, _l, _i, _i, _i, _vp, _l, _vp, _vp, _l, _vp]),
     "pc_eigh_batched": (_i, [_i, _i, _vp, _vp, _vp, _vp]),
     "pc_rayleigh_ritz": (_i, [_i, _i, _i, _vp, _vp, _d, _vp, _vp, _vp, _vp]),
