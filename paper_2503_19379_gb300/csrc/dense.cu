@@ -4,6 +4,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "dfloat.cuh"
 #include "pc_internal.cuh"
 
 namespace pc {
@@ -438,12 +439,23 @@ __global__ void __launch_bounds__(256) residual_mixed_partial_kernel(
   float2 *r2 = R2 + (long)b * sr2 + (long)j * L;
   float2 *x32 = X32 ? X32 + (long)b * sx32 + (long)j * L : nullptr;
   float2 *ax32 = AX32 ? AX32 + (long)b * sax32 + (long)j * L : nullptr;
-  TX sr = 0, sxx = 0;
+  float sr = 0.f, sxx = 0.f;  // column sums need ~3 digits: FP32 per thread, FP64 per block
   const long beg = (long)blockIdx.x * chunk, end = min(L, beg + chunk);
   for (long l = beg + threadIdx.x; l < end; l += blockDim.x) {
     const cplx<TX> xv = x[l], av = ax[l];
-    const TX rx = av.x - th * xv.x, ry = av.y - th * xv.y;
-    const float2 rf = make_float2((float)rx, (float)ry);
+    float rx, ry;
+    if constexpr (std::is_same<TX, double>::value) {
+      // r = ax - theta x cancels to ~tol |ax|: double-float arithmetic keeps it exact to ~2^-44 |ax| on the FP32 pipe
+      const df t = df_from((double)th);
+      const df rxd = df_sub(df_from(av.x), df_mul(t, df_from(xv.x)));
+      const df ryd = df_sub(df_from(av.y), df_mul(t, df_from(xv.y)));
+      rx = rxd.hi + rxd.lo;
+      ry = ryd.hi + ryd.lo;
+    } else {
+      rx = av.x - th * xv.x;
+      ry = av.y - th * xv.y;
+    }
+    const float2 rf = make_float2(rx, ry);
     r1[l] = rf;
     r2[l] = rf;
     if (x32) {
@@ -451,7 +463,7 @@ __global__ void __launch_bounds__(256) residual_mixed_partial_kernel(
       ax32[l] = make_float2((float)av.x, (float)av.y);
     }
     sr += rx * rx + ry * ry;
-    sxx += xv.x * xv.x + xv.y * xv.y;
+    sxx += (float)xv.x * (float)xv.x + (float)xv.y * (float)xv.y;
   }
   __shared__ double red[2][256];
   red[0][threadIdx.x] = (double)sr;

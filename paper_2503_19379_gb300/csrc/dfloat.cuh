@@ -1,0 +1,74 @@
+// Double-float ("float-float") arithmetic: a value is an unevaluated sum hi + lo of two FP32 numbers with
+// |lo| <= ulp(hi)/2, about 48 significant bits. Built from the error-free transformations
+//   two_sum(a, b):  s = fl(a + b), e = (a - (s - bb)) + (b - bb), bb = s - a   (Knuth), a + b = s + e exactly;
+//   two_prod(a, b): p = fl(a b),   e = fma(a, b, -p),                             a b = p + e exactly;
+// (Dekker 1971; Hida, Li and Bailey, "Library for double-double and quad-double arithmetic", 2001).
+// On GB300 the FP32 pipe is ~62x faster than the FP64 pipe, so the FP64-accurate parts of the mixed-precision solve
+// (the block X, its operator image, the X-X Gram block) run in this format: ~10 FP32 operations per operation, a
+// relative error of ~2^-44 instead of 2^-53, which the eigensolver does not resolve (its FP64 residual floor is
+// ~1e-10 here).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace pc {
+
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df df_from(double x) {
+  df r;
+  r.hi = (float)x;
+  r.lo = (float)(x - (double)r.hi);
+  return r;
+}
+__device__ __forceinline__ double df_to(df x) { return (double)x.hi + (double)x.lo; }
+
+__device__ __forceinline__ df quick_two_sum(float a, float b) {  // requires |a| >= |b| (or a == 0)
+  df r;
+  r.hi = a + b;
+  r.lo = b - (r.hi - a);
+  return r;
+}
+__device__ __forceinline__ df two_sum(float a, float b) {
+  df r;
+  r.hi = a + b;
+  const float bb = r.hi - a;
+  r.lo = (a - (r.hi - bb)) + (b - bb);
+  return r;
+}
+__device__ __forceinline__ df df_add(df x, df y) {
+  const df s = two_sum(x.hi, y.hi);
+  return quick_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+__device__ __forceinline__ df df_neg(df x) { return df{-x.hi, -x.lo}; }
+__device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df_neg(y)); }
+__device__ __forceinline__ df df_mul(df x, df y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return quick_two_sum(p, e);
+}
+// multiplication by a power of two (exact)
+__device__ __forceinline__ df df_scale2(df x, float s) { return df{x.hi * s, x.lo * s}; }
+
+// complex double-float
+struct cdf {
+  df re, im;
+};
+__device__ __forceinline__ cdf cdf_from(double2 z) { return cdf{df_from(z.x), df_from(z.y)}; }
+__device__ __forceinline__ double2 cdf_to(cdf z) { return make_double2(df_to(z.re), df_to(z.im)); }
+__device__ __forceinline__ cdf cdf_add(cdf a, cdf b) { return cdf{df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ cdf cdf_sub(cdf a, cdf b) { return cdf{df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
+__device__ __forceinline__ cdf cdf_mul(cdf a, cdf b) {
+  return cdf{df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+// conj(a) * b
+__device__ __forceinline__ cdf cdf_mulc(cdf a, cdf b) {
+  return cdf{df_add(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_sub(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+__device__ __forceinline__ cdf cdf_scale(cdf a, df s) { return cdf{df_mul(a.re, s), df_mul(a.im, s)}; }
+__device__ __forceinline__ cdf cdf_scale2(cdf a, float s) { return cdf{df_scale2(a.re, s), df_scale2(a.im, s)}; }
+
+}  // namespace pc

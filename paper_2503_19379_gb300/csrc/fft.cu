@@ -26,7 +26,9 @@ __device__ __forceinline__ int bitrev(int p, int logN) { return (int)(__brev((un
 // In-place radix-2 FFTs of `lines` lines of length N held in shared memory. Line l = g * lpg + u (group g, member
 // u) starts at g * gs + u * ls and its element t sits t * es further. Forward = DIF with exp(-), inverse = DIT with
 // exp(+).
-template <typename C, bool FWD>
+// LINE_MAJOR: consecutive threads take consecutive lines (for lines that are adjacent in memory, ls = 1, so that a
+// warp reads consecutive addresses); otherwise consecutive butterflies of one line (for contiguous lines, es = 1).
+template <typename C, bool FWD, bool LINE_MAJOR = false>
 __device__ __forceinline__ void fft_lines(C *a, int lines, int lpg, int gs, int ls, int es, int logN, const C *tw) {
   const int N = 1 << logN, halfN = N >> 1;
   const int total = lines * halfN;
@@ -34,7 +36,7 @@ __device__ __forceinline__ void fft_lines(C *a, int lines, int lpg, int gs, int 
     for (int lh = logN - 1; lh >= 0; --lh) {
       const int half = 1 << lh;
       for (int q = threadIdx.x; q < total; q += blockDim.x) {
-        const int l = q / halfN, r = q - l * halfN;
+        const int l = LINE_MAJOR ? q % lines : q / halfN, r = LINE_MAJOR ? q / lines : q - l * halfN;
         const int g = r >> lh, jj = r & (half - 1);
         const int lg = l / lpg, lu = l - lg * lpg;
         const int i0 = lg * gs + lu * ls + ((g << (lh + 1)) + jj) * es, i1 = i0 + half * es;
@@ -48,7 +50,7 @@ __device__ __forceinline__ void fft_lines(C *a, int lines, int lpg, int gs, int 
     for (int lh = 0; lh < logN; ++lh) {
       const int half = 1 << lh;
       for (int q = threadIdx.x; q < total; q += blockDim.x) {
-        const int l = q / halfN, r = q - l * halfN;
+        const int l = LINE_MAJOR ? q % lines : q / halfN, r = LINE_MAJOR ? q / lines : q - l * halfN;
         const int g = r >> lh, jj = r & (half - 1);
         const int lg = l / lpg, lu = l - lg * lpg;
         const int i0 = lg * gs + lu * ls + ((g << (lh + 1)) + jj) * es, i1 = i0 + half * es;
@@ -110,7 +112,7 @@ __global__ void __launch_bounds__(256) fft_y_kernel(const cplx<T> *__restrict__ 
     a[i] = in[base_i + (long)y * N + u];
   }
   __syncthreads();
-  fft_lines<C, FWD>(a, U, U, 0, 1, U, logN, s_tw);
+  fft_lines<C, FWD, true>(a, U, U, 0, 1, U, logN, s_tw);
   for (int i = threadIdx.x; i < N * U; i += blockDim.x) {
     const int y = i / U, u = i - y * U;
     out[base_o + (long)y * N + u] = a[i];
@@ -142,10 +144,10 @@ __global__ void __launch_bounds__(256) fft_z_symbol_kernel(const cplx<T> *__rest
     a[i] = in[base_i + comp * n + (long)z * N * N + u];
   }
   __syncthreads();
-  fft_lines<C, true>(a, 3 * U, U, N * U, 1, U, logN, s_tw);  // lines (comp, u); z stride U
+  fft_lines<C, true, true>(a, 3 * U, U, N * U, 1, U, logN, s_tw);  // lines (comp, u); z stride U
   // symbol inverse per mode
   const double2 *symb = sym + (long)b * 3 * N;
-  const double gam = kp[b].gamma;
+  const T fac = (T)((kp[b].gamma - 1.0) / kp[b].gamma);  // (gamma - 1) / gamma, once per block
   const T scale = (T)(1.0 / (double)n);
   const int my = bitrev(y, logN);
   const double2 d2d = symb[N + my];
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(256) fft_z_symbol_kernel(const cplx<T> *__rest
       const T inv = scale / sigma;
       if (!laplacian) {
         const C s = cadd(cadd(cmul(d1, r1), cmul(d2, r2)), cmul(d3, r3));  // d^T r
-        const T f = (T)((gam - 1.0) / gam) / sigma;
+        const T f = fac / sigma;
         r1 = csub(r1, cscale(cmulc(d1, s), f));  // conj(d1) * s
         r2 = csub(r2, cscale(cmulc(d2, s), f));
         r3 = csub(r3, cscale(cmulc(d3, s), f));
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(256) fft_z_symbol_kernel(const cplx<T> *__rest
     a[2 * N * U + i] = r3;
   }
   __syncthreads();
-  fft_lines<C, false>(a, 3 * U, U, N * U, 1, U, logN, s_tw);
+  fft_lines<C, false, true>(a, 3 * U, U, N * U, 1, U, logN, s_tw);
   for (int i = threadIdx.x; i < 3 * N * U; i += blockDim.x) {
     const int u = i % U, z = (i / U) % N, comp = i / (U * N);
     out[base_o + comp * n + (long)z * N * N + u] = a[i];

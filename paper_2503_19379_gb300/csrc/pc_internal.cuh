@@ -42,6 +42,8 @@ template <typename C, typename T> __host__ __device__ __forceinline__ C cscale(C
 struct KParam {
   double k[3];   // Bloch vector (units 1/a)
   double gamma;  // penalty of eq. pnt_number
+  float khf[3];  // k_i / 2 and gamma rounded to FP32, so that complex64 kernels do no FP64 arithmetic
+  float gammaf;
 };
 
 // ---------------------------------------------------------------- error state
@@ -171,6 +173,13 @@ int launch_rr_patch(int nb, int n, int m, void *G, void *H, const void *RQ, cons
                     const void *HX, const int *phase, cudaStream_t st, const int *act);
 int launch_widen(int nb, long L, int m, const void *X, long sx, void *Y, long sy, cudaStream_t st, const int *act);
 int launch_narrow(int nb, long L, int m, const void *X, long sx, void *Y, long sy, cudaStream_t st, const int *act);
+// double-float (FP32-pair) versions of the FP64-accurate kernels of the mixed solve (mixed_df.cu)
+int launch_apply_op_df(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act);
+int launch_update_df(int nb, long L, int p, int q, const void *X, long sx, const void *C, long sc, void *Y, long sy,
+                     const void *Z, long sz, cudaStream_t st, const int *act);
+int launch_gram_df(int nb, long L, int p, const void *S, const void *AS, long ss, void *G, void *H, void *scratch,
+                   size_t scratch_bytes, cudaStream_t st, const int *act);
+size_t gram_df_scratch_bytes(int nb, long L, int p);
 // the mixed-precision LOBPCG driver (solver_mixed.cu); k-points already reduced, gammas per k-point
 int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam, const std::vector<int> &zero,
                 int nbands, int m, double tol, double *evals, void *evecs, int *iters, double *resid);

@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -72,8 +73,12 @@ int upload_kpoints(pc_ctx *ctx, int nb, const double *kpts, const double *gammas
   std::vector<KParam> kp(nb);
   std::vector<double2> sym((size_t)3 * ctx->N * nb);
   for (int b = 0; b < nb; ++b) {
-    for (int d = 0; d < 3; ++d) kp[b].k[d] = kpts[3 * b + d];
+    for (int d = 0; d < 3; ++d) {
+      kp[b].k[d] = kpts[3 * b + d];
+      kp[b].khf[d] = (float)(0.5 * kpts[3 * b + d]);
+    }
     kp[b].gamma = gammas[b];
+    kp[b].gammaf = (float)gammas[b];
     for (int d = 0; d < 3; ++d) axis_symbols(ctx->N, kpts[3 * b + d], &sym[((size_t)b * 3 + d) * ctx->N]);
   }
   PC_CK(cudaMemcpyAsync(ctx->kparam.p, kp.data(), sizeof(KParam) * nb, cudaMemcpyHostToDevice, ctx->stream));
@@ -287,6 +292,7 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
   PC_CK(ctx->mask.reserve(sizeof(int) * (size_t)nb * m));
   int *d_mask = ctx->mask.as<int>();
   uint64_t restarts = 0;
+  const bool verbose = std::getenv("PC_VERBOSE") != nullptr;  // host-side trace of the iteration (stderr)
   PC_CK(cudaMemcpyAsync(d_zero, zero.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
 
   std::vector<int> act;
@@ -372,6 +378,17 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
     PC_CK(cudaMemcpyAsync(h_norms.data(), norms, sizeof(double) * nb * m * 2, cudaMemcpyDeviceToHost, st));
     PC_CK(cudaStreamSynchronize(st));
     if ((rc = harvest_timing(ctx))) return rc;
+    if (verbose) {
+      for (int b : act) {
+        double mx = 0;
+        for (int j = 0; j < nbands; ++j) {
+          const double r = h_norms[((size_t)b * m + j) * 2], x = h_norms[((size_t)b * m + j) * 2 + 1];
+          mx = std::max(mx, r / (std::fabs(h_theta[(size_t)b * m + j]) * x));
+        }
+        std::fprintf(stderr, "[pc] it %d k %d gamma %.4g maxres %.3e theta0..%d = %.6g .. %.6g\n", it, b, gam[b], mx,
+                     m - 1, h_theta[(size_t)b * m], h_theta[(size_t)b * m + m - 1]);
+      }
+    }
     std::vector<int> conv;
     for (int b : act) {
       bool ok = true;
@@ -441,6 +458,13 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
       // would never leave; they are replaced by fresh counter-based columns before the re-solve
       std::vector<int> mask((size_t)nb * m);
       spurious_mask(redo, m, nbands, tol, h_theta, h_rn, mask);
+      if (verbose)
+        for (int b : redo) {
+          std::fprintf(stderr, "[pc] it %d k %d doubling -> gamma %.4g, replaced columns:", it, b, gam[b]);
+          for (int j = 0; j < m; ++j)
+            if (mask[(size_t)b * m + j]) std::fprintf(stderr, " %d", j);
+          std::fprintf(stderr, "\n");
+        }
       PC_CK(cudaMemcpyAsync(d_mask, mask.data(), sizeof(int) * mask.size(), cudaMemcpyHostToDevice, st));
       ++restarts;
       RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, 0.0, [&] {

@@ -11,7 +11,8 @@
 // * The X-X block (X^H X, X^H AX) and the residual need FP64: the residual floor of a complex64 X is eps32 |Op| / lambda
 //   (about 1e-3 here), and the X-X block's rounding shifts the Ritz values by eps32 lambda.
 // Phase 1 (every k-point starts here): X and AX in complex64 as well, until the complex64 residual stops falling.
-// Phase 2: X, AX in FP64; X' = X C_X (FP64) + P' (complex64 correction); AX' by the FP64 stencil.
+// Phase 2: X, AX stored in FP64; X' = X C_X + P' (complex64 correction), AX' by the stencil and the X-X block, all
+// three in double-float arithmetic (mixed_df.cu) on the FP32 pipe.
 // Convergence and Algorithm 4.1 are decided in phase 2 only, on FP64 residuals and FP64 norms.
 #include <algorithm>
 #include <cmath>
@@ -47,7 +48,7 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
   PC_CK(ctx->rank.reserve(sizeof(int) * (size_t)nb * 2));
   PC_CK(ctx->flag.reserve(sizeof(int) * (size_t)nb));
   PC_CK(ctx->phase.reserve(sizeof(int) * (size_t)nb));
-  const size_t scr = std::max({gram_pair_scratch_bytes(nb, L, nmax), gram_pair_scratch_bytes(nb, L, m),
+  const size_t scr = std::max({gram_pair_scratch_bytes(nb, L, nmax), gram_df_scratch_bytes(nb, L, m),
                                gram_scratch_bytes(nb, L, m, 2 * m), residual_scratch_bytes(nb, L, m),
                                sizeof(double2) * (size_t)nb * 3 * m * 16, sizeof(double) * 3 * (size_t)nb * m * 64,
                                (size_t)16});
@@ -88,9 +89,9 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
     return run_stage(ctx, PC_STAGE_STENCIL, 1, 214.0 * nd * nbk * cols, 2.0 * Ld * 8.0 * nbk * cols + 12.0 * nd,
                      [&] { return launch_apply_op(ctx, nbk, cols, PC_C64, X, sx, Y, sy, d_act); });
   };
-  auto OP64 = [&](int nbk, const void *X, void *Y) {
+  auto OP64 = [&](int nbk, const void *X, void *Y) {  // FP64 block, double-float arithmetic
     return run_stage(ctx, PC_STAGE_STENCIL, 1, 214.0 * nd * nbk * m, 2.0 * Ld * 16.0 * nbk * m + 24.0 * nd,
-                     [&] { return launch_apply_op(ctx, nbk, m, PC_C128, X, sX, Y, sX, d_act); });
+                     [&] { return launch_apply_op_df(ctx, nbk, m, X, sX, Y, sX, d_act); });
   };
   auto DEFL = [&](int nbk, void *X, long sx, int dtype) {
     return run_stage(ctx, PC_STAGE_OTHER, 2, 4.0 * Ld * m * nbk, 2.0 * Ld * (dtype == PC_C64 ? 8.0 : 16.0) * m * nbk,
@@ -279,7 +280,7 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
       RUN(set_act(act2));
       const int n2 = (int)act2.size();
       RUN(run_stage(ctx, PC_STAGE_GRAM, 2, 8.0 * m * (m + 1) * Ld * n2, 2.0 * m * Ld * 16.0 * n2, [&] {
-        return launch_gram_pair(n2, L, m, PC_C128, X64[cur], AX64, sX, GX, HX, scratch, scr, st, d_act);
+        return launch_gram_df(n2, L, m, X64[cur], AX64, sX, GX, HX, scratch, scr, st, d_act);
       }));
       RUN(set_act(act));
     }
@@ -306,8 +307,8 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
       RUN(set_act(act2));
       const int n2 = (int)act2.size();
       RUN(run_stage(ctx, PC_STAGE_UPDATE, 1, 8.0 * m * m * Ld * n2, (2.0 * 16.0 + 8.0) * m * Ld * n2, [&] {
-        return launch_block_update(n2, L, m, m, PC_C128, X64[cur], sX, coef, (long)nc * m, X64[nxt], sX, st, d_act,
-                                   F[nxt] + 2L * m * L, sF);
+        return launch_update_df(n2, L, m, m, X64[cur], sX, coef, (long)nc * m, X64[nxt], sX, F[nxt] + 2L * m * L,
+                                sF, st, d_act);
       }));
       if (any_zero) RUN(DEFL(n2, X64[nxt], sX, PC_C128));
       RUN(OP64(n2, X64[nxt], AX64));

@@ -57,9 +57,19 @@ __global__ void __launch_bounds__(256) op_kernel(const cplx<T> *__restrict__ X, 
   const int z0 = (t / tilesY) * TZ;
   const C *Xb = X + (long)b * sx + (long)j * 3 * n;
   C *Yb = Y + (long)b * sy + (long)j * 3 * n;
-  const KParam p = kp[b];
-  const T kh0 = (T)(0.5 * p.k[0]), kh1 = (T)(0.5 * p.k[1]), kh2 = (T)(0.5 * p.k[2]);
-  const T gam = (T)p.gamma;
+  const KParam &p = kp[b];
+  T kh0, kh1, kh2, gam;
+  if constexpr (std::is_same<T, float>::value) {
+    kh0 = p.khf[0];
+    kh1 = p.khf[1];
+    kh2 = p.khf[2];
+    gam = p.gammaf;
+  } else {
+    kh0 = 0.5 * p.k[0];
+    kh1 = 0.5 * p.k[1];
+    kh2 = 0.5 * p.k[2];
+    gam = p.gamma;
+  }
 
   for (int i = threadIdx.x; i < 3 * VZ * VY * VX; i += blockDim.x) {
     int lx = i % VX, r = i / VX;
