@@ -198,6 +198,16 @@ def kernel_case(args):
     elif args.kernel_case.startswith("precond"):
         Y = torch.empty_like(X)
         run = lambda: solver.apply_precond(kp, gam, X, out=Y)
+    elif args.kernel_case == "rr":
+        # 40 pencils of size 48 (3 x 16 columns) like one solver iteration: G = S^H S, H = S^H A S
+        gr = np.random.default_rng(1)
+        Sm = gr.standard_normal((40, 300, 48)) + 1j * gr.standard_normal((40, 300, 48))
+        lam = np.linspace(1.0, 1e3, 300)
+        Gm = np.einsum("bli,blj->bij", Sm.conj(), Sm)
+        Hm = np.einsum("bli,l,blj->bij", Sm.conj(), lam, Sm)
+        Gt = torch.from_numpy(Gm).cuda()
+        Ht = torch.from_numpy(Hm).cuda()
+        run = lambda: pc.rayleigh_ritz(Gt, Ht, 16)
     elif args.kernel_case.startswith("gram"):
         S = X.reshape(nb, m, L)
         AS = S.clone()
@@ -233,7 +243,7 @@ def main():
                          "are split across ranks")
     ap.add_argument("--ref-iters", type=int, default=12)
     ap.add_argument("--kernel-case", default=None,
-                    choices=["stencil64", "stencil32", "precond64", "precond32", "gram64", "gram32"],
+                    choices=["stencil64", "stencil32", "precond64", "precond32", "gram64", "gram32", "rr"],
                     help="run one hot kernel alone on a small batch (profiling) instead of the benchmark")
     args = ap.parse_args()
     if args.kernel_case:

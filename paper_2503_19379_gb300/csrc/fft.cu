@@ -8,10 +8,10 @@
 //
 // Passes (each a read and a write of the block):
 //   1. forward FFT along x (decimation in frequency: natural order in, bit-reversed mode order out)
-//   2. forward FFT along y (same)
+//   2. forward FFT along y (same); 1 and 2 run as one plane kernel when an N x N plane fits in shared memory
 //   3. along z, for all three components of a column at once: forward DIF FFT, the 3x3 symbol inverse at the mode
 //      (bitrev x, bitrev y, bitrev z) times 1/N^3, inverse FFT (decimation in time: bit-reversed in, natural out)
-//   4. inverse FFT along y (DIT), 5. inverse FFT along x (DIT).
+//   4. inverse FFT along y (DIT), 5. inverse FFT along x (DIT); again one plane kernel when the plane fits.
 // The frequency data never needs reordering: the DIT inverse consumes the DIF output order directly.
 // Each line is transformed in shared memory with radix-2 butterflies; twiddles exp(-2 pi i t / N) come from a
 // table computed once on the host.
@@ -119,6 +119,35 @@ __global__ void __launch_bounds__(256) fft_y_kernel(const cplx<T> *__restrict__ 
   }
 }
 
+// Both in-plane transforms of one (component, z) plane held in shared memory: forward = x then y (DIF), inverse =
+// y then x (DIT). grid (3N, m, nb). Replaces the separate x and y passes when N^2 elements fit.
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(512) fft_xy_kernel(const cplx<T> *__restrict__ in, long si, cplx<T> *__restrict__ out,
+                                                     long so, const cplx<T> *__restrict__ tw, const int *act,
+                                                     int logN) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = 1 << logN;
+  C *s_tw = reinterpret_cast<C *>(smem_raw);
+  C *a = s_tw + N / 2;  // [y][x]
+  const long n = 1L << (3 * logN);
+  const int b = act ? act[blockIdx.z] : (int)blockIdx.z;
+  const long off = (long)blockIdx.y * 3 * n + (long)blockIdx.x * N * N;  // plane = comp * N + z
+  const C *src = in + (long)b * si + off;
+  C *dst = out + (long)b * so + off;
+  load_tw(s_tw, tw, N / 2);
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) a[i] = src[i];
+  __syncthreads();
+  if (FWD) {
+    fft_lines<C, true>(a, N, N, 0, N, 1, logN, s_tw);        // rows (x)
+    fft_lines<C, true, true>(a, N, N, 0, 1, N, logN, s_tw);  // columns (y), line-major
+  } else {
+    fft_lines<C, false, true>(a, N, N, 0, 1, N, logN, s_tw);
+    fft_lines<C, false>(a, N, N, 0, N, 1, logN, s_tw);
+  }
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) dst[i] = a[i];
+}
+
 // Pass along z with the symbol: all 3 components of U contiguous x values at one y. grid (N*(N/U), m, nb).
 template <typename T>
 __global__ void __launch_bounds__(256) fft_z_symbol_kernel(const cplx<T> *__restrict__ in, long si,
@@ -209,18 +238,37 @@ static int launch_precond_t(pc_ctx *ctx, int nb, int m, const void *R, long sr, 
   const C *Rc = static_cast<const C *>(R);
   C *Wc = static_cast<C *>(W);
   const unsigned gx = (unsigned)(3 * N * N / Rr), gy = (unsigned)(3 * N * (N / Uy)), gz = (unsigned)(N * (N / Uz));
-  fft_x_kernel<T, true><<<dim3(gx, m, nb), 256, sx, ctx->stream>>>(Rc, sr, Wc, sw, tw, act, logN, Rr);
-  PC_CK_LAUNCH();
-  fft_y_kernel<T, true><<<dim3(gy, m, nb), 256, sy, ctx->stream>>>(Wc, sw, Wc, sw, tw, act, logN, Uy);
-  PC_CK_LAUNCH();
+  const size_t sxy = tw_b + sizeof(C) * (size_t)N * N;
+  const bool plane = sxy <= 200 * 1024;  // both in-plane transforms in one pass
+  static bool configured_xy = false;
+  if (plane && !configured_xy) {
+    PC_CK(cudaFuncSetAttribute(fft_xy_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    PC_CK(cudaFuncSetAttribute(fft_xy_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    configured_xy = true;
+  }
+  const int txy = N * N >= 4096 ? 512 : 256;
+  if (plane) {
+    fft_xy_kernel<T, true><<<dim3(3 * N, m, nb), txy, sxy, ctx->stream>>>(Rc, sr, Wc, sw, tw, act, logN);
+    PC_CK_LAUNCH();
+  } else {
+    fft_x_kernel<T, true><<<dim3(gx, m, nb), 256, sx, ctx->stream>>>(Rc, sr, Wc, sw, tw, act, logN, Rr);
+    PC_CK_LAUNCH();
+    fft_y_kernel<T, true><<<dim3(gy, m, nb), 256, sy, ctx->stream>>>(Wc, sw, Wc, sw, tw, act, logN, Uy);
+    PC_CK_LAUNCH();
+  }
   fft_z_symbol_kernel<T><<<dim3(gz, m, nb), 256, sz, ctx->stream>>>(Wc, sw, Wc, sw, tw, ctx->symd.as<double2>(),
                                                                     ctx->kparam.as<KParam>(), act, logN, Uz,
                                                                     ctx->opts.precond == PC_PRECOND_LAPLACIAN);
   PC_CK_LAUNCH();
-  fft_y_kernel<T, false><<<dim3(gy, m, nb), 256, sy, ctx->stream>>>(Wc, sw, Wc, sw, tw, act, logN, Uy);
-  PC_CK_LAUNCH();
-  fft_x_kernel<T, false><<<dim3(gx, m, nb), 256, sx, ctx->stream>>>(Wc, sw, Wc, sw, tw, act, logN, Rr);
-  PC_CK_LAUNCH();
+  if (plane) {
+    fft_xy_kernel<T, false><<<dim3(3 * N, m, nb), txy, sxy, ctx->stream>>>(Wc, sw, Wc, sw, tw, act, logN);
+    PC_CK_LAUNCH();
+  } else {
+    fft_y_kernel<T, false><<<dim3(gy, m, nb), 256, sy, ctx->stream>>>(Wc, sw, Wc, sw, tw, act, logN, Uy);
+    PC_CK_LAUNCH();
+    fft_x_kernel<T, false><<<dim3(gx, m, nb), 256, sx, ctx->stream>>>(Wc, sw, Wc, sw, tw, act, logN, Rr);
+    PC_CK_LAUNCH();
+  }
   return PC_OK;
 }
 

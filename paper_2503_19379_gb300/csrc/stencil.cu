@@ -130,6 +130,138 @@ __global__ void __launch_bounds__(256) op_kernel(const cplx<T> *__restrict__ X, 
   }
 }
 
+// ------------------------------------------------------------------------------------------------ z-marching stencil
+// The same operator with a 2.5D blocking: a block owns a TX x TY column tile and walks ZC consecutive z planes. Per
+// plane z it loads v(z+1) (with a one-point x/y halo), forms e(z+1) = M0 A' v on the tile grown by one point in +x/+y
+// and c(z) = B v on the tile grown by one point in -x/-y, and writes y(z) = A e + gamma B' c from the two e planes
+// (z, z+1) and the two c planes (z-1, z) held in ring buffers. Halo work is (TX+1)(TY+1)/(TX TY) instead of the
+// (TX+1)(TY+1)(TZ+1)/(TX TY TZ) of the cube tile, and only 2+2+2 planes live in shared memory.
+template <typename T, int TX, int TY> constexpr size_t opz_smem_bytes() {
+  return sizeof(cplx<T>) * (size_t)(2 * 3 * (TY + 2) * (TX + 2) + 2 * 3 * (TY + 1) * (TX + 1) + 2 * (TY + 1) * (TX + 1));
+}
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) opz_kernel(const cplx<T> *__restrict__ X, long sx, cplx<T> *__restrict__ Y,
+                                                      long sy, const T *__restrict__ m0, const KParam *__restrict__ kp,
+                                                      const int *__restrict__ act, int logN, int ZC, T ih) {
+  using C = cplx<T>;
+  constexpr int VX = TX + 2, VY = TY + 2, VP = VX * VY;  // v plane: local (lx, ly) <-> global (x0 + lx - 1, ...)
+  constexpr int EX = TX + 1, EY = TY + 1, EP = EX * EY;  // e plane: global x0 + ex; c plane: global x0 + ex - 1
+  constexpr int NT = TX * TY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *vbuf = reinterpret_cast<C *>(smem_raw);  // [2][3][VP]
+  C *ebuf = vbuf + 2 * 3 * VP;                 // [2][3][EP]
+  C *cbuf = ebuf + 2 * 3 * EP;                 // [2][EP]
+  const int N = 1 << logN, mask = N - 1;
+  const long n = 1L << (3 * logN), plane = 1L << (2 * logN);
+  const int b = act ? act[blockIdx.z] : (int)blockIdx.z;
+  const int j = blockIdx.y;
+  const int tilesX = N / TX, tilesY = N / TY;
+  int t = blockIdx.x;
+  const int x0 = (t % tilesX) * TX;
+  t /= tilesX;
+  const int y0 = (t % tilesY) * TY;
+  const int zb = (t / tilesY) * ZC;
+  const C *Xb = X + (long)b * sx + (long)j * 3 * n;
+  C *Yb = Y + (long)b * sy + (long)j * 3 * n;
+  const KParam &p = kp[b];
+  T kh0, kh1, kh2, gam;
+  if constexpr (std::is_same<T, float>::value) {
+    kh0 = p.khf[0];
+    kh1 = p.khf[1];
+    kh2 = p.khf[2];
+    gam = p.gammaf;
+  } else {
+    kh0 = 0.5 * p.k[0];
+    kh1 = 0.5 * p.k[1];
+    kh2 = 0.5 * p.k[2];
+    gam = p.gamma;
+  }
+  const int tid = threadIdx.x;
+
+  auto load_v = [&](int slot, int z) {
+    const int gz = z & mask;
+    C *vs = vbuf + slot * 3 * VP;
+    for (int i = tid; i < 3 * VP; i += NT) {
+      const int comp = i / VP, r = i - comp * VP, ly = r / VX, lx = r - ly * VX;
+      const int gx = (x0 + lx - 1) & mask, gy = (y0 + ly - 1) & mask;
+      vs[i] = Xb[comp * n + gz * plane + ((long)gy << logN) + gx];
+    }
+  };
+  // e(z) from v(z) (slot sz) and v(z-1) (slot szm), on the tile grown by one in +x/+y
+  auto make_e = [&](int eslot, int z, int sz, int szm) {
+    const C *v0 = vbuf + sz * 3 * VP, *vm = vbuf + szm * 3 * VP;
+    C *es = ebuf + eslot * 3 * EP;
+    const int gz = z & mask;
+    for (int i = tid; i < EP; i += NT) {
+      const int ey = i / EX, ex = i - ey * EX;
+      const int o = (ey + 1) * VX + ex + 1;  // v local index of global (x0 + ex, y0 + ey)
+      const C v1 = v0[o], v2 = v0[VP + o], v3 = v0[2 * VP + o];
+      const C d3v2 = dbwd(vm[VP + o], v2, ih, kh2);
+      const C d2v3 = dbwd(v0[2 * VP + o - VX], v3, ih, kh1);
+      const C d3v1 = dbwd(vm[o], v1, ih, kh2);
+      const C d1v3 = dbwd(v0[2 * VP + o - 1], v3, ih, kh0);
+      const C d2v1 = dbwd(v0[o - VX], v1, ih, kh1);
+      const C d1v2 = dbwd(v0[VP + o - 1], v2, ih, kh0);
+      const long gi = gz * plane + ((long)((y0 + ey) & mask) << logN) + ((x0 + ex) & mask);
+      es[i] = cscale(csub(d3v2, d2v3), m0[gi]);
+      es[EP + i] = cscale(csub(d1v3, d3v1), m0[n + gi]);
+      es[2 * EP + i] = cscale(csub(d2v1, d1v2), m0[2 * n + gi]);
+    }
+  };
+  // c(z) from v(z) (slot sz) and v(z+1) (slot szp), on the tile grown by one in -x/-y
+  auto make_c = [&](int cslot, int sz, int szp) {
+    const C *v0 = vbuf + sz * 3 * VP, *vp = vbuf + szp * 3 * VP;
+    C *cs = cbuf + cslot * EP;
+    for (int i = tid; i < EP; i += NT) {
+      const int cy = i / EX, cx = i - cy * EX;
+      const int o = cy * VX + cx;  // v local index of global (x0 + cx - 1, y0 + cy - 1)
+      C cc = dfwd(v0[o], v0[o + 1], ih, kh0);
+      cc = cadd(cc, dfwd(v0[VP + o], v0[VP + o + VX], ih, kh1));
+      cc = cadd(cc, dfwd(v0[2 * VP + o], vp[2 * VP + o], ih, kh2));
+      cs[i] = cc;
+    }
+  };
+
+  // prologue: v(zb-1), v(zb) -> e(zb), c(zb-1)
+  load_v(0, zb - 1);
+  load_v(1, zb);
+  __syncthreads();
+  make_e(0, zb, 1, 0);
+  make_c(0, 0, 1);
+  int sv = 1, se = 0, sc = 0;  // slots holding v(z), e(z), c(z-1)
+  for (int z = zb; z < zb + ZC; ++z) {
+    __syncthreads();                     // previous y(z-1) done reading; v(z-1) slot free
+    load_v(1 - sv, z + 1);               // v(z+1) into the free slot
+    __syncthreads();
+    make_e(1 - se, z + 1, 1 - sv, sv);   // e(z+1)
+    make_c(1 - sc, sv, 1 - sv);          // c(z)
+    __syncthreads();
+    {
+      const C *e0 = ebuf + se * 3 * EP, *e1p = ebuf + (1 - se) * 3 * EP;  // e(z), e(z+1)
+      const C *cm = cbuf + sc * EP, *c0p = cbuf + (1 - sc) * EP;          // c(z-1), c(z)
+      const int ly = tid / TX, lx = tid - ly * TX;
+      const int eo = ly * EX + lx;             // e index of (x0+lx, y0+ly)
+      const int co = (ly + 1) * EX + lx + 1;   // c index of (x0+lx, y0+ly)
+      const C c0 = c0p[co];
+      const C e1 = e0[eo], e2 = e0[EP + eo], e3 = e0[2 * EP + eo];
+      C y1 = csub(dfwd(e3, e0[2 * EP + eo + EX], ih, kh1), dfwd(e2, e1p[EP + eo], ih, kh2));
+      y1 = cadd(y1, cscale(dbwd(c0p[co - 1], c0, ih, kh0), gam));
+      C y2 = csub(dfwd(e1, e1p[eo], ih, kh2), dfwd(e3, e0[2 * EP + eo + 1], ih, kh0));
+      y2 = cadd(y2, cscale(dbwd(c0p[co - EX], c0, ih, kh1), gam));
+      C y3 = csub(dfwd(e2, e0[EP + eo + 1], ih, kh0), dfwd(e1, e0[eo + EX], ih, kh1));
+      y3 = cadd(y3, cscale(dbwd(cm[co], c0, ih, kh2), gam));
+      const long gi = (long)z * plane + ((long)(y0 + ly) << logN) + x0 + lx;
+      Yb[gi] = y1;
+      Yb[n + gi] = y2;
+      Yb[2 * n + gi] = y3;
+    }
+    sv = 1 - sv;
+    se = 1 - se;
+    sc = 1 - sc;
+  }
+}
+
 // ------------------------------------------------------------------------------------------------ half applies
 // A' x at edge point r and B x at cell point r, read straight from global memory (not on the per-iteration path).
 struct HalfOut {
@@ -243,10 +375,33 @@ static int launch_op_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, void 
   return PC_OK;
 }
 
+template <typename T, int TX, int TY>
+static int launch_opz_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act) {
+  constexpr size_t smem = opz_smem_bytes<T, TX, TY>();
+  static bool configured = false;
+  if (!configured) {
+    PC_CK(cudaFuncSetAttribute(opz_kernel<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = true;
+  }
+  const int N = ctx->N;
+  // z chunk: enough blocks to fill the GPU several times over, at least 4 planes per chunk
+  const long tiles = (long)(N / TX) * (N / TY) * m * nb;
+  int ZC = N;
+  while (ZC > 4 && tiles * (N / ZC) < 4L * 152 * 4) ZC >>= 1;
+  dim3 grid((N / TX) * (N / TY) * (N / ZC), m, nb);
+  const T *m0 = std::is_same<T, double>::value ? ctx->m0d.as<T>() : ctx->m0f.as<T>();
+  opz_kernel<T, TX, TY><<<grid, TX * TY, smem, ctx->stream>>>(static_cast<const cplx<T> *>(X), sx,
+                                                                static_cast<cplx<T> *>(Y), sy, m0,
+                                                                ctx->kparam.as<KParam>(), act, ctx->logN, ZC, (T)ctx->N);
+  PC_CK_LAUNCH();
+  return PC_OK;
+}
+
 int launch_apply_op(pc_ctx *ctx, int nb, int m, int dtype, const void *X, long sx, void *Y, long sy,
                     const int *act) {
   if (nb == 0 || m == 0) return PC_OK;
   const int N = ctx->N;
+  if (dtype == PC_C64 && N >= 32) return launch_opz_t<float, 32, 8>(ctx, nb, m, X, sx, Y, sy, act);
   if (dtype == PC_C128) {
     if (N >= 32) return launch_op_t<double, 32, 4, 4>(ctx, nb, m, X, sx, Y, sy, act);
     if (N == 16) return launch_op_t<double, 16, 4, 4>(ctx, nb, m, X, sx, Y, sy, act);
