@@ -47,6 +47,7 @@ extern "C" {
 
 #define PC_C128 0
 #define PC_C64 1
+#define PC_C128_DF 2 /* complex128 storage, double-float (FP32-pair) arithmetic: ~2^-44 relative rounding, FP32 pipe */
 
 /* Preconditioner variants (Section 5.1 and Corollary discrete_vec_lap_mat). */
 #define PC_PRECOND_GAMMA 0     /* P = A A' + gamma B'B, eq. penalised_marix (default) */
@@ -148,7 +149,8 @@ int pc_eps_spheres(int N, int nsph, const double *spheres, double eps_bg, double
 
 /* a1: Y = Op X = A M0 A' X + gamma B'B X for nb k-points x m fields (eq. Ker_comp; stencils of Section 4.1.2).
  *   kpts: host [nb][3] (used as given, no zone reduction); gammas: host [nb].
- *   X, Y: device blocks, dtype PC_C128 or PC_C64, batch stride m*3N^3 elements. X and Y must not overlap. */
+ *   X, Y: device blocks, dtype PC_C128, PC_C64 or PC_C128_DF (complex128 data, double-float arithmetic), batch
+ *         stride m*3N^3 elements. X and Y must not overlap. */
 int pc_apply_op(pc_ctx *ctx, int nb, const double *kpts, const double *gammas, int m, int dtype, const void *X,
                 void *Y);
 

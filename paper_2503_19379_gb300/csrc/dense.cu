@@ -74,6 +74,67 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const cplx<T> *__rest
     }
 }
 
+// General p x q product with the thread tile sized to the output: block (ceil(q/R), ceil(p/R)), R x R per thread.
+template <typename T, int R>
+__global__ void __launch_bounds__(256) gram_tile_partial_kernel(const cplx<T> *__restrict__ A, long sa,
+                                                               const cplx<T> *__restrict__ B, long sb, long L, int p,
+                                                               int q, long chunk, double2 *__restrict__ part,
+                                                               const int *__restrict__ act) {
+  using C = cplx<T>;
+  __shared__ C As[64][GRAM_TL + 1];
+  __shared__ C Bs[64][GRAM_TL + 1];
+  const int bi = blockIdx.z;
+  const int b = act ? act[bi] : bi;
+  const C *Ab = A + (long)b * sa;
+  const C *Bb = B + (long)b * sb;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * blockDim.x + tx, nthr = blockDim.x * blockDim.y;
+  C acc[R][R];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < R; ++c) acc[r][c] = cmake<C>((T)0, (T)0);
+  const long beg = (long)blockIdx.x * chunk, end = min(L, beg + chunk);
+  const int pq = max(p, q);
+  for (long l0 = beg; l0 < end; l0 += GRAM_TL) {
+    for (int i = tid; i < pq * GRAM_TL; i += nthr) {
+      const int col = i / GRAM_TL, t = i - col * GRAM_TL;
+      const long l = l0 + t;
+      C va = cmake<C>((T)0, (T)0), vb = va;
+      if (l < end) {
+        if (col < p) va = Ab[(long)col * L + l];
+        if (col < q) vb = Bb[(long)col * L + l];
+      }
+      As[col][t] = va;
+      Bs[col][t] = vb;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int t = 0; t < GRAM_TL; ++t) {
+      C a[R], bv[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) a[r] = As[min(ty * R + r, pq - 1)][t];
+#pragma unroll
+      for (int c = 0; c < R; ++c) bv[c] = Bs[min(tx * R + c, pq - 1)][t];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+          acc[r][c].x = fma(a[r].x, bv[c].x, fma(a[r].y, bv[c].y, acc[r][c].x));
+          acc[r][c].y = fma(a[r].x, bv[c].y, fma(-a[r].y, bv[c].x, acc[r][c].y));
+        }
+    }
+    __syncthreads();
+  }
+  double2 *o = part + ((long)bi * gridDim.x + blockIdx.x) * p * q;
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+      const int i = ty * R + r, j = tx * R + c;
+      if (i < p && j < q) o[i * q + j] = cmake<double2>((double)acc[r][c].x, (double)acc[r][c].y);
+    }
+}
+
 __global__ void gram_reduce_kernel(const double2 *__restrict__ part, int nchunk, int p, int q,
                                    const int *__restrict__ act, double2 *__restrict__ G) {
   const int bi = blockIdx.x;
@@ -106,7 +167,15 @@ int launch_gram(int nb, long L, int p, int q, int dtype, const void *A, long sa,
   long chunk = (L + nchunk - 1) / nchunk;
   chunk = (chunk + GRAM_TL - 1) / GRAM_TL * GRAM_TL;
   double2 *part = static_cast<double2 *>(scratch);
-  if (dtype == PC_C128)
+  const int R = std::max(p, q) <= 32 ? 2 : 4;
+  const dim3 blk((q + R - 1) / R, (p + R - 1) / R);
+  if (R == 2 && dtype == PC_C128)
+    gram_tile_partial_kernel<double, 2><<<dim3(nchunk, 1, nb), blk, 0, st>>>(
+        static_cast<const double2 *>(A), sa, static_cast<const double2 *>(B), sb, L, p, q, chunk, part, act);
+  else if (R == 2)
+    gram_tile_partial_kernel<float, 2><<<dim3(nchunk, 1, nb), blk, 0, st>>>(
+        static_cast<const float2 *>(A), sa, static_cast<const float2 *>(B), sb, L, p, q, chunk, part, act);
+  else if (dtype == PC_C128)
     gram_partial_kernel<double><<<dim3(nchunk, 1, nb), 256, 0, st>>>(
         static_cast<const double2 *>(A), sa, static_cast<const double2 *>(B), sb, L, p, q, chunk, part, act);
   else

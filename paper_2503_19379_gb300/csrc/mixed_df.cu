@@ -133,10 +133,145 @@ static int launch_op_df_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, vo
   return PC_OK;
 }
 
+// z-marching version (the blocking of opz_kernel in stencil.cu): a TX x TY column tile walks ZC planes with ring
+// buffers of v (2 planes), e = M0 A' v (2 planes) and c = B v (2 planes).
+template <int TX, int TY> constexpr size_t opz_df_smem_bytes() {
+  return sizeof(cdf) * (size_t)(2 * 3 * (TY + 2) * (TX + 2) + 2 * 3 * (TY + 1) * (TX + 1) + 2 * (TY + 1) * (TX + 1));
+}
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) opz_df_kernel(const double2 *__restrict__ X, long sx,
+                                                         double2 *__restrict__ Y, long sy,
+                                                         const double *__restrict__ m0,
+                                                         const KParam *__restrict__ kp, const int *__restrict__ act,
+                                                         int logN, int ZC) {
+  constexpr int VX = TX + 2, VY = TY + 2, VP = VX * VY;
+  constexpr int EX = TX + 1, EY = TY + 1, EP = EX * EY;
+  constexpr int NT = TX * TY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cdf *vbuf = reinterpret_cast<cdf *>(smem_raw);
+  cdf *ebuf = vbuf + 2 * 3 * VP;
+  cdf *cbuf = ebuf + 2 * 3 * EP;
+  const int N = 1 << logN, mask = N - 1;
+  const long n = 1L << (3 * logN), plane = 1L << (2 * logN);
+  const int b = act ? act[blockIdx.z] : (int)blockIdx.z;
+  const int j = blockIdx.y;
+  const int tilesX = N / TX, tilesY = N / TY;
+  int t = blockIdx.x;
+  const int x0 = (t % tilesX) * TX;
+  t /= tilesX;
+  const int y0 = (t % tilesY) * TY;
+  const int zb = (t / tilesY) * ZC;
+  const double2 *Xb = X + (long)b * sx + (long)j * 3 * n;
+  double2 *Yb = Y + (long)b * sy + (long)j * 3 * n;
+  const KParam &p = kp[b];
+  const df kh0 = df_from(0.5 * p.k[0]), kh1 = df_from(0.5 * p.k[1]), kh2 = df_from(0.5 * p.k[2]);
+  const df gam = df_from(p.gamma);
+  const float ih = (float)N;
+  const int tid = threadIdx.x;
+  auto load_v = [&](int slot, int z) {
+    const int gz = z & mask;
+    cdf *vs = vbuf + slot * 3 * VP;
+    for (int i = tid; i < 3 * VP; i += NT) {
+      const int comp = i / VP, r = i - comp * VP, ly = r / VX, lx = r - ly * VX;
+      const int gx = (x0 + lx - 1) & mask, gy = (y0 + ly - 1) & mask;
+      vs[i] = cdf_from(Xb[comp * n + gz * plane + ((long)gy << logN) + gx]);
+    }
+  };
+  auto make_e = [&](int eslot, int z, int sz, int szm) {
+    const cdf *v0 = vbuf + sz * 3 * VP, *vm = vbuf + szm * 3 * VP;
+    cdf *es = ebuf + eslot * 3 * EP;
+    const int gz = z & mask;
+    for (int i = tid; i < EP; i += NT) {
+      const int ey = i / EX, ex = i - ey * EX;
+      const int o = (ey + 1) * VX + ex + 1;
+      const cdf v1 = v0[o], v2 = v0[VP + o], v3 = v0[2 * VP + o];
+      const cdf d3v2 = dbwd_df(vm[VP + o], v2, ih, kh2);
+      const cdf d2v3 = dbwd_df(v0[2 * VP + o - VX], v3, ih, kh1);
+      const cdf d3v1 = dbwd_df(vm[o], v1, ih, kh2);
+      const cdf d1v3 = dbwd_df(v0[2 * VP + o - 1], v3, ih, kh0);
+      const cdf d2v1 = dbwd_df(v0[o - VX], v1, ih, kh1);
+      const cdf d1v2 = dbwd_df(v0[VP + o - 1], v2, ih, kh0);
+      const long gi = gz * plane + ((long)((y0 + ey) & mask) << logN) + ((x0 + ex) & mask);
+      es[i] = cdf_scale(cdf_sub(d3v2, d2v3), df_from(m0[gi]));
+      es[EP + i] = cdf_scale(cdf_sub(d1v3, d3v1), df_from(m0[n + gi]));
+      es[2 * EP + i] = cdf_scale(cdf_sub(d2v1, d1v2), df_from(m0[2 * n + gi]));
+    }
+  };
+  auto make_c = [&](int cslot, int sz, int szp) {
+    const cdf *v0 = vbuf + sz * 3 * VP, *vp = vbuf + szp * 3 * VP;
+    cdf *cs = cbuf + cslot * EP;
+    for (int i = tid; i < EP; i += NT) {
+      const int cy = i / EX, cx = i - cy * EX;
+      const int o = cy * VX + cx;
+      cdf cc = dfwd_df(v0[o], v0[o + 1], ih, kh0);
+      cc = cdf_add(cc, dfwd_df(v0[VP + o], v0[VP + o + VX], ih, kh1));
+      cc = cdf_add(cc, dfwd_df(v0[2 * VP + o], vp[2 * VP + o], ih, kh2));
+      cs[i] = cc;
+    }
+  };
+  load_v(0, zb - 1);
+  load_v(1, zb);
+  __syncthreads();
+  make_e(0, zb, 1, 0);
+  make_c(0, 0, 1);
+  int sv = 1, se = 0, sc = 0;
+  for (int z = zb; z < zb + ZC; ++z) {
+    __syncthreads();
+    load_v(1 - sv, z + 1);
+    __syncthreads();
+    make_e(1 - se, z + 1, 1 - sv, sv);
+    make_c(1 - sc, sv, 1 - sv);
+    __syncthreads();
+    {
+      const cdf *e0 = ebuf + se * 3 * EP, *e1p = ebuf + (1 - se) * 3 * EP;
+      const cdf *cm = cbuf + sc * EP, *c0p = cbuf + (1 - sc) * EP;
+      const int ly = tid / TX, lx = tid - ly * TX;
+      const int eo = ly * EX + lx;
+      const int co = (ly + 1) * EX + lx + 1;
+      const cdf c0 = c0p[co];
+      const cdf e1 = e0[eo], e2 = e0[EP + eo], e3 = e0[2 * EP + eo];
+      cdf y1 = cdf_sub(dfwd_df(e3, e0[2 * EP + eo + EX], ih, kh1), dfwd_df(e2, e1p[EP + eo], ih, kh2));
+      y1 = cdf_add(y1, cdf_scale(dbwd_df(c0p[co - 1], c0, ih, kh0), gam));
+      cdf y2 = cdf_sub(dfwd_df(e1, e1p[eo], ih, kh2), dfwd_df(e3, e0[2 * EP + eo + 1], ih, kh0));
+      y2 = cdf_add(y2, cdf_scale(dbwd_df(c0p[co - EX], c0, ih, kh1), gam));
+      cdf y3 = cdf_sub(dfwd_df(e2, e0[EP + eo + 1], ih, kh0), dfwd_df(e1, e0[eo + EX], ih, kh1));
+      y3 = cdf_add(y3, cdf_scale(dbwd_df(cm[co], c0, ih, kh2), gam));
+      const long gi = (long)z * plane + ((long)(y0 + ly) << logN) + x0 + lx;
+      Yb[gi] = cdf_to(y1);
+      Yb[n + gi] = cdf_to(y2);
+      Yb[2 * n + gi] = cdf_to(y3);
+    }
+    sv = 1 - sv;
+    se = 1 - se;
+    sc = 1 - sc;
+  }
+}
+
+template <int TX, int TY>
+static int launch_opz_df_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act) {
+  constexpr size_t smem = opz_df_smem_bytes<TX, TY>();
+  static bool configured = false;
+  if (!configured) {
+    PC_CK(cudaFuncSetAttribute(opz_df_kernel<TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = true;
+  }
+  const int N = ctx->N;
+  const long tiles = (long)(N / TX) * (N / TY) * m * nb;
+  int ZC = N;
+  while (ZC > 4 && tiles * (N / ZC) < 4L * 152 * 4) ZC >>= 1;
+  dim3 grid((N / TX) * (N / TY) * (N / ZC), m, nb);
+  opz_df_kernel<TX, TY><<<grid, TX * TY, smem, ctx->stream>>>(static_cast<const double2 *>(X), sx,
+                                                               static_cast<double2 *>(Y), sy, ctx->m0d.as<double>(),
+                                                               ctx->kparam.as<KParam>(), act, ctx->logN, ZC);
+  PC_CK_LAUNCH();
+  return PC_OK;
+}
+
 int launch_apply_op_df(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act) {
   if (nb == 0 || m == 0) return PC_OK;
   const int N = ctx->N;
-  if (N >= 32) return launch_op_df_t<32, 4, 4>(ctx, nb, m, X, sx, Y, sy, act);
+  if (N >= 32) return launch_opz_df_t<32, 8>(ctx, nb, m, X, sx, Y, sy, act);
   if (N == 16) return launch_op_df_t<16, 4, 4>(ctx, nb, m, X, sx, Y, sy, act);
   return launch_op_df_t<8, 4, 4>(ctx, nb, m, X, sx, Y, sy, act);
 }
@@ -199,7 +334,7 @@ int launch_update_df(int nb, long L, int p, int q, const void *X, long sx, const
 constexpr int DF_TL = 16;
 
 template <int R>
-__global__ void __launch_bounds__(256) gram_df_kernel(const double2 *__restrict__ S, const double2 *__restrict__ AS,
+__global__ void __launch_bounds__(1024) gram_df_kernel(const double2 *__restrict__ S, const double2 *__restrict__ AS,
                                                      long ss, long L, int p, long chunk,
                                                      double2 *__restrict__ partG, double2 *__restrict__ partH,
                                                      const int *__restrict__ act) {
@@ -290,8 +425,8 @@ __global__ void gram_df_reduce_kernel(const double2 *__restrict__ partG, const d
 }
 
 static int df_chunks(int nb, long L) {
-  long want = std::max<long>(1, (4L * 152 + nb - 1) / std::max(nb, 1));
-  return (int)std::min<long>(std::min<long>(want, std::max<long>(1, L / 1024)), 128);
+  long want = std::max<long>(1, (8L * 152 + nb - 1) / std::max(nb, 1));
+  return (int)std::min<long>(std::min<long>(want, std::max<long>(1, L / 512)), 128);
 }
 
 size_t gram_df_scratch_bytes(int nb, long L, int p) {
@@ -310,13 +445,9 @@ int launch_gram_df(int nb, long L, int p, const void *S, const void *AS, long ss
   chunk = (chunk + DF_TL - 1) / DF_TL * DF_TL;
   double2 *pG = static_cast<double2 *>(scratch), *pH = pG + (size_t)nb * nchunk * p * p;
   const double2 *Sd = static_cast<const double2 *>(S), *Ad = static_cast<const double2 *>(AS);
-  if (p <= 16) {
-    const int TD = (p + 1) / 2;
-    gram_df_kernel<2><<<dim3(nchunk, 1, nb), dim3(TD, TD), 0, st>>>(Sd, Ad, ss, L, p, chunk, pG, pH, act);
-  } else {
-    const int TD = (p + 2) / 3;
-    gram_df_kernel<3><<<dim3(nchunk, 1, nb), dim3(TD, TD), 0, st>>>(Sd, Ad, ss, L, p, chunk, pG, pH, act);
-  }
+  // one output pair per thread (p x p threads, the upper triangle active): the double-float arithmetic is the
+  // bottleneck, so parallelism matters more than register reuse
+  gram_df_kernel<1><<<dim3(nchunk, 1, nb), dim3(p, p), 0, st>>>(Sd, Ad, ss, L, p, chunk, pG, pH, act);
   PC_CK_LAUNCH();
   gram_df_reduce_kernel<<<nb, 256, 0, st>>>(pG, pH, nchunk, p, act, static_cast<double2 *>(G),
                                             static_cast<double2 *>(H));

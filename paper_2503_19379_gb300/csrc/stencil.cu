@@ -436,10 +436,11 @@ extern "C" int pc_apply_op(pc_ctx *ctx, int nb, const double *kpts, const double
                            const void *X, void *Y) {
   PC_REQUIRE(ctx && kpts && gammas && X && Y, "pc_apply_op: null argument");
   PC_REQUIRE(nb >= 0 && m >= 0, "pc_apply_op: negative size");
-  PC_REQUIRE(dtype == PC_C128 || dtype == PC_C64, "pc_apply_op: bad dtype %d", dtype);
+  PC_REQUIRE(dtype == PC_C128 || dtype == PC_C64 || dtype == PC_C128_DF, "pc_apply_op: bad dtype %d", dtype);
   int rc = upload_kpoints(ctx, nb, kpts, gammas);
   if (rc) return rc;
   const long blk = (long)m * 3 * ctx->n;
+  if (dtype == PC_C128_DF) return launch_apply_op_df(ctx, nb, m, X, blk, Y, blk, nullptr);
   return launch_apply_op(ctx, nb, m, dtype, X, blk, Y, blk, nullptr);
 }
 

@@ -13,7 +13,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "libpc.so")
 
-PC_C128, PC_C64 = 0, 1
+PC_C128, PC_C64, PC_C128_DF = 0, 1, 2
 PC_PRECOND_GAMMA, PC_PRECOND_LAPLACIAN = 0, 1
 PC_PREC_FP64, PC_PREC_MIXED = 0, 1
 PC_NOT_CONVERGED, PC_SPURIOUS = 1, 2
@@ -198,13 +198,18 @@ class Solver:
                 for name, a in zip(STAGES, arr)}
 
     # ---- step-level kernels (device tensors shaped (nb, m, 3, N, N, N))
-    def apply_op(self, kpts, gammas, X):
+    def apply_op(self, kpts, gammas, X, double_float=False):
+        """Y = Op X; double_float=True evaluates a complex128 block in double-float arithmetic (PC_C128_DF)."""
         k = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
         g = np.ascontiguousarray(np.asarray(gammas, dtype=np.float64).reshape(-1))
         Y = _torch().empty_like(X)
         nb, m = X.shape[0], X.shape[1]
-        _check(lib().pc_apply_op(self._h, nb, _dptr(k), _dptr(g), m, _dtype_code(X), _dev(X), _dev(Y)),
-               "pc_apply_op")
+        code = _dtype_code(X)
+        if double_float:
+            if code != PC_C128:
+                raise PCError("double-float evaluation needs a complex128 block")
+            code = PC_C128_DF
+        _check(lib().pc_apply_op(self._h, nb, _dptr(k), _dptr(g), m, code, _dev(X), _dev(Y)), "pc_apply_op")
         return Y
 
     def apply_half(self, kpts, X):

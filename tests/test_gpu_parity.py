@@ -64,7 +64,24 @@ def test_apply_op_fp64(pcmod, N):
         assert np.max(np.abs(Y[b] - ref)) <= 1e-13 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("N", [8, 32])
+@pytest.mark.parametrize("N", [8, 16, 32, 64])
+def test_apply_op_double_float(pcmod, N):
+    """complex128 block evaluated in double-float arithmetic (the phase-2 stencil of the mixed solve): rounding of
+    ~2^-44 per operation, so 1e-11 relative to the largest output."""
+    S, m0 = make_solver(pcmod, N)
+    g = np.random.default_rng(N + 5)
+    nb, m = 2, 3
+    kpts = g.uniform(-3.5, 3.5, (nb, 3))
+    gammas = np.array([2.0 * N, 7.25])
+    X = rand_block(N + 3, (nb, m, 3 * N ** 3))
+    Y = S.apply_op(kpts, gammas, to_dev(X.reshape(nb, m, 3, N, N, N)), double_float=True).cpu().numpy()
+    Y = Y.reshape(nb, m, -1)
+    for b in range(nb):
+        ref = (mfd.compensated_operator(N, kpts[b], 1.0 / N, m0, gammas[b]) @ X[b].T).T
+        assert np.max(np.abs(Y[b] - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("N", [8, 16, 32, 64])
 def test_apply_op_fp32(pcmod, N):
     S, m0 = make_solver(pcmod, N)
     kpts = np.array([[0.4, -1.3, 2.2]])
