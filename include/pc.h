@@ -170,15 +170,17 @@ int pc_apply_precond(pc_ctx *ctx, int nb, const double *kpts, const double *gamm
                      const void *R, void *W);
 
 /* a3: G_b = A_b^H B_b for tall-skinny blocks (L rows; p and q columns, column stride L; batch strides sa, sb in
- * elements). G: device complex128 [nb][p][q] row-major. p, q <= 64. dtype applies to A and B; accumulation is
- * FP64. */
+ * elements). G: device complex128 [nb][p][q] row-major. p, q <= 64. dtype applies to A and B. PC_C128: FP64
+ * products and sums. PC_C64: FP32 products and partial sums over chunks of the rows, chunks added in FP64; where L
+ * is a multiple of 16 and the panels are 16-byte aligned this runs on the tensor cores (TF32 operands split into
+ * hi + lo, accumulators drained every 64 rows), otherwise on the CUDA cores. */
 int pc_gram(int nb, long L, int p, int q, int dtype, const void *A, long sa, const void *B, long sb, void *G,
             void *stream);
 
 /* a3: the Rayleigh-Ritz pencil of one panel: G_b = S_b^H S_b and H_b = S_b^H AS_b, with S_b and AS_b of p columns
  * (length L, column stride L, the same batch stride ss for both). Op is Hermitian, so both outputs are Hermitian:
  * only the upper triangle is accumulated (FP64) and the lower triangle is its conjugate mirror. G, H: device
- * complex128 [nb][p][p]. p <= 64; dtype applies to S and AS. */
+ * complex128 [nb][p][p]. p <= 64; dtype applies to S and AS, with the accumulation of pc_gram for that dtype. */
 int pc_gram_pair(int nb, long L, int p, int dtype, const void *S, long ss, const void *AS, void *G, void *H,
                  void *stream);
 

@@ -159,6 +159,10 @@ size_t gram_scratch_bytes(int nb, long L, int p, int q) {
 int launch_gram(int nb, long L, int p, int q, int dtype, const void *A, long sa, const void *B, long sb, void *G,
                 void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act) {
   if (nb == 0 || p == 0 || q == 0) return PC_OK;
+  if (dtype == PC_C64) {
+    const int rc = launch_gram_tc(nb, L, p, q, A, sa, B, sb, G, scratch, scratch_bytes, st, act);
+    if (rc != PC_EUNSUPPORTED) return rc;
+  }
   const int nchunk = gram_chunks(nb, L);
   if (gram_scratch_bytes(nb, L, p, q) > scratch_bytes) {
     set_error("gram: scratch too small");
@@ -295,6 +299,17 @@ size_t gram_pair_scratch_bytes(int nb, long L, int p) {
   return 2 * sizeof(double2) * (size_t)nb * gram_chunks(nb, L) * p * p;
 }
 
+void launch_gram_pair_reduce(int nb, int nchunk, int p, const double2 *part, const int *act, void *G, void *H,
+                             cudaStream_t st) {
+  gram_pair_reduce_kernel<<<nb, 256, 0, st>>>(part, part + (size_t)nb * nchunk * p * p, nchunk, p, act,
+                                              static_cast<double2 *>(G), static_cast<double2 *>(H));
+}
+
+void launch_gram_reduce(int nb, int nchunk, int p, int q, const double2 *part, const int *act, void *G,
+                        cudaStream_t st) {
+  gram_reduce_kernel<<<nb, 256, 0, st>>>(part, nchunk, p, q, act, static_cast<double2 *>(G));
+}
+
 template <typename T>
 static int launch_gram_pair_t(int nb, long L, int p, const void *S, const void *AS, long ss, double2 *part,
                               int nchunk, long chunk, cudaStream_t st, const int *act) {
@@ -325,6 +340,10 @@ int launch_gram_pair(int nb, long L, int p, int dtype, const void *S, const void
   if (gram_pair_scratch_bytes(nb, L, p) > scratch_bytes) {
     set_error("gram_pair: scratch too small");
     return PC_EINVAL;
+  }
+  if (dtype == PC_C64) {
+    const int rc = launch_gram_pair_tc(nb, L, p, S, AS, ss, G, H, scratch, scratch_bytes, st, act);
+    if (rc != PC_EUNSUPPORTED) return rc;
   }
   const int nchunk = gram_chunks(nb, L);
   long chunk = (L + nchunk - 1) / nchunk;

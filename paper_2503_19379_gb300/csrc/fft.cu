@@ -214,6 +214,202 @@ __global__ void __launch_bounds__(256) fft_z_symbol_kernel(const cplx<T> *__rest
   }
 }
 
+// ------------------------------------------------------------------------------------------------ register path
+// complex64, N = 2^LOGN <= 64: one thread per line with the whole line in registers; shared memory only carries the
+// transposes between the passes. Same butterflies and orders as fft_lines (DIF: natural in, bit-reversed out;
+// DIT inverse: bit-reversed in, natural out), with the loop structure resolved at compile time.
+template <int LOGN, int LH>
+__device__ __forceinline__ void reg_dif_stage(float2 (&v)[1 << LOGN], const float2 (&w)[(1 << LOGN) / 2]) {
+  constexpr int half = 1 << LH;
+#pragma unroll
+  for (int r = 0; r < (1 << LOGN) / 2; ++r) {
+    const int j = r & (half - 1), i0 = ((r >> LH) << (LH + 1)) + j, i1 = i0 + half;
+    const float2 x0 = v[i0], x1 = v[i1];
+    v[i0] = cadd(x0, x1);
+    v[i1] = j == 0 ? csub(x0, x1) : cmul(csub(x0, x1), w[j << (LOGN - 1 - LH)]);  // w[0] = 1
+  }
+  if constexpr (LH > 0) reg_dif_stage<LOGN, LH - 1>(v, w);
+}
+template <int LOGN, int LH>
+__device__ __forceinline__ void reg_dit_stage(float2 (&v)[1 << LOGN], const float2 (&w)[(1 << LOGN) / 2]) {
+  constexpr int half = 1 << LH;
+#pragma unroll
+  for (int r = 0; r < (1 << LOGN) / 2; ++r) {
+    const int j = r & (half - 1), i0 = ((r >> LH) << (LH + 1)) + j, i1 = i0 + half;
+    const float2 t = j == 0 ? v[i1] : cmulc(w[j << (LOGN - 1 - LH)], v[i1]);
+    const float2 x0 = v[i0];
+    v[i1] = csub(x0, t);
+    v[i0] = cadd(x0, t);
+  }
+  if constexpr (LH + 1 < LOGN) reg_dit_stage<LOGN, LH + 1>(v, w);
+}
+template <int LOGN>
+__device__ __forceinline__ void reg_dif(float2 (&v)[1 << LOGN], const float2 (&w)[(1 << LOGN) / 2]) {
+  reg_dif_stage<LOGN, LOGN - 1>(v, w);
+}
+template <int LOGN>
+__device__ __forceinline__ void reg_dit_inv(float2 (&v)[1 << LOGN], const float2 (&w)[(1 << LOGN) / 2]) {
+  reg_dit_stage<LOGN, 0>(v, w);
+}
+template <int LOGN> __device__ __forceinline__ void reg_twiddles(float2 (&w)[(1 << LOGN) / 2], const float2 *tw) {
+#pragma unroll
+  for (int i = 0; i < (1 << LOGN) / 2; ++i) w[i] = tw[i];
+}
+
+// Both in-plane transforms of P = min(256 / N, N) planes (component, z): rows (x) then columns (y) forward, columns
+// then rows inverse. Plane rows are padded to N + 1 elements so that row-wise and column-wise line reads are free of
+// bank conflicts. grid (3N / P, m, nb), P N threads; thread t owns line t % N of plane t / N.
+template <int LOGN> constexpr int xy_planes() { return (256 >> LOGN) < (1 << LOGN) ? (256 >> LOGN) : (1 << LOGN); }
+template <int LOGN, bool FWD>
+__global__ void __launch_bounds__(xy_planes<LOGN>() * (1 << LOGN)) fft_xy_reg_kernel(const float2 *__restrict__ in, long si,
+                                                         float2 *__restrict__ out, long so,
+                                                         const float2 *__restrict__ tw, const int *act) {
+  constexpr int N = 1 << LOGN, P = xy_planes<LOGN>(), LD = N + 1, NT = P * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *a = reinterpret_cast<float2 *>(smem_raw);  // [P][N][LD]
+  const long n = (long)N * N * N;
+  const int b = act ? act[blockIdx.z] : (int)blockIdx.z;
+  const long off = (long)blockIdx.y * 3 * n + (long)blockIdx.x * P * N * N;
+  const float2 *src = in + (long)b * si + off;
+  float2 *dst = out + (long)b * so + off;
+  float2 w[N / 2];
+  reg_twiddles<LOGN>(w, tw);
+  for (int i = threadIdx.x; i < P * N * N; i += NT) {
+    const int x = i % N, py = i / N;  // py = plane * N + y
+    a[py * LD + x] = src[i];
+  }
+  __syncthreads();
+  const int pl = threadIdx.x / N, l = threadIdx.x % N;
+  float2 *ap = a + pl * N * LD;
+  float2 v[N];
+#pragma unroll
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool rows = FWD ? pass == 0 : pass == 1;  // row lines: x varies, fixed y = l
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = rows ? ap[l * LD + i] : ap[i * LD + l];
+    if (FWD)
+      reg_dif<LOGN>(v, w);
+    else
+      reg_dit_inv<LOGN>(v, w);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      if (rows)
+        ap[l * LD + i] = v[i];
+      else
+        ap[i * LD + l] = v[i];
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < P * N * N; i += NT) {
+    const int x = i % N, py = i / N;
+    dst[i] = a[py * LD + x];
+  }
+}
+
+// Along z with the symbol: YP rows y (YP * 3 * N threads, one per (y, component, x) line), all x. The forward DIF
+// along z, the 3x3 symbol inverse per mode (components exchanged through shared memory) and the inverse DIT.
+// grid (N / YP, m, nb).
+template <int LOGN, int YP>
+__global__ void __launch_bounds__(YP * 3 * (1 << LOGN)) fft_z_reg_kernel(const float2 *__restrict__ in, long si,
+                                                                        float2 *__restrict__ out, long so,
+                                                                        const float2 *__restrict__ tw,
+                                                                        const double2 *__restrict__ sym,
+                                                                        const KParam *__restrict__ kp,
+                                                                        const int *act, int laplacian) {
+  constexpr int N = 1 << LOGN, NT = YP * 3 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *a = reinterpret_cast<float2 *>(smem_raw);  // [YP][3][N z][N x]
+  float2 *s1 = a + YP * 3 * N * N;                   // symbols d1 (x), d2 (y), d3 (z) in FP32: [3][N]
+  const long n = (long)N * N * N;
+  const int b = act ? act[blockIdx.z] : (int)blockIdx.z;
+  const int y0 = blockIdx.x * YP;
+  const long base_i = (long)b * si + (long)blockIdx.y * 3 * n + (long)y0 * N;
+  const long base_o = (long)b * so + (long)blockIdx.y * 3 * n + (long)y0 * N;
+  const double2 *symb = sym + (long)b * 3 * N;
+  for (int i = threadIdx.x; i < 3 * N; i += NT) s1[i] = make_float2((float)symb[i].x, (float)symb[i].y);
+  float2 w[N / 2];
+  reg_twiddles<LOGN>(w, tw);
+  // a[yy][c][z][x] <- in[c n + z N^2 + (y0 + yy) N + x]
+  for (int i = threadIdx.x; i < YP * 3 * N * N; i += NT) {
+    const int x = i % N, z = (i / N) % N, c = (i / (N * N)) % 3, yy = i / (3 * N * N);
+    a[i] = in[base_i + (long)c * n + (long)z * N * N + (long)yy * N + x];
+  }
+  __syncthreads();
+  const int x = threadIdx.x % N, line = threadIdx.x / N;  // line = yy * 3 + c
+  float2 *al = a + (long)line * N * N + x;
+  float2 v[N];
+#pragma unroll
+  for (int z = 0; z < N; ++z) v[z] = al[z * N];
+  reg_dif<LOGN>(v, w);
+#pragma unroll
+  for (int z = 0; z < N; ++z) al[z * N] = v[z];
+  __syncthreads();
+  const float fac = (float)((kp[b].gamma - 1.0) / kp[b].gamma);
+  const float scale = 1.0f / (float)n;
+  for (int i = threadIdx.x; i < YP * N * N; i += NT) {
+    const int xx = i % N, z = (i / N) % N, yy = i / (N * N);
+    const float2 d1 = s1[bitrev(xx, LOGN)], d2 = s1[N + bitrev(y0 + yy, LOGN)], d3 = s1[2 * N + bitrev(z, LOGN)];
+    const float sigma = d1.x * d1.x + d1.y * d1.y + d2.x * d2.x + d2.y * d2.y + d3.x * d3.x + d3.y * d3.y;
+    float2 *e = a + (long)yy * 3 * N * N + z * N + xx;
+    float2 r1 = e[0], r2 = e[N * N], r3 = e[2 * N * N];
+    if (!(sigma > 0.f)) {
+      r1 = r2 = r3 = make_float2(0.f, 0.f);
+    } else {
+      const float inv = scale / sigma;
+      if (!laplacian) {
+        const float2 sd = cadd(cadd(cmul(d1, r1), cmul(d2, r2)), cmul(d3, r3));  // d^T r
+        const float f = fac / sigma;
+        r1 = csub(r1, cscale(cmulc(d1, sd), f));
+        r2 = csub(r2, cscale(cmulc(d2, sd), f));
+        r3 = csub(r3, cscale(cmulc(d3, sd), f));
+      }
+      r1 = cscale(r1, inv);
+      r2 = cscale(r2, inv);
+      r3 = cscale(r3, inv);
+    }
+    e[0] = r1;
+    e[N * N] = r2;
+    e[2 * N * N] = r3;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int z = 0; z < N; ++z) v[z] = al[z * N];
+  reg_dit_inv<LOGN>(v, w);
+#pragma unroll
+  for (int z = 0; z < N; ++z) al[z * N] = v[z];
+  __syncthreads();
+  for (int i = threadIdx.x; i < YP * 3 * N * N; i += NT) {
+    const int xx = i % N, z = (i / N) % N, c = (i / (N * N)) % 3, yy = i / (3 * N * N);
+    out[base_o + (long)c * n + (long)z * N * N + (long)yy * N + xx] = a[i];
+  }
+}
+
+template <int LOGN>
+static int launch_precond_reg(pc_ctx *ctx, int nb, int m, const float2 *R, long sr, float2 *W, long sw,
+                              const int *act) {
+  constexpr int N = 1 << LOGN, P = xy_planes<LOGN>();
+  constexpr int YP = N >= 64 ? 1 : (N >= 32 ? 2 : (N >= 16 ? 4 : 8));
+  const size_t sxy = sizeof(float2) * (size_t)P * N * (N + 1);
+  const size_t sz = sizeof(float2) * ((size_t)YP * 3 * N * N + 3 * N);
+  static bool configured = false;
+  if (!configured) {
+    PC_CK(cudaFuncSetAttribute(fft_xy_reg_kernel<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sxy));
+    PC_CK(cudaFuncSetAttribute(fft_xy_reg_kernel<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sxy));
+    PC_CK(cudaFuncSetAttribute(fft_z_reg_kernel<LOGN, YP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz));
+    configured = true;
+  }
+  const float2 *tw = ctx->twf.as<float2>();
+  const int lap = ctx->opts.precond == PC_PRECOND_LAPLACIAN;
+  fft_xy_reg_kernel<LOGN, true><<<dim3(3 * N / P, m, nb), P * N, sxy, ctx->stream>>>(R, sr, W, sw, tw, act);
+  PC_CK_LAUNCH();
+  fft_z_reg_kernel<LOGN, YP><<<dim3(N / YP, m, nb), YP * 3 * N, sz, ctx->stream>>>(
+      W, sw, W, sw, tw, ctx->symd.as<double2>(), ctx->kparam.as<KParam>(), act, lap);
+  PC_CK_LAUNCH();
+  fft_xy_reg_kernel<LOGN, false><<<dim3(3 * N / P, m, nb), P * N, sxy, ctx->stream>>>(W, sw, W, sw, tw, act);
+  PC_CK_LAUNCH();
+  return PC_OK;
+}
+
 template <typename T>
 static int launch_precond_t(pc_ctx *ctx, int nb, int m, const void *R, long sr, void *W, long sw, const int *act) {
   using C = cplx<T>;
@@ -276,7 +472,15 @@ int launch_precond(pc_ctx *ctx, int nb, int m, int dtype, const void *R, long sr
                    const int *act) {
   if (nb == 0 || m == 0) return PC_OK;
   if (dtype == PC_C128) return launch_precond_t<double>(ctx, nb, m, R, sr, W, sw, act);
-  return launch_precond_t<float>(ctx, nb, m, R, sr, W, sw, act);
+  const float2 *Rf = static_cast<const float2 *>(R);
+  float2 *Wf = static_cast<float2 *>(W);
+  switch (ctx->logN) {
+    case 3: return launch_precond_reg<3>(ctx, nb, m, Rf, sr, Wf, sw, act);
+    case 4: return launch_precond_reg<4>(ctx, nb, m, Rf, sr, Wf, sw, act);
+    case 5: return launch_precond_reg<5>(ctx, nb, m, Rf, sr, Wf, sw, act);
+    case 6: return launch_precond_reg<6>(ctx, nb, m, Rf, sr, Wf, sw, act);
+    default: return launch_precond_t<float>(ctx, nb, m, R, sr, W, sw, act);
+  }
 }
 
 }  // namespace pc

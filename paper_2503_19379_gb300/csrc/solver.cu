@@ -265,8 +265,11 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
   }
   int rc = upload_kpoints(ctx, nb, kr.data(), gam.data());
   if (rc) return rc;
-  if (ctx->opts.precision == PC_PREC_MIXED)
-    return solve_mixed(ctx, nb, kr.data(), gam, zero, nbands, m, tol, evals, evecs, iters, resid);
+  if (ctx->opts.precision == PC_PREC_MIXED) {
+    rc = solve_mixed(ctx, nb, kr.data(), gam, zero, nbands, m, tol, evals, evecs, iters, resid);
+    const int tc = gram_tc_check();  // a time-out inside the tensor-core Gram kernel voids the result
+    return tc ? tc : rc;
+  }
 
   const long sS = 3L * m * L;  // panel stride per k-point (elements)
   const size_t panel = sizeof(double2) * (size_t)sS * nb;

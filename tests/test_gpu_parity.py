@@ -139,16 +139,23 @@ def test_apply_precond_fp64(pcmod, N, variant):
             assert np.max(np.abs(W[b, j] - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
-def test_apply_precond_fp32(pcmod):
-    N = 32
-    S, _ = make_solver(pcmod, N)
-    kpts = np.array([[1.1, -0.2, 0.7]])
-    R = rand_block(5, (1, 2, 3 * N ** 3)).astype(np.complex64)
-    W = S.apply_precond(kpts, [64.0], to_dev(R.reshape(1, 2, 3, N, N, N), torch.complex64)).cpu().numpy()
-    W = W.reshape(1, 2, -1)
-    for j in range(2):
-        ref = precond.apply_preconditioner(R[0, j].astype(np.complex128), N, 1.0 / N, kpts[0], 64.0).ravel()
-        assert np.max(np.abs(W[0, j] - ref)) <= 2e-5 * np.max(np.abs(ref))
+@pytest.mark.parametrize("N,variant", [(8, 0), (16, 0), (32, 0), (64, 0), (32, 1), (128, 0)])
+def test_apply_precond_fp32(pcmod, N, variant):
+    """complex64 solve (register-resident line FFTs for N <= 64, shared-memory FFTs above) against the FP64
+    oracle, including a k = 0 point whose zero mode is singular and maps to zero."""
+    S, _ = make_solver(pcmod, N, precond=variant)
+    kpts = np.array([[1.1, -0.2, 0.7], [0.0, 0.0, 0.0]])
+    gammas = [64.0, 2.0 * N]
+    nf = 1 if N > 64 else 2
+    R = rand_block(5 + N, (2, nf, 3 * N ** 3)).astype(np.complex64)
+    W = S.apply_precond(kpts, gammas, to_dev(R.reshape(2, nf, 3, N, N, N), torch.complex64)).cpu().numpy()
+    W = W.reshape(2, nf, -1)
+    name = "laplacian" if variant else "gamma"
+    for b in range(2):
+        for j in range(nf):
+            ref = precond.apply_preconditioner(R[b, j].astype(np.complex128), N, 1.0 / N, kpts[b], gammas[b], 1,
+                                               name).ravel()
+            assert np.max(np.abs(W[b, j] - ref)) <= 2e-5 * np.max(np.abs(ref))
 
 
 def test_precond_inverts_operator_at_unit_eps(pcmod):
