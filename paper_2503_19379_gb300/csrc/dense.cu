@@ -157,10 +157,10 @@ size_t gram_scratch_bytes(int nb, long L, int p, int q) {
 }
 
 int launch_gram(int nb, long L, int p, int q, int dtype, const void *A, long sa, const void *B, long sb, void *G,
-                void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act) {
+                void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc) {
   if (nb == 0 || p == 0 || q == 0) return PC_OK;
   if (dtype == PC_C64) {
-    const int rc = launch_gram_tc(nb, L, p, q, A, sa, B, sb, G, scratch, scratch_bytes, st, act);
+    const int rc = launch_gram_tc(nb, L, p, q, A, sa, B, sb, G, scratch, scratch_bytes, st, act, nb_alloc);
     if (rc != PC_EUNSUPPORTED) return rc;
   }
   const int nchunk = gram_chunks(nb, L);
@@ -331,7 +331,7 @@ static int launch_gram_pair_t(int nb, long L, int p, const void *S, const void *
 }
 
 int launch_gram_pair(int nb, long L, int p, int dtype, const void *S, const void *AS, long ss, void *G, void *H,
-                     void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act) {
+                     void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc) {
   if (nb == 0 || p == 0) return PC_OK;
   if (p > 64) {
     set_error("gram_pair: at most 64 columns");
@@ -342,7 +342,7 @@ int launch_gram_pair(int nb, long L, int p, int dtype, const void *S, const void
     return PC_EINVAL;
   }
   if (dtype == PC_C64) {
-    const int rc = launch_gram_pair_tc(nb, L, p, S, AS, ss, G, H, scratch, scratch_bytes, st, act);
+    const int rc = launch_gram_pair_tc(nb, L, p, S, AS, ss, G, H, scratch, scratch_bytes, st, act, nb_alloc);
     if (rc != PC_EUNSUPPORTED) return rc;
   }
   const int nchunk = gram_chunks(nb, L);

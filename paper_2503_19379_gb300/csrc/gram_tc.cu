@@ -17,16 +17,20 @@
 // 4 TC_GROUP additions of hi.hi, which keeps the result at the accuracy of an FP32 CUDA-core product.
 //
 // Structure (one CTA per (k-point, K-chunk), 16 warps):
-//   warp 0       bulk copies (cp.async.bulk) of 128-byte row segments of A and B1 into a 4-stage staging ring;
+//   warp 0       one thread issues 2D tensor-map copies (cp.async.bulk.tensor, 128-byte swizzle) of the A and B1
+//                tiles (32 floats x rows) into a 4-stage staging ring;
 //   warp 1       one thread issues the tcgen05.mma chain (12 per 32-float K tile) into the TMEM accumulators;
-//   warps 2..7   turn each staged tile into the hi/lo operand tiles in the 128-byte-swizzled K-major layout the
-//                tensor core reads (rows of 128 bytes, 16-byte chunks XOR-ed with the row index mod 8), double
-//                buffered against the MMAs;
+//   warps 2..7   turn each staged tile into the hi/lo operand tiles of the K-major layout the tensor core reads
+//                (rows of 128 bytes, 16-byte chunks XOR-ed with the row index mod 8, as the copy left them; every
+//                block of rows starts at a multiple of 8, so a chunk keeps its position), double buffered against
+//                the MMAs;
 //   warps 8..15  drain the accumulators (tcgen05.ld: TMEM lane quarter = warp % 4, two warps per quarter splitting
 //                the columns) into registers and finally write FP64 partial sums per chunk, which the Gram reduction
 //                kernels add up.
 // Every wait is bounded in time: a wait that runs out raises an abort flag that the other roles observe, copies and
 // MMAs in flight are drained (again with a bound), TMEM is released and an error flag is left for the host.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -95,10 +99,12 @@ __device__ bool bar_wait(uint32_t bar, uint32_t parity, volatile int *abort, boo
     }
   }
 }
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -149,8 +155,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 struct TcArgs {
-  const float2 *A, *B;  // panels: k-point b at + b * sa (b * sb), column c at + c * L (complex elements)
-  long sa, sb, L;
+  long cppA, cppB;      // columns per k-point panel (panel strides / L): tensor-map row of (b, c) = b * cpp + c
+  long L;
   int p, q;             // columns of A and of B1
   int PB, QB;           // padded row counts (multiples of 8); the B operand is rows [0, N) of the operand region
   int N;                // MMA N: QB + PB when pair (B = [B1; A]), else QB (multiple of 16, <= 128)
@@ -164,7 +170,8 @@ struct TcArgs {
   const int *act;
 };
 
-__global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tmA,
+                                                                const __grid_constant__ CUtensorMap tmB) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_addr(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -226,30 +233,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a) 
 
   if (warp == 0) {
     // ------------------------------------------------ producer
-    const float2 *Ab = a.A + (long)b * a.sa;
-    const float2 *Bb = a.B + (long)b * a.sb;
-    const int rows = a.p + a.q;
-    const uint32_t tx = (uint32_t)rows * 128u;
+    const uint32_t tx = (uint32_t)(a.PB + a.QB) * 128u;  // whole boxes (rows past the tensor are zero-filled)
+    const int yA = (int)(b * a.cppA), yB = (int)(b * a.cppB);
     int issued = 0;
-    for (int t = 0; t < ntile; ++t) {
-      const int s = t % ns;
-      if (!bar_wait(bar_empty + 8u * s, ((t / ns) & 1) ^ 1, abort)) break;
-      if (lane == 0) bar_expect_tx(bar_full + 8u * s, tx);
-      __syncwarp();
-      const long kc = (long)(t_begin + t) * (TC_KT / 2);  // complex offset of the tile
-      const uint32_t st = base + off_stage + (uint32_t)s * stage_bytes;
-      for (int r = lane; r < rows; r += 32) {
-        const bool isA = r < a.p;
-        const int c = isA ? r : r - a.p;
-        const float2 *src = (isA ? Ab : Bb) + (long)c * a.L + kc;
-        const uint32_t dst = st + (uint32_t)(isA ? c : a.PB + c) * 128u;
-        bulk_g2s(dst, src, 128u, bar_full + 8u * s);
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      for (int t = 0; t < ntile; ++t) {
+        const int s = t % ns;
+        if (!bar_wait(bar_empty + 8u * s, ((t / ns) & 1) ^ 1, abort)) break;
+        bar_expect_tx(bar_full + 8u * s, tx);
+        const int x = (t_begin + t) * TC_KT;  // float offset: a multiple of 32 (128 bytes)
+        const uint32_t st = base + off_stage + (uint32_t)s * stage_bytes;
+        tma_load_2d(st, &tmA, x, yA, bar_full + 8u * s);
+        tma_load_2d(st + (uint32_t)a.PB * 128u, &tmB, x, yB, bar_full + 8u * s);
+        issued = t + 1;
       }
-      issued = t + 1;
+      // drain: the last use of every stage must have landed before the CTA may exit
+      for (int t = max(0, issued - ns); t < issued; ++t)
+        bar_wait(bar_full + 8u * (t % ns), (t / ns) & 1, abort, false);
     }
-    // drain: the last use of every stage must have landed before the CTA may exit
-    for (int t = max(0, issued - ns); t < issued; ++t)
-      bar_wait(bar_full + 8u * (t % ns), (t / ns) & 1, abort, false);
+    __syncwarp();
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
@@ -299,8 +303,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a) 
       const unsigned char *st = sm + off_stage + (size_t)s * stage_bytes;
       unsigned char *hi = sm + (size_t)u * opbuf, *lo = hi + region;
       for (int e = tt; e < nel; e += 32 * TC_NTR) {
-        const int row = e >> 3, c = e & 7;
-        const float4 v = *reinterpret_cast<const float4 *>(st + row * 128 + c * 16);
+        const int row = e >> 3, pc = e & 7;  // physical 16-byte chunk, kept in every row it is copied to
+        const float4 v = *reinterpret_cast<const float4 *>(st + row * 128 + pc * 16);
         float4 h, l;
         h.x = tf32_rna(v.x);
         h.y = tf32_rna(v.y);
@@ -315,13 +319,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a) 
           // A row: at QB + row, and its (-im, re) partner at QB + PB + row
           R = a.QB + row;
           const int R2 = R + a.PB;
-          const uint32_t o2 = (uint32_t)R2 * 128u + (uint32_t)((c ^ (R2 & 7)) << 4);
+          const uint32_t o2 = (uint32_t)R2 * 128u + (uint32_t)pc * 16u;
           *reinterpret_cast<float4 *>(hi + o2) = make_float4(-h.y, h.x, -h.w, h.z);
           *reinterpret_cast<float4 *>(lo + o2) = make_float4(-l.y, l.x, -l.w, l.z);
         } else {
           R = row - a.PB;  // B1 row
         }
-        const uint32_t o = (uint32_t)R * 128u + (uint32_t)((c ^ (R & 7)) << 4);
+        const uint32_t o = (uint32_t)R * 128u + (uint32_t)pc * 16u;
         *reinterpret_cast<float4 *>(hi + o) = h;
         *reinterpret_cast<float4 *>(lo + o) = l;
       }
@@ -438,13 +442,38 @@ int tc_chunks(int nb, int ktiles, long maxc) {
   return std::max(1, best);
 }
 
-int launch_tc(int nb, long L, int p, int q, bool pair, const void *A, long sa, const void *B, long sb, double2 *part,
-              size_t scratch_bytes, cudaStream_t st, const int *act, int *nchunk_out) {
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+// rows of a panel array as a 2D FP32 tensor: x = float offset along a column (2L), y = b * cpp + column
+bool make_map(CUtensorMap *map, const void *base, long L, long rows, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)(2 * L), (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(8 * L)};
+  const cuuint32_t box[2] = {(cuuint32_t)TC_KT, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int launch_tc(int nb, int nb_alloc, long L, int p, int q, bool pair, const void *A, long sa, const void *B, long sb,
+              double2 *part, size_t scratch_bytes, cudaStream_t st, const int *act, int *nchunk_out) {
   TcArgs a{};
-  a.A = static_cast<const float2 *>(A);
-  a.B = static_cast<const float2 *>(B);
-  a.sa = sa;
-  a.sb = sb;
+  a.cppA = sa / L;
+  a.cppB = sb / L;
   a.L = L;
   a.p = p;
   a.q = q;
@@ -481,7 +510,11 @@ int launch_tc(int nb, long L, int p, int q, bool pair, const void *A, long sa, c
   // a CTA that takes all 512 TMEM columns must have its SM to itself: ask for more than half the shared memory
   size_t smem = tc_smem(a.PB, a.QB, ns);
   if (a.tmem_cols == 512) smem = std::max<size_t>(smem, TC_SMEM_MAX / 2 + 4096);
-  gram_tc_kernel<<<dim3(c, nb), TC_THREADS, smem, st>>>(a);
+  CUtensorMap tmA, tmB;
+  if (!make_map(&tmA, A, L, (long)(nb_alloc - 1) * a.cppA + p, a.PB) ||
+      !make_map(&tmB, B, L, (long)(nb_alloc - 1) * a.cppB + q, a.QB))
+    return PC_EUNSUPPORTED;
+  gram_tc_kernel<<<dim3(c, nb), TC_THREADS, smem, st>>>(a, tmA, tmB);
   PC_CK_LAUNCH();
   *nchunk_out = c;
   return PC_OK;
@@ -501,8 +534,8 @@ bool tc_shape_ok(long L, int p, int q, const void *A, long sa, const void *B, lo
   if (L <= 0 || L % (TC_KT / 2) != 0) return false;  // whole 32-float tiles
   if (p < 1 || p > 64 || q < 1 || q > 128) return false;
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) return false;
-  if ((sa | sb) & 1) return false;  // 16-byte aligned panels
-  return true;
+  if (sa % L != 0 || sb % L != 0) return false;  // panels of whole columns: one 2D tensor per panel array
+  return encode_fn() != nullptr;
 }
 
 }  // namespace
@@ -510,11 +543,12 @@ bool tc_shape_ok(long L, int p, int q, const void *A, long sa, const void *B, lo
 // G = S^H S and H = S^H AS (complex64 panels, p <= 64) on the tensor cores; PC_EUNSUPPORTED when the shape or
 // alignment does not fit (the caller then takes the CUDA-core kernel).
 int launch_gram_pair_tc(int nb, long L, int p, const void *S, const void *AS, long ss, void *G, void *H,
-                        void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act) {
+                        void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc) {
   if (!tc_shape_ok(L, p, p, S, ss, AS, ss)) return PC_EUNSUPPORTED;
   int c = 0;
   double2 *part = static_cast<double2 *>(scratch);
-  int rc = launch_tc(nb, L, p, p, true, S, ss, AS, ss, part, scratch_bytes, st, act, &c);
+  int rc = launch_tc(nb, nb_alloc > 0 ? nb_alloc : nb, L, p, p, true, S, ss, AS, ss, part, scratch_bytes, st, act,
+                     &c);
   if (rc) return rc;
   launch_gram_pair_reduce(nb, c, p, part, act, G, H, st);
   PC_CK_LAUNCH();
@@ -523,11 +557,12 @@ int launch_gram_pair_tc(int nb, long L, int p, const void *S, const void *AS, lo
 
 // G = A^H B (complex64, p <= 64 columns of A, q <= 128 of B) on the tensor cores; PC_EUNSUPPORTED as above.
 int launch_gram_tc(int nb, long L, int p, int q, const void *A, long sa, const void *B, long sb, void *G,
-                   void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act) {
+                   void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc) {
   if (!tc_shape_ok(L, p, q, A, sa, B, sb)) return PC_EUNSUPPORTED;
   int c = 0;
   double2 *part = static_cast<double2 *>(scratch);
-  int rc = launch_tc(nb, L, p, q, false, A, sa, B, sb, part, scratch_bytes, st, act, &c);
+  int rc = launch_tc(nb, nb_alloc > 0 ? nb_alloc : nb, L, p, q, false, A, sa, B, sb, part, scratch_bytes, st, act,
+                     &c);
   if (rc) return rc;
   launch_gram_reduce(nb, c, p, q, part, act, G, st);
   PC_CK_LAUNCH();

@@ -147,11 +147,12 @@ int launch_apply_op(pc_ctx *ctx, int nb, int m, int dtype, const void *X, long s
                     const int *act);
 int launch_precond(pc_ctx *ctx, int nb, int m, int dtype, const void *R, long sr, void *W, long sw,
                    const int *act);
+// nb_alloc: k-points in the panel arrays (the act list indexes them); <= 0 means nb
 int launch_gram(int nb, long L, int p, int q, int dtype, const void *A, long sa, const void *B, long sb, void *G,
-                void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act);
+                void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc = -1);
 size_t gram_scratch_bytes(int nb, long L, int p, int q);
 int launch_gram_pair(int nb, long L, int p, int dtype, const void *S, const void *AS, long ss, void *G, void *H,
-                     void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act);
+                     void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc = -1);
 size_t gram_pair_scratch_bytes(int nb, long L, int p);
 // reductions of per-chunk partial sums ([nb][nchunk][p][q] double2; the pair: G block then H block, upper triangles)
 void launch_gram_pair_reduce(int nb, int nchunk, int p, const double2 *part, const int *act, void *G, void *H,
@@ -160,9 +161,9 @@ void launch_gram_reduce(int nb, int nchunk, int p, int q, const double2 *part, c
                         cudaStream_t st);
 // complex64 Gram products on the tensor cores (gram_tc.cu); PC_EUNSUPPORTED when the shape does not fit
 int launch_gram_pair_tc(int nb, long L, int p, const void *S, const void *AS, long ss, void *G, void *H,
-                        void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act);
+                        void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc);
 int launch_gram_tc(int nb, long L, int p, int q, const void *A, long sa, const void *B, long sb, void *G,
-                   void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act);
+                   void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc);
 // reads and clears the time-out flag of the tensor-core Gram kernel (call after a synchronisation)
 int gram_tc_check();
 // Y = S C (+ Z, a complex64 addend, if Z is not null); arithmetic in the precision of dtype

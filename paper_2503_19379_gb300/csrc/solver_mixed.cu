@@ -114,7 +114,7 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
                 [&] { return launch_narrow(nb, L, m, X64[0], sX, F[0], sF, st, d_act); }));
   RUN(OP32(nb, m, F[0], sF, AF[0], sF));
   RUN(run_stage(ctx, PC_STAGE_GRAM, 2, 8.0 * m * (m + 1) * Ld * nb, 2.0 * m * Ld * 8.0 * nb, [&] {
-    return launch_gram_pair(nb, L, m, PC_C64, F[0], AF[0], sF, Gm, Hm, scratch, scr, st, d_act);
+    return launch_gram_pair(nb, L, m, PC_C64, F[0], AF[0], sF, Gm, Hm, scratch, scr, st, d_act, nb);
   }));
   RUN(run_stage(ctx, PC_STAGE_RR, 1, 0.0, 2.0 * m * m * 16.0 * nb,
                 [&] { return launch_rr(nb, m, m, Gm, Hm, drop, theta, coef, nullptr, st, d_act); }));
@@ -271,10 +271,11 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
     RUN(OP32(na, m, F[cur] + (long)m * L, sF, AF[cur] + (long)m * L, sF));
     // ---- pencil: complex64 products over [X | W | P], the R^H Q coupling, FP64 X-X block in phase 2
     RUN(run_stage(ctx, PC_STAGE_GRAM, 2, 8.0 * nc * (nc + 1) * Ld * na, 2.0 * nc * Ld * 8.0 * na, [&] {
-      return launch_gram_pair(na, L, nc, PC_C64, F[cur], AF[cur], sF, Gm, Hm, scratch, scr, st, d_act);
+      return launch_gram_pair(na, L, nc, PC_C64, F[cur], AF[cur], sF, Gm, Hm, scratch, scr, st, d_act, nb);
     }));
     RUN(run_stage(ctx, PC_STAGE_GRAM, 2, 8.0 * m * nq * Ld * na, (double)(m + nq) * Ld * 8.0 * na, [&] {
-      return launch_gram(na, L, m, nq, PC_C64, R32, sX, F[cur] + (long)m * L, sF, RQ, scratch, scr, st, d_act);
+      return launch_gram(na, L, m, nq, PC_C64, R32, sX, F[cur] + (long)m * L, sF, RQ, scratch, scr, st, d_act,
+                         nb);
     }));
     if (!act2.empty()) {
       RUN(set_act(act2));
