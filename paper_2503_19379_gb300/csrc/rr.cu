@@ -1,0 +1,561 @@
+// Batched Rayleigh-Ritz step of LOBPCG (Section 5.1): for every k-point the pencil (H, G) = (S^H Op S, S^H S) of
+// its search space S = [X | W | P] (n <= 64 columns) is reduced to its m lowest Ritz pairs, one thread block per
+// k-point, everything in shared memory, FP64.
+//
+//   1. unit-diagonal scaling D of G (a zero column gets D = 0 and is dropped below);
+//   2. Cholesky of D G D with diagonal pivoting, stopped when the largest remaining pivot is below `drop`: the
+//      retained pivot columns span the numerically independent part of span(S); rank r;
+//   3. H3 = L^{-1} (D H D)_r L^{-H} by two forward substitutions (the second on Y^H = (L^{-1} H_r)^H);
+//   4. Householder reduction of H3 to a real symmetric tridiagonal T (complex reflectors, then a diagonal phase
+//      scaling makes the off-diagonal real and non-negative);
+//   5. bisection on Sturm counts for the m lowest eigenvalues of T;
+//   6. inverse iteration on T (partially pivoted tridiagonal LU, 3 steps), with modified Gram-Schmidt against
+//      earlier members of the same cluster (eigenvalues closer than 1e-7 |T|), processed cluster position by
+//      position so that members are orthogonal;
+//   7. back-transformation y = Q Phi z, then coef = D P L^{-H} y.
+//
+// A GB300 SM retires about 2 FP64 FMA per clock, and a block's FP64 work here is a few hundred thousand operations,
+// so the kernel is bound by the length of its dependent chains. Every phase is therefore spread over the block:
+// substitutions column-oriented (one rank-1 row update per step for all threads), norms and dot products as warp
+// reductions, the back-transformation one warp per Ritz vector with the vector in registers, shared matrices with
+// an odd leading dimension (row-wise access by consecutive threads hits distinct banks), reciprocals of pivots
+// taken once. Bisection (step 5) runs two lanes per eigenvalue (trisection: each lane counts at one interior
+// point), first in FP32 down to ~30 eps32 |T| (backward-stable Sturm counts make the FP32 bracket exact for a
+// matrix within a few eps32 |T|; the bracket is widened by 16 eps32 |T| and verified by two FP64 counts, with the
+// Gershgorin interval as fallback), then in FP64 to the absolute width eps64 |T| (LAPACK's default for bisection,
+// below which the FP64 Sturm count itself is not accurate).
+#include <cfloat>
+#include <cmath>
+
+#include "pc_internal.cuh"
+
+namespace pc {
+
+namespace {
+
+constexpr double RR_CLUSTER_REL = 1e-7;
+constexpr int RR_MAXN = 64;
+constexpr int RR_THREADS = 256;
+constexpr double RR_EPS = 2.220446049250313e-16;
+
+__device__ __forceinline__ double2 shfl_xor_d2(double2 v, int mask) {
+  return make_double2(__shfl_xor_sync(0xffffffffu, v.x, mask), __shfl_xor_sync(0xffffffffu, v.y, mask));
+}
+__device__ __forceinline__ double2 warp_sum_d2(double2 v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = cadd(v, shfl_xor_d2(v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Partially pivoted LU of the tridiagonal (T - lam I), T = (d, e): factors in f[0..4r): 1/u0, u1, u2, l; pivots as
+// 0/1 in f[4r..5r).
+__device__ void tri_factor(const double *d, const double *e, int r, double lam, double tiny, double *f) {
+  double *u0i = f, *u1 = f + r, *u2 = f + 2 * r, *l = f + 3 * r, *piv = f + 4 * r;
+  double ca = d[0] - lam, cb = r > 1 ? e[0] : 0.0;
+  for (int i = 0; i < r - 1; ++i) {
+    const double sub = e[i];
+    const double ai1 = d[i + 1] - lam, bi1 = (i + 1 < r - 1) ? e[i + 1] : 0.0;
+    if (fabs(ca) >= fabs(sub)) {
+      if (ca == 0.0) ca = tiny;
+      const double ic = 1.0 / ca;
+      l[i] = sub * ic;
+      piv[i] = 0.0;
+      u0i[i] = ic;
+      u1[i] = cb;
+      u2[i] = 0.0;
+      ca = ai1 - l[i] * cb;
+      cb = bi1;
+    } else {
+      const double is = 1.0 / sub;
+      l[i] = ca * is;
+      piv[i] = 1.0;
+      u0i[i] = is;
+      u1[i] = ai1;
+      u2[i] = bi1;
+      ca = cb - l[i] * ai1;
+      cb = -l[i] * bi1;
+    }
+  }
+  if (ca == 0.0) ca = tiny;
+  u0i[r - 1] = 1.0 / ca;
+}
+
+__device__ void tri_solve(const double *f, int r, double *y) {
+  const double *u0i = f, *u1 = f + r, *u2 = f + 2 * r, *l = f + 3 * r, *piv = f + 4 * r;
+  for (int i = 0; i < r - 1; ++i) {
+    if (piv[i] != 0.0) {
+      const double yi = y[i];
+      y[i] = y[i + 1];
+      y[i + 1] = yi - l[i] * y[i + 1];
+    } else {
+      y[i + 1] -= l[i] * y[i];
+    }
+  }
+  for (int i = r - 1; i >= 0; --i) {
+    double s = y[i];
+    if (i + 1 < r) s -= u1[i] * y[i + 1];
+    if (i + 2 < r) s -= u2[i] * y[i + 2];
+    y[i] = s * u0i[i];
+  }
+}
+
+// number of eigenvalues of T = (d, e) below x (e2 = e^2), in the precision T of the arguments
+template <typename R>
+__device__ __forceinline__ int sturm_count(const R *d, const R *e2, int r, R x, R pivmin) {
+  R q = d[0] - x;
+  int c = q < R(0);
+  for (int i = 1; i < r; ++i) {
+    if (fabs(q) < pivmin) q = -pivmin;
+    q = d[i] - x - e2[i - 1] / q;
+    c += q < R(0);
+  }
+  return c;
+}
+
+// Trisection on the pair of lanes (2j, 2j+1): lane `side` counts at the interior point lo + (side + 1) (hi - lo) / 3;
+// both lanes apply the same update. Runs while any pair of the warp is still wider than its tolerance.
+template <typename R>
+__device__ void trisect(const R *d, const R *e2, int r, R pivmin, int j, int side, bool active, R &lo, R &hi,
+                        R atol, R rtol, int maxit) {
+  for (int it = 0; it < maxit; ++it) {
+    const bool open = active && !(hi - lo <= fmax(atol, rtol * fmax(fabs(lo), fabs(hi))) + pivmin);
+    if (!__any_sync(0xffffffffu, open)) break;
+    const R third = (hi - lo) / R(3);
+    const R x1 = lo + third, x2 = lo + R(2) * third;
+    const int mine = open ? sturm_count<R>(d, e2, r, side ? x2 : x1, pivmin) : 0;
+    const int other = __shfl_xor_sync(0xffffffffu, mine, 1);
+    const int c1 = side ? other : mine, c2 = side ? mine : other;
+    if (open) {
+      if (c1 > j) {
+        hi = x1;
+      } else if (c2 > j) {
+        lo = x1;
+        hi = x2;
+      } else {
+        lo = x2;
+      }
+    }
+  }
+}
+
+__host__ __device__ inline int rr_ld(int n) { return (n & 1) ? n : n + 1; }
+
+size_t rr_smem(int n, int m) {
+  const int ld = rr_ld(n);
+  return sizeof(double2) * (3 * (size_t)n * ld + 3 * (size_t)n) + sizeof(double) * (8 * (size_t)n + m) +
+         sizeof(float) * 2 * (size_t)n + sizeof(int) * (2 * (size_t)n + m) + 64;
+}
+
+__global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restrict__ Gg, const double2 *__restrict__ Hg,
+                                                        int n, int m, double drop, double *__restrict__ thetag,
+                                                        double2 *__restrict__ coefg, int *__restrict__ rankg,
+                                                        const int *__restrict__ act) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int LD = rr_ld(n);
+  double2 *A = reinterpret_cast<double2 *>(smem_raw);  // scaled G -> pivoted Cholesky factor (lower)
+  double2 *B = A + n * LD;                              // scaled H -> H3 -> tridiagonal; then Z (real r x m)
+  double2 *Vh = B + n * LD;                             // Householder vectors, row k = v_k
+  double2 *phi = Vh + n * LD;                           // phases of the tridiagonal scaling
+  double2 *pv = phi + n;                                // p / q vectors of the Householder step
+  double2 *vv = pv + n;                                 // current Householder vector
+  double *dsc = reinterpret_cast<double *>(vv + n);
+  double *dd = dsc + n, *ee = dd + n, *e2 = ee + n, *tau = e2 + n, *dinv = tau + n, *w = dinv + n;  // w: m
+  double *spare = w + m;                                                                              // 2n
+  float *d32 = reinterpret_cast<float *>(spare + 2 * n);
+  float *e232 = d32 + n;
+  int *perm = reinterpret_cast<int *>(e232 + n);
+  int *pos = perm + n;  // m
+  __shared__ int s_p, s_r, s_stop, s_maxpos;
+  __shared__ double s_piv, s_tau, s_gl, s_gu, s_tn, s_pivmin;
+  __shared__ double2 s_alpha, s_K;
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
+  const int b = act ? act[blockIdx.x] : (int)blockIdx.x;
+  const double2 *G = Gg + (long)b * n * n;
+  const double2 *H = Hg + (long)b * n * n;
+  double *Z = reinterpret_cast<double *>(B);
+
+  // 1. scaling
+  for (int i = tid; i < n; i += nt) {
+    const double gii = G[i * n + i].x;
+    dsc[i] = gii > 0.0 ? 1.0 / sqrt(gii) : 0.0;
+    perm[i] = i;
+  }
+  __syncthreads();
+  for (int i = tid; i < n * n; i += nt) {
+    const int r = i / n, c = i - r * n;
+    const double f = dsc[r] * dsc[c];
+    const double2 x = G[r * n + c], y = G[c * n + r];
+    A[r * LD + c] = cmake<double2>(0.5 * (x.x + y.x) * f, 0.5 * (x.y - y.y) * f);
+    const double2 u = H[r * n + c], v = H[c * n + r];
+    B[r * LD + c] = cmake<double2>(0.5 * (u.x + v.x) * f, 0.5 * (u.y - v.y) * f);
+  }
+  if (tid == 0) s_r = n;
+  __syncthreads();
+
+  // 2. pivoted Cholesky
+  for (int k = 0; k < n; ++k) {
+    if (warp == 0) {
+      double best = -HUGE_VAL;
+      int bi = n;
+      for (int i = k + lane; i < n; i += 32) {
+        const double v = A[i * LD + i].x;
+        if (v > best) {
+          best = v;
+          bi = i;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        s_p = bi < n ? bi : k;
+        s_piv = best;
+        s_stop = !(best > drop);
+        if (s_stop) s_r = k;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int p = s_p;
+    if (p != k) {
+      for (int c = tid; c < n; c += nt) {
+        double2 t = A[k * LD + c];
+        A[k * LD + c] = A[p * LD + c];
+        A[p * LD + c] = t;
+        t = B[k * LD + c];
+        B[k * LD + c] = B[p * LD + c];
+        B[p * LD + c] = t;
+      }
+      __syncthreads();
+      for (int r = tid; r < n; r += nt) {
+        double2 t = A[r * LD + k];
+        A[r * LD + k] = A[r * LD + p];
+        A[r * LD + p] = t;
+        t = B[r * LD + k];
+        B[r * LD + k] = B[r * LD + p];
+        B[r * LD + p] = t;
+      }
+      if (tid == 0) {
+        const int t = perm[k];
+        perm[k] = perm[p];
+        perm[p] = t;
+      }
+      __syncthreads();
+    }
+    const double lkk = sqrt(s_piv), il = 1.0 / lkk;
+    for (int i = k + 1 + tid; i < n; i += nt) A[i * LD + k] = cscale(A[i * LD + k], il);
+    __syncthreads();
+    if (tid == 0) A[k * LD + k] = cmake<double2>(lkk, 0.0);
+    const int t = n - k - 1;
+    for (int e = tid; e < t * t; e += nt) {
+      const int i = k + 1 + e / t, j = k + 1 + e % t;
+      const double2 a = A[i * LD + k], c = A[j * LD + k];
+      A[i * LD + j] = csub(A[i * LD + j], cmake<double2>(a.x * c.x + a.y * c.y, a.y * c.x - a.x * c.y));
+    }
+    __syncthreads();
+  }
+  const int r = s_r;
+  for (int i = tid; i < r; i += nt) dinv[i] = 1.0 / A[i * LD + i].x;
+  __syncthreads();
+
+  // 3. H3 = L^{-1} H_r L^{-H}: two column-oriented forward substitutions (row i, once final, updates all rows below
+  // it; the rows are scaled by 1/L_ii at the end), with a conjugate transpose in between
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i = 0; i + 1 < r; ++i) {
+      const int below = r - i - 1;
+      for (int e = tid; e < below * r; e += nt) {
+        const int kk = i + 1 + e / r, j = e % r;
+        const double2 c = cscale(A[kk * LD + i], dinv[i]);
+        B[kk * LD + j] = csub(B[kk * LD + j], cmul(c, B[i * LD + j]));
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < r * r; e += nt) {
+      const int i = e / r, j = e % r;
+      B[i * LD + j] = cscale(B[i * LD + j], dinv[i]);
+    }
+    __syncthreads();
+    if (pass == 0) {
+      for (int e = tid; e < r * r; e += nt) {
+        const int i = e / r, j = e % r;
+        if (i < j) {
+          const double2 x = B[i * LD + j], y = B[j * LD + i];
+          B[i * LD + j] = cmake<double2>(y.x, -y.y);
+          B[j * LD + i] = cmake<double2>(x.x, -x.y);
+        } else if (i == j) {
+          B[i * LD + i].y = -B[i * LD + i].y;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = tid; e < r * r; e += nt) {
+    const int i = e / r, j = e % r;
+    if (i < j) {
+      const double2 x = B[i * LD + j], y = B[j * LD + i];
+      const double2 h = cmake<double2>(0.5 * (x.x + y.x), 0.5 * (x.y - y.y));
+      B[i * LD + j] = h;
+      B[j * LD + i] = cmake<double2>(h.x, -h.y);
+    } else if (i == j) {
+      B[i * LD + i].y = 0.0;
+    }
+  }
+  __syncthreads();
+
+  // 4. Householder tridiagonalisation of H3 (r x r)
+  for (int k = 0; k + 2 < r; ++k) {
+    const int t = r - k - 1;
+    if (warp == 0) {
+      double sig = 0.0;
+      for (int i = lane; i < t; i += 32) {
+        const double2 x = B[(k + 1 + i) * LD + k];
+        sig += x.x * x.x + x.y * x.y;
+      }
+      sig = warp_sum_d(sig);
+      if (lane == 0) {
+        const double2 x0 = B[(k + 1) * LD + k];
+        const double ax0 = hypot(x0.x, x0.y);
+        if (sig == 0.0) {
+          s_tau = 0.0;
+        } else {
+          const double2 ph = ax0 > 0.0 ? cmake<double2>(x0.x / ax0, x0.y / ax0) : cmake<double2>(1.0, 0.0);
+          const double nrm = sqrt(sig);
+          s_alpha = cmake<double2>(-ph.x * nrm, -ph.y * nrm);
+          const double2 v0 = csub(x0, s_alpha);
+          const double vn2 = sig - ax0 * ax0 + v0.x * v0.x + v0.y * v0.y;
+          s_tau = 2.0 / vn2;
+          vv[0] = v0;
+        }
+      }
+    }
+    __syncthreads();
+    const double tk = s_tau;
+    if (tid == 0) tau[k] = tk;
+    if (tk == 0.0) {
+      for (int i = tid; i < t; i += nt) Vh[k * LD + i] = cmake<double2>(0.0, 0.0);
+      __syncthreads();
+      continue;
+    }
+    for (int i = 1 + tid; i < t; i += nt) vv[i] = B[(k + 1 + i) * LD + k];
+    __syncthreads();
+    for (int i = tid; i < t; i += nt) Vh[k * LD + i] = vv[i];
+    // p = tau B_sub v: one warp per row, lanes across the row
+    for (int i = warp; i < t; i += nwarp) {
+      const double2 *row = B + (k + 1 + i) * LD + k + 1;
+      double2 s = cmake<double2>(0.0, 0.0);
+      for (int j = lane; j < t; j += 32) s = cadd(s, cmul(row[j], vv[j]));
+      s = warp_sum_d2(s);
+      if (lane == 0) pv[i] = cscale(s, tk);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double2 s = cmake<double2>(0.0, 0.0);
+      for (int i = lane; i < t; i += 32) s = cadd(s, cmulc(vv[i], pv[i]));
+      s = warp_sum_d2(s);
+      if (lane == 0) s_K = cscale(s, 0.5 * tk);
+    }
+    __syncthreads();
+    const double2 K = s_K;
+    for (int i = tid; i < t; i += nt) pv[i] = csub(pv[i], cmul(K, vv[i]));
+    __syncthreads();
+    for (int e = tid; e < t * t; e += nt) {
+      const int i = e / t, j = e % t;
+      const double2 vi = vv[i], qi = pv[i], vj = vv[j], qj = pv[j];
+      // v_i conj(q_j) + q_i conj(v_j)
+      const double2 upd = cadd(cmake<double2>(vi.x * qj.x + vi.y * qj.y, vi.y * qj.x - vi.x * qj.y),
+                               cmake<double2>(qi.x * vj.x + qi.y * vj.y, qi.y * vj.x - qi.x * vj.y));
+      B[(k + 1 + i) * LD + k + 1 + j] = csub(B[(k + 1 + i) * LD + k + 1 + j], upd);
+    }
+    for (int i = tid; i < t; i += nt) {
+      const double2 val = i == 0 ? s_alpha : cmake<double2>(0.0, 0.0);
+      B[(k + 1 + i) * LD + k] = val;
+      B[k * LD + k + 1 + i] = cmake<double2>(val.x, -val.y);
+    }
+    __syncthreads();
+  }
+
+  // real tridiagonal T = Phi^H T_c Phi: moduli and unit phases in parallel, the phase product on one thread
+  for (int i = tid; i < r; i += nt) {
+    dd[i] = B[i * LD + i].x;
+    d32[i] = (float)dd[i];
+    if (i + 1 < r) {
+      const double2 c = B[(i + 1) * LD + i];
+      const double ac = hypot(c.x, c.y);
+      ee[i] = ac;
+      e2[i] = ac * ac;
+      e232[i] = (float)(ac * ac);
+      pv[i] = ac > 0.0 ? cmake<double2>(c.x / ac, c.y / ac) : cmake<double2>(1.0, 0.0);
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double gl = HUGE_VAL, gu = -HUGE_VAL, tn = 0.0, emax2 = 0.0;
+    for (int i = lane; i < r; i += 32) {
+      const double off = (i > 0 ? ee[i - 1] : 0.0) + (i + 1 < r ? ee[i] : 0.0);
+      gl = fmin(gl, dd[i] - off);
+      gu = fmax(gu, dd[i] + off);
+      tn = fmax(tn, fabs(dd[i]) + off);
+      if (i + 1 < r) emax2 = fmax(emax2, e2[i]);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      gl = fmin(gl, __shfl_xor_sync(0xffffffffu, gl, o));
+      gu = fmax(gu, __shfl_xor_sync(0xffffffffu, gu, o));
+      tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+      emax2 = fmax(emax2, __shfl_xor_sync(0xffffffffu, emax2, o));
+    }
+    if (lane == 0) {
+      const double pm = 1e-300 * fmax(1.0, emax2);
+      s_pivmin = pm;
+      s_tn = tn;
+      s_gl = gl - RR_EPS * 2.0 * tn - pm;
+      s_gu = gu + RR_EPS * 2.0 * tn + pm;
+    }
+  } else if (tid == 32) {
+    phi[0] = cmake<double2>(1.0, 0.0);
+    for (int i = 0; i + 1 < r; ++i) phi[i + 1] = cmul(phi[i], pv[i]);
+  }
+  __syncthreads();
+
+  // 5. bisection: eigenvalue j (ascending) of T on lanes (2j, 2j+1)
+  const int mm = m < r ? m : r;
+  if (tid < ((2 * mm + 31) & ~31)) {
+    const int j = tid >> 1, side = tid & 1;
+    const bool active = j < mm;
+    const int jj = active ? j : 0;
+    const double tn = s_tn, pivmin = s_pivmin;
+    // FP32 bracket
+    const float tn32 = (float)tn;
+    const float pivmin32 = 1e-30f * fmaxf(1.0f, tn32 * tn32);
+    float lo32 = (float)s_gl, hi32 = (float)s_gu;
+    lo32 -= fabsf(lo32) * 1e-6f + FLT_MIN;
+    hi32 += fabsf(hi32) * 1e-6f + FLT_MIN;
+    trisect<float>(d32, e232, r, pivmin32, jj, side, active, lo32, hi32, 32.0f * FLT_EPSILON * tn32, 0.0f, 60);
+    // widen, verify in FP64 (one count per lane), fall back to the Gershgorin interval
+    const double margin = 16.0 * FLT_EPSILON * tn + pivmin;
+    double lo = (double)lo32 - margin, hi = (double)hi32 + margin;
+    const int cnt = active ? sturm_count<double>(dd, e2, r, side ? hi : lo, pivmin) : 0;
+    const int cnt_o = __shfl_xor_sync(0xffffffffu, cnt, 1);
+    const int clo = side ? cnt_o : cnt, chi = side ? cnt : cnt_o;
+    if (!(clo <= jj && chi > jj)) {
+      lo = s_gl;
+      hi = s_gu;
+    }
+    trisect<double>(dd, e2, r, pivmin, jj, side, active, lo, hi, RR_EPS * tn, 2.0 * RR_EPS, 200);
+    if (active && side == 0) w[j] = 0.5 * (lo + hi);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int mp = 0;
+    for (int j = 0; j < mm; ++j) {
+      pos[j] = (j > 0 && w[j] - w[j - 1] <= RR_CLUSTER_REL * s_tn) ? pos[j - 1] + 1 : 0;
+      mp = pos[j] > mp ? pos[j] : mp;
+    }
+    s_maxpos = mp;
+  }
+  __syncthreads();
+
+  // 6. inverse iteration, cluster position by cluster position; Z (r x mm, column-major by j) lives in B
+  const int maxpos = s_maxpos;
+  for (int round = 0; round <= maxpos; ++round) {
+    for (int j = tid; j < mm; j += nt) {
+      if (pos[j] != round) continue;
+      double work[5 * RR_MAXN];
+      double *z = Z + (long)j * r;
+      tri_factor(dd, ee, r, w[j], RR_EPS * s_tn + 1e-300, work);
+      for (int i = 0; i < r; ++i) {  // a fixed start vector with no special structure
+        const unsigned hsh = (unsigned)i * 2654435761u + (unsigned)j * 40503u + 12345u;
+        z[i] = 1.0 + 0.37 * ((double)((hsh >> 12) & 1023u) / 512.0 - 1.0);
+      }
+      for (int step = 0; step < 3; ++step) {
+        tri_solve(work, r, z);
+        for (int q = j - pos[j]; q < j; ++q) {  // earlier members of the cluster
+          const double *zq = Z + (long)q * r;
+          double dot = 0.0;
+          for (int i = 0; i < r; ++i) dot += zq[i] * z[i];
+          for (int i = 0; i < r; ++i) z[i] -= dot * zq[i];
+        }
+        double nrm = 0.0;
+        for (int i = 0; i < r; ++i) nrm += z[i] * z[i];
+        nrm = 1.0 / sqrt(nrm);
+        for (int i = 0; i < r; ++i) z[i] *= nrm;
+      }
+    }
+    __syncthreads();
+  }
+
+  // 7. back-transformation, one warp per Ritz vector held in registers (lane l owns rows l and l + 32):
+  // y = Q Phi z (reflectors applied last to first), then L^H x = y, coef = D P x
+  double2 *out = coefg + (long)b * n * m;
+  for (int j = warp; j < m; j += nwarp) {
+    double2 y0 = cmake<double2>(0.0, 0.0), y1 = y0;
+    const int i0 = lane, i1 = lane + 32;
+    if (j < mm) {
+      const double *z = Z + (long)j * r;
+      if (i0 < r) y0 = cscale(phi[i0], z[i0]);
+      if (i1 < r) y1 = cscale(phi[i1], z[i1]);
+      for (int k = r - 3; k >= 0; --k) {
+        const double tk = tau[k];
+        if (tk == 0.0) continue;
+        // rows k+1 .. r-1 hold v_k[row - k - 1]
+        double2 s = cmake<double2>(0.0, 0.0);
+        if (i0 > k && i0 < r) s = cadd(s, cmulc(Vh[k * LD + i0 - k - 1], y0));
+        if (i1 > k && i1 < r) s = cadd(s, cmulc(Vh[k * LD + i1 - k - 1], y1));
+        s = cscale(warp_sum_d2(s), tk);
+        if (i0 > k && i0 < r) y0 = csub(y0, cmul(Vh[k * LD + i0 - k - 1], s));
+        if (i1 > k && i1 < r) y1 = csub(y1, cmul(Vh[k * LD + i1 - k - 1], s));
+      }
+      // L^H x = y (upper triangular), rows from the last
+      for (int i = r - 1; i >= 0; --i) {
+        double2 s = cmake<double2>(0.0, 0.0);
+        if (i0 > i && i0 < r) s = cadd(s, cmulc(A[i0 * LD + i], y0));
+        if (i1 > i && i1 < r) s = cadd(s, cmulc(A[i1 * LD + i], y1));
+        s = warp_sum_d2(s);
+        if (i0 == i) y0 = cscale(csub(y0, s), dinv[i]);
+        if (i1 == i) y1 = cscale(csub(y1, s), dinv[i]);
+      }
+    }
+    for (int i = lane; i < n; i += 32) out[i * m + j] = cmake<double2>(0.0, 0.0);
+    __syncwarp();
+    if (j < mm) {
+      if (i0 < r) out[perm[i0] * m + j] = cscale(y0, dsc[perm[i0]]);
+      if (i1 < r) out[perm[i1] * m + j] = cscale(y1, dsc[perm[i1]]);
+    }
+    if (lane == 0) thetag[(long)b * m + j] = j < mm ? w[j] : 0.0;
+  }
+  if (rankg && tid == 0) rankg[b] = r;
+}
+
+}  // namespace
+
+int launch_rr(int nb, int n, int m, const void *G, const void *H, double drop, double *theta, void *coef, int *rank,
+              cudaStream_t st, const int *act) {
+  if (nb == 0) return PC_OK;
+  if (n > RR_MAXN || m > n) {
+    set_error("rayleigh_ritz: need m <= n <= %d", RR_MAXN);
+    return PC_EINVAL;
+  }
+  static bool configured = false;
+  if (!configured) {
+    PC_CK(cudaFuncSetAttribute(rr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)rr_smem(RR_MAXN, RR_MAXN)));
+    configured = true;
+  }
+  rr_kernel<<<nb, RR_THREADS, rr_smem(n, m), st>>>(static_cast<const double2 *>(G), static_cast<const double2 *>(H),
+                                                    n, m, drop, theta, static_cast<double2 *>(coef), rank, act);
+  PC_CK_LAUNCH();
+  return PC_OK;
+}
+
+}  // namespace pc
