@@ -45,6 +45,32 @@ def load_peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Double-float arithmetic (mixed_df.cu): one complex multiply-add (8 FP64-equivalent flops) is 4 products
+# (mul + 3 fma + 3 for the renormalisation = 7 FP32 operations each) and 4 sums (11 each) = 72 FP32 operations,
+# i.e. 9 FP32 operations per FP64-equivalent flop; its ALU peak in FP64-equivalent flops is the FP32 peak / 9.
+DF_OPS_PER_FLOP = 9.0
+
+
+def stage_roofline(stage, d, precision, peaks, src):
+    """Roofline entry for one stage: algorithmic work per launch / average event time of a launch."""
+    calls = max(d["calls"], 1)
+    t = d["ms"] / calls / 1e3
+    if precision == "fp64" or stage in ("rr", "recompute"):
+        achieved = d["flops"] / calls / t / 1e12
+        return {"bound": "alu", "kernel": stage, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (FP64 CUDA cores)"}
+    if stage == "dfloat":
+        achieved = d["flops"] / calls / t / 1e12
+        peak = FP32_PEAK_TFLOPS / DF_OPS_PER_FLOP
+        return {"bound": "alu", "kernel": stage, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "derived: FP32 peak (152 SMs x 128 lanes x 2 x 2.07 GHz) / 9 FP32 ops per "
+                               "double-float flop"}
+    achieved = d["bytes"] / calls / t / 1e9
+    peak = float(peaks["hbm_gbs"])
+    return {"bound": "hbm", "kernel": stage, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)"}
 
 
 def dist_init():
@@ -236,7 +262,11 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
+                    help="mixed: the chosen precision (complex64 search directions, FP64 block via double-float); "
+                         "fp64: the plain FP64 solve")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the plain-FP64 comparison solve reported beside the chosen precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
                     help="weak: every rank solves the whole path (independent replicas); strong: the path's k-points "
@@ -298,6 +328,7 @@ def main():
     total_k = nk * ws if args.scaling == "weak" else len(wl.workload_fcc_32().kpts)
     value = total_k / (ms_step_max / 1e3)
     mean_iters = float(np.mean(np.concatenate(iters)))
+    max_iters = int(np.max(np.concatenate(iters)))
 
     # ---- end to end through the public API with host buffers: setup (eps H2D) + solve (evals D2H)
     barrier(dist)
@@ -312,24 +343,37 @@ def main():
     h2d = eps.nbytes + w.kpts.nbytes
     d2h = o2["evals"].nbytes + o2["iters"].nbytes + o2["resid"].nbytes
 
-    # ---- roofline of the dominant stage
+    # ---- roofline of the dominant stage (and of every stage, for reference)
     peaks, src = load_peaks()
     dom = max(st, key=lambda k: st[k]["ms"])
-    d = st[dom]
-    per_launch_ms = d["ms"] / max(d["calls"], 1)
-    if args.precision == "fp64" or dom in ("gram", "update", "rr"):
-        achieved = d["flops"] / max(d["calls"], 1) / (per_launch_ms / 1e3) / 1e12
-        peak = FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x FP64 FMA/clk x 2 x 2.07 GHz (FP64 CUDA-core, the path's unit)"}
-    else:
-        achieved = d["bytes"] / max(d["calls"], 1) / (per_launch_ms / 1e3) / 1e9
-        peak = float(peaks["hbm_gbs"])
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": src}
+    roof = stage_roofline(dom, st[dom], args.precision, peaks, src)
+    stage_roofs = {k: {kk: v for kk, v in stage_roofline(k, st[k], args.precision, peaks, src).items()
+                       if kk in ("bound", "achieved", "unit", "frac")}
+                   for k in st if st[k]["calls"] > 0}
+
+    # ---- the plain FP64 solve of the same workload, for the metric's comparison (fewer steps: ~13 s each)
+    fp64_cmp = None
+    if args.precision == "mixed" and not args.no_fp64_compare:
+        s64 = pc.Solver(w.N, eps, stream=stream.cuda_stream, precision=pc.pc.PC_PREC_FP64)
+        s64.solve(w.kpts, w.nbands, w.tol)
+        barrier(dist)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        o64 = s64.solve(w.kpts, w.nbands, w.tol)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = max_over_ranks(f0.elapsed_time(f1), dist)
+        ev_m, ev_64 = out["evals"], o64["evals"]
+        fp64_cmp = {"value": total_k / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "steps": 1, "warmup": 1,
+                    "mean_lobpcg_iterations": float(np.mean(o64["iters"])), "status": int(o64["status"]),
+                    "max_rel_eval_diff_vs_chosen": float(np.max(np.abs(ev_m - ev_64) / np.abs(ev_64))),
+                    "speedup_of_chosen": value / (total_k / (ms64 / 1e3))}
+        s64.close()
     sten = st["stencil"]
     sten_gbs = sten["bytes"] / max(sten["ms"], 1e-9) / 1e6
+    # stage times are CUDA-event intervals on the stream that ran them; the solve's two k-point groups run on two
+    # streams, so stage times of different groups overlap and their sum can exceed the wall time
     stages = {k: {"ms_per_step": v["ms"] / args.steps, "calls_per_step": v["calls"] / args.steps,
                   "share": v["ms"] / max(sum(x["ms"] for x in st.values()), 1e-9)} for k, v in st.items()}
     launches = int(sum(v["kernels"] for v in st.values()))
@@ -341,9 +385,12 @@ def main():
                                     "10 bands, 40 k-points Gamma-X-W-K-Gamma-L, tol 1e-6, all k-points in one "
                                     "batched solve"),
                        "precision": args.precision, "nk_per_gpu": nk, "nbands": w.nbands, "tol": w.tol,
-                       "mean_lobpcg_iterations": mean_iters, "status": max(statuses),
+                       "mean_lobpcg_iterations": mean_iters, "max_lobpcg_iterations": max_iters,
+                       "status": max(statuses),
                        "cache": "inputs larger than L2 (search blocks ~9 GB per GPU), no flush"},
             "roofline": roof,
+            "fp64_comparison": fp64_cmp,
+            "stage_rooflines": stage_roofs,
             "stencil": {"achieved_gbs": sten_gbs, "peak_gbs": float(peaks["hbm_gbs"]),
                         "frac": sten_gbs / float(peaks["hbm_gbs"]),
                         "note": "algorithmic bytes (read X, write Op X, M0 once per launch) / event time"},

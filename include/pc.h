@@ -68,6 +68,9 @@ typedef struct {
     int maxiter;           /* LOBPCG iteration cap per k-point and gamma-doubling round (default 400) */
     int max_doublings;     /* Algorithm 4.1 gamma doublings cap (default 8) */
     uint64_t seed;         /* seed of the counter-based initial blocks */
+    int groups;            /* PC_PREC_MIXED: k-point groups iterated on separate streams so that one group's
+                              latency-bound steps (Rayleigh-Ritz, host decisions) overlap the other's kernels;
+                              0 (default): 2 when there are at least 8 k-points, else 1 */
 } pc_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -118,7 +121,8 @@ const char *pc_last_error(void);
 #define PC_STAGE_RESIDUAL 5  /* a5: residual and column norms */
 #define PC_STAGE_RECOMPUTE 6 /* a6: Algorithm 4.1 norms */
 #define PC_STAGE_OTHER 7     /* initial block, k = 0 projection */
-#define PC_NSTAGES 8
+#define PC_STAGE_DFLOAT 8    /* mixed solve, phase 2: double-float Op X, X-X Gram block and X update */
+#define PC_NSTAGES 9
 
 typedef struct {
     long calls;    /* stage invocations */

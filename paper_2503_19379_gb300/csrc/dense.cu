@@ -136,13 +136,13 @@ __global__ void __launch_bounds__(256) gram_tile_partial_kernel(const cplx<T> *_
 }
 
 __global__ void gram_reduce_kernel(const double2 *__restrict__ part, int nchunk, int p, int q,
-                                   const int *__restrict__ act, double2 *__restrict__ G) {
+                                   const int *__restrict__ act, double2 *__restrict__ G, long sg) {
   const int bi = blockIdx.x;
   const int b = act ? act[bi] : bi;
   for (int i = threadIdx.x; i < p * q; i += blockDim.x) {
     double2 s = cmake<double2>(0.0, 0.0);
     for (int c = 0; c < nchunk; ++c) s = cadd(s, part[((long)bi * nchunk + c) * p * q + i]);
-    G[(long)b * p * q + i] = s;
+    G[(long)b * sg + i] = s;
   }
 }
 
@@ -157,10 +157,10 @@ size_t gram_scratch_bytes(int nb, long L, int p, int q) {
 }
 
 int launch_gram(int nb, long L, int p, int q, int dtype, const void *A, long sa, const void *B, long sb, void *G,
-                void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc) {
+                void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc, long sg) {
   if (nb == 0 || p == 0 || q == 0) return PC_OK;
   if (dtype == PC_C64) {
-    const int rc = launch_gram_tc(nb, L, p, q, A, sa, B, sb, G, scratch, scratch_bytes, st, act, nb_alloc);
+    const int rc = launch_gram_tc(nb, L, p, q, A, sa, B, sb, G, scratch, scratch_bytes, st, act, nb_alloc, sg);
     if (rc != PC_EUNSUPPORTED) return rc;
   }
   const int nchunk = gram_chunks(nb, L);
@@ -186,7 +186,7 @@ int launch_gram(int nb, long L, int p, int q, int dtype, const void *A, long sa,
     gram_partial_kernel<float><<<dim3(nchunk, 1, nb), 256, 0, st>>>(
         static_cast<const float2 *>(A), sa, static_cast<const float2 *>(B), sb, L, p, q, chunk, part, act);
   PC_CK_LAUNCH();
-  gram_reduce_kernel<<<nb, 256, 0, st>>>(part, nchunk, p, q, act, static_cast<double2 *>(G));
+  gram_reduce_kernel<<<nb, 256, 0, st>>>(part, nchunk, p, q, act, static_cast<double2 *>(G), sg > 0 ? sg : (long)p * q);
   PC_CK_LAUNCH();
   return PC_OK;
 }
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(256) gram_pair_partial_kernel(const cplx<T> *_
 // sums the chunks of the upper triangle and mirrors it: G[j][i] = conj(G[i][j])
 __global__ void gram_pair_reduce_kernel(const double2 *__restrict__ partG, const double2 *__restrict__ partH,
                                         int nchunk, int p, const int *__restrict__ act, double2 *__restrict__ G,
-                                        double2 *__restrict__ H) {
+                                        double2 *__restrict__ H, long sgb) {
   const int bi = blockIdx.x;
   const int b = act ? act[bi] : bi;
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
@@ -288,10 +288,10 @@ __global__ void gram_pair_reduce_kernel(const double2 *__restrict__ partG, const
       sg.y = 0.0;
       sh.y = 0.0;
     }
-    G[(long)b * p * p + i * p + j] = sg;
-    H[(long)b * p * p + i * p + j] = sh;
-    G[(long)b * p * p + j * p + i] = cmake<double2>(sg.x, -sg.y);
-    H[(long)b * p * p + j * p + i] = cmake<double2>(sh.x, -sh.y);
+    G[(long)b * sgb + i * p + j] = sg;
+    H[(long)b * sgb + i * p + j] = sh;
+    G[(long)b * sgb + j * p + i] = cmake<double2>(sg.x, -sg.y);
+    H[(long)b * sgb + j * p + i] = cmake<double2>(sh.x, -sh.y);
   }
 }
 
@@ -300,14 +300,15 @@ size_t gram_pair_scratch_bytes(int nb, long L, int p) {
 }
 
 void launch_gram_pair_reduce(int nb, int nchunk, int p, const double2 *part, const int *act, void *G, void *H,
-                             cudaStream_t st) {
+                             cudaStream_t st, long sg) {
   gram_pair_reduce_kernel<<<nb, 256, 0, st>>>(part, part + (size_t)nb * nchunk * p * p, nchunk, p, act,
-                                              static_cast<double2 *>(G), static_cast<double2 *>(H));
+                                              static_cast<double2 *>(G), static_cast<double2 *>(H),
+                                              sg > 0 ? sg : (long)p * p);
 }
 
 void launch_gram_reduce(int nb, int nchunk, int p, int q, const double2 *part, const int *act, void *G,
-                        cudaStream_t st) {
-  gram_reduce_kernel<<<nb, 256, 0, st>>>(part, nchunk, p, q, act, static_cast<double2 *>(G));
+                        cudaStream_t st, long sg) {
+  gram_reduce_kernel<<<nb, 256, 0, st>>>(part, nchunk, p, q, act, static_cast<double2 *>(G), sg > 0 ? sg : (long)p * q);
 }
 
 template <typename T>
@@ -331,7 +332,7 @@ static int launch_gram_pair_t(int nb, long L, int p, const void *S, const void *
 }
 
 int launch_gram_pair(int nb, long L, int p, int dtype, const void *S, const void *AS, long ss, void *G, void *H,
-                     void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc) {
+                     void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc, long sg) {
   if (nb == 0 || p == 0) return PC_OK;
   if (p > 64) {
     set_error("gram_pair: at most 64 columns");
@@ -342,7 +343,7 @@ int launch_gram_pair(int nb, long L, int p, int dtype, const void *S, const void
     return PC_EINVAL;
   }
   if (dtype == PC_C64) {
-    const int rc = launch_gram_pair_tc(nb, L, p, S, AS, ss, G, H, scratch, scratch_bytes, st, act, nb_alloc);
+    const int rc = launch_gram_pair_tc(nb, L, p, S, AS, ss, G, H, scratch, scratch_bytes, st, act, nb_alloc, sg);
     if (rc != PC_EUNSUPPORTED) return rc;
   }
   const int nchunk = gram_chunks(nb, L);
@@ -353,7 +354,8 @@ int launch_gram_pair(int nb, long L, int p, int dtype, const void *S, const void
                             : launch_gram_pair_t<float>(nb, L, p, S, AS, ss, part, nchunk, chunk, st, act);
   if (rc) return rc;
   gram_pair_reduce_kernel<<<nb, 256, 0, st>>>(part, part + (size_t)nb * nchunk * p * p, nchunk, p, act,
-                                              static_cast<double2 *>(G), static_cast<double2 *>(H));
+                                              static_cast<double2 *>(G), static_cast<double2 *>(H),
+                                              sg > 0 ? sg : (long)p * p);
   PC_CK_LAUNCH();
   return PC_OK;
 }
@@ -482,6 +484,11 @@ __global__ void residual_reduce_kernel(const double *__restrict__ part, int nchu
   }
 }
 
+void launch_residual_reduce(int nb, int nchunk, int m, const double *part, const int *act, double *norms,
+                            cudaStream_t st) {
+  residual_reduce_kernel<<<nb, 64, 0, st>>>(part, nchunk, m, act, norms);
+}
+
 static int residual_chunks(long L) { return (int)std::min<long>(32, std::max<long>(1, L / 4096)); }
 
 size_t residual_scratch_bytes(int nb, long L, int m) {
@@ -600,40 +607,48 @@ int launch_residual_mixed(int nb, long L, int m, int dtype_x, const void *X, lon
   return PC_OK;
 }
 
-// Completes the Rayleigh-Ritz pencil of the mixed solve (n = m + nq columns [X | Q]):
-//   H[i][m+j] = theta_i G[i][m+j] + (R^H Q)[i][j], mirrored, from AX = X Theta + R and Op Hermitian, so that the
-//   coupling never multiplies X by the large AQ in complex64; and, for k-points whose block X is held in FP64
-//   (phase[b] == 2), G[:m,:m] and H[:m,:m] from the FP64 products GX, HX.
+// Completes the Rayleigh-Ritz pencil of the mixed solve (n = m + nq columns [X | Q]) from RS = R^H [X | Q]
+// ([nb][m][n]) and AX = X Theta + R (Op Hermitian), so that no product multiplies X by the large AQ in complex64:
+//   H[i][m+j] = theta_i G[i][m+j] + (R^H Q)[i][j], mirrored;
+// and, for k-points whose block X is held in FP64 (phase[b] == 2), G[:m,:m] = GX (the FP64 X^H X) and
+//   H[:m,:m] = the Hermitian part of (theta_i GX[i][j] + (R^H X)[i][j]).
 __global__ void rr_patch_kernel(double2 *__restrict__ G, double2 *__restrict__ H, int n, int m,
-                                const double2 *__restrict__ RQ, const double *__restrict__ theta,
-                                const double2 *__restrict__ GX, const double2 *__restrict__ HX,
-                                const int *__restrict__ phase, const int *__restrict__ act) {
+                                const double2 *__restrict__ RS, const double *__restrict__ theta,
+                                const double2 *__restrict__ GX, const int *__restrict__ phase,
+                                const int *__restrict__ act, long sg, long srs) {
   const int b = act ? act[blockIdx.x] : (int)blockIdx.x;
-  double2 *Gb = G + (long)b * n * n, *Hb = H + (long)b * n * n;
+  double2 *Gb = G + (long)b * sg, *Hb = H + (long)b * sg;
+  const double2 *RSb = RS + (long)b * srs;
+  const double *th = theta + (long)b * m;
   const int nq = n - m;
   for (int e = threadIdx.x; e < m * nq; e += blockDim.x) {
     const int i = e / nq, j = e - i * nq;
-    const double th = theta[(long)b * m + i];
-    const double2 g = Gb[i * n + m + j], rq = RQ[(long)b * m * nq + e];
-    const double2 h = cmake<double2>(th * g.x + rq.x, th * g.y + rq.y);
+    const double2 g = Gb[i * n + m + j], rq = RSb[i * n + m + j];
+    const double2 h = cmake<double2>(th[i] * g.x + rq.x, th[i] * g.y + rq.y);
     Hb[i * n + m + j] = h;
     Hb[(m + j) * n + i] = cmake<double2>(h.x, -h.y);
   }
   if (phase && phase[b] == 2) {
+    const double2 *GXb = GX + (long)b * m * m;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
       const int i = e / m, j = e - i * m;
-      Gb[i * n + j] = GX[(long)b * m * m + e];
-      Hb[i * n + j] = HX[(long)b * m * m + e];
+      const double2 gij = GXb[i * m + j], gji = GXb[j * m + i];
+      const double2 rij = RSb[i * n + j], rji = RSb[j * n + i];
+      // M = Theta GX + R^H X; H = (M + M^H) / 2
+      const double2 mij = cmake<double2>(th[i] * gij.x + rij.x, th[i] * gij.y + rij.y);
+      const double2 mji = cmake<double2>(th[j] * gji.x + rji.x, th[j] * gji.y + rji.y);
+      Gb[i * n + j] = gij;
+      Hb[i * n + j] = cmake<double2>(0.5 * (mij.x + mji.x), 0.5 * (mij.y - mji.y));
     }
   }
 }
 
-int launch_rr_patch(int nb, int n, int m, void *G, void *H, const void *RQ, const double *theta, const void *GX,
-                    const void *HX, const int *phase, cudaStream_t st, const int *act) {
+int launch_rr_patch(int nb, int n, int m, void *G, void *H, const void *RS, const double *theta, const void *GX,
+                    const int *phase, cudaStream_t st, const int *act, long sg, long srs) {
   if (nb == 0) return PC_OK;
   rr_patch_kernel<<<nb, 256, 0, st>>>(static_cast<double2 *>(G), static_cast<double2 *>(H), n, m,
-                                      static_cast<const double2 *>(RQ), theta, static_cast<const double2 *>(GX),
-                                      static_cast<const double2 *>(HX), phase, act);
+                                      static_cast<const double2 *>(RS), theta, static_cast<const double2 *>(GX),
+                                      phase, act, sg > 0 ? sg : (long)n * n, srs > 0 ? srs : (long)m * n);
   PC_CK_LAUNCH();
   return PC_OK;
 }
@@ -909,7 +924,7 @@ extern "C" int pc_gram_pair_noalloc(int nb, long L, int p, int dtype, const void
                         : launch_gram_pair_t<float>(nb, L, p, S, AS, ss, part, nchunk, chunk, st, nullptr);
   if (rc) return rc;
   gram_pair_reduce_kernel<<<nb, 256, 0, st>>>(part, part + (size_t)nb * nchunk * p * p, nchunk, p, nullptr,
-                                              static_cast<double2 *>(G), static_cast<double2 *>(H));
+                                              static_cast<double2 *>(G), static_cast<double2 *>(H), (long)p * p);
   PC_CK_LAUNCH();
   return PC_OK;
 }

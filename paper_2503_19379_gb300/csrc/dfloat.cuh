@@ -69,6 +69,26 @@ __device__ __forceinline__ cdf cdf_mulc(cdf a, cdf b) {
   return cdf{df_add(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_sub(df_mul(a.re, b.im), df_mul(a.im, b.re))};
 }
 __device__ __forceinline__ cdf cdf_scale(cdf a, df s) { return cdf{df_mul(a.re, s), df_mul(a.im, s)}; }
+
+// s += a b for double-float a, b, s: the product's rounding error is exact via fma, the sum via two_sum, then one
+// renormalisation (15 FP32 operations); about 2^-44 relative per step
+__device__ __forceinline__ void df_mac(df &s, df a, df b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float t = s.hi + p;
+  const float bb = t - s.hi;
+  const float err = (s.hi - (t - bb)) + (p - bb);
+  s = quick_two_sum(t, err + (s.lo + e));
+}
+// s += a b for complex double-float
+__device__ __forceinline__ void cdf_mac(cdf &s, cdf a, cdf b) {
+  df_mac(s.re, a.re, b.re);
+  df_mac(s.re, df_neg(a.im), b.im);
+  df_mac(s.im, a.re, b.im);
+  df_mac(s.im, a.im, b.re);
+}
 __device__ __forceinline__ cdf cdf_scale2(cdf a, float s) { return cdf{df_scale2(a.re, s), df_scale2(a.im, s)}; }
 
 }  // namespace pc

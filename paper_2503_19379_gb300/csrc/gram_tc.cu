@@ -161,6 +161,7 @@ struct TcArgs {
   int PB, QB;           // padded row counts (multiples of 8); the B operand is rows [0, N) of the operand region
   int N;                // MMA N: QB + PB when pair (B = [B1; A]), else QB (multiple of 16, <= 128)
   int pair;             // pair: outputs G = A^H A and H = A^H B1 (upper triangles); else A^H B1 (p x q)
+  int transpose;        // general mode: write the conjugate transpose (B1^H A, q x p) instead
   int ns;               // staging stages
   int ktiles, tpc, nchunk;
   int nc;                // accumulator columns per slot (N rounded up to 32)
@@ -392,7 +393,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a, 
               if (j < a.N && jj < a.p && ii <= jj)
                 (isH ? a.partH : a.partG)[2 * (oG + (long)ii * a.p + jj) + im] = val;
             } else if (j < a.q) {
-              a.partH[2 * (oG + (long)ii * a.q + j) + im] = val;
+              if (a.transpose)
+                a.partH[2 * (oG + (long)j * a.p + ii) + im] = im ? -val : val;
+              else
+                a.partH[2 * (oG + (long)ii * a.q + j) + im] = val;
             }
           }
         }
@@ -470,7 +474,8 @@ bool make_map(CUtensorMap *map, const void *base, long L, long rows, int box_row
 }
 
 int launch_tc(int nb, int nb_alloc, long L, int p, int q, bool pair, const void *A, long sa, const void *B, long sb,
-              double2 *part, size_t scratch_bytes, cudaStream_t st, const int *act, int *nchunk_out) {
+              double2 *part, size_t scratch_bytes, cudaStream_t st, const int *act, int *nchunk_out,
+              bool transpose = false) {
   TcArgs a{};
   a.cppA = sa / L;
   a.cppB = sb / L;
@@ -481,6 +486,7 @@ int launch_tc(int nb, int nb_alloc, long L, int p, int q, bool pair, const void 
   a.QB = pair ? a.PB : (q + 15) / 16 * 16;
   a.N = pair ? a.QB + a.PB : a.QB;
   a.pair = pair ? 1 : 0;
+  a.transpose = transpose ? 1 : 0;
   a.ktiles = (int)(2 * L / TC_KT);
   int ns = 4;
   while (ns > 2 && tc_smem(a.PB, a.QB, ns) > (size_t)TC_SMEM_MAX) --ns;
@@ -543,28 +549,32 @@ bool tc_shape_ok(long L, int p, int q, const void *A, long sa, const void *B, lo
 // G = S^H S and H = S^H AS (complex64 panels, p <= 64) on the tensor cores; PC_EUNSUPPORTED when the shape or
 // alignment does not fit (the caller then takes the CUDA-core kernel).
 int launch_gram_pair_tc(int nb, long L, int p, const void *S, const void *AS, long ss, void *G, void *H,
-                        void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc) {
+                        void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc, long sg) {
   if (!tc_shape_ok(L, p, p, S, ss, AS, ss)) return PC_EUNSUPPORTED;
   int c = 0;
   double2 *part = static_cast<double2 *>(scratch);
   int rc = launch_tc(nb, nb_alloc > 0 ? nb_alloc : nb, L, p, p, true, S, ss, AS, ss, part, scratch_bytes, st, act,
                      &c);
   if (rc) return rc;
-  launch_gram_pair_reduce(nb, c, p, part, act, G, H, st);
+  launch_gram_pair_reduce(nb, c, p, part, act, G, H, st, sg);
   PC_CK_LAUNCH();
   return PC_OK;
 }
 
 // G = A^H B (complex64, p <= 64 columns of A, q <= 128 of B) on the tensor cores; PC_EUNSUPPORTED as above.
 int launch_gram_tc(int nb, long L, int p, int q, const void *A, long sa, const void *B, long sb, void *G,
-                   void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc) {
+                   void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc, long sg) {
   if (!tc_shape_ok(L, p, q, A, sa, B, sb)) return PC_EUNSUPPORTED;
   int c = 0;
   double2 *part = static_cast<double2 *>(scratch);
-  int rc = launch_tc(nb, nb_alloc > 0 ? nb_alloc : nb, L, p, q, false, A, sa, B, sb, part, scratch_bytes, st, act,
-                     &c);
+  // the wider panel takes the MMA rows (2 x its columns of the 128): B^H A, written conjugate-transposed
+  const bool swap = q > p && q <= 64;
+  int rc = swap ? launch_tc(nb, nb_alloc > 0 ? nb_alloc : nb, L, q, p, false, B, sb, A, sa, part, scratch_bytes, st,
+                            act, &c, true)
+                : launch_tc(nb, nb_alloc > 0 ? nb_alloc : nb, L, p, q, false, A, sa, B, sb, part, scratch_bytes, st,
+                            act, &c);
   if (rc) return rc;
-  launch_gram_reduce(nb, c, p, q, part, act, G, st);
+  launch_gram_reduce(nb, c, p, q, part, act, G, st, sg);
   PC_CK_LAUNCH();
   return PC_OK;
 }

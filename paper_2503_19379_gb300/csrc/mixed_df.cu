@@ -25,6 +25,67 @@ __device__ __forceinline__ cdf dbwd_df(cdf gm, cdf g0, float ih, df kh) {
   return cdf{df_add(df_scale2(a.re, ih), df_mul(kh, s.im)), df_sub(df_scale2(a.im, ih), df_mul(kh, s.re))};
 }
 
+// Residual epilogue of the stencil (the mixed solve's phase 2): instead of AX the kernel writes, per point,
+// r = AX - theta_j X rounded to complex64 (twice: the preconditioner's input slot and the persistent copy used by
+// the Rayleigh-Ritz coupling), complex64 copies of X and AX for the complex64 Gram products, and per-block partial
+// sums of |r|^2 and |x|^2 (FP32 per thread, FP64 per block), reduced per column by residual_reduce.
+struct ResidArgs {
+  const double *theta;  // [nb][m]
+  int m;
+  float2 *R1, *R2, *X32, *AX32;
+  long sr1, sr2, sx32, sax32;
+  double *part;  // [nb][m][blocks per field][2]
+};
+
+__device__ __forceinline__ float2 cdf_round(cdf a) { return make_float2(a.re.hi + a.re.lo, a.im.hi + a.im.lo); }
+
+// writes the three components of one point; returns |r|^2 and |x|^2 contributions
+__device__ __forceinline__ void resid_point(const ResidArgs &ra, int b, int j, long n, long gi, df th, const cdf (&y)[3],
+                                            const cdf (&x)[3], float &sr, float &sxx) {
+  const long L = 3 * n;
+  float2 *r1 = ra.R1 + (long)b * ra.sr1 + (long)j * L, *r2 = ra.R2 + (long)b * ra.sr2 + (long)j * L;
+  float2 *x32 = ra.X32 + (long)b * ra.sx32 + (long)j * L, *ax32 = ra.AX32 + (long)b * ra.sax32 + (long)j * L;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cdf r = cdf_sub(y[c], cdf_scale(x[c], th));
+    const float2 rf = cdf_round(r), xf = make_float2(x[c].re.hi, x[c].im.hi);
+    const long o = c * n + gi;
+    r1[o] = rf;
+    r2[o] = rf;
+    x32[o] = xf;
+    ax32[o] = cdf_round(y[c]);
+    sr += rf.x * rf.x + rf.y * rf.y;
+    sxx += xf.x * xf.x + xf.y * xf.y;
+  }
+}
+
+// block sum of (sr, sxx) into the partial-sum slot of this block
+__device__ __forceinline__ void resid_block_sum(const ResidArgs &ra, float sr, float sxx) {
+  __shared__ double red[2][32];
+  double a = sr, c = sxx;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][w] = a;
+    red[1][w] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0;
+    for (int i = 0; i < nw; ++i) {
+      s0 += red[0][i];
+      s1 += red[1][i];
+    }
+    double *o = ra.part + (((long)blockIdx.z * ra.m + blockIdx.y) * gridDim.x + blockIdx.x) * 2;
+    o[0] = s0;
+    o[1] = s1;
+  }
+}
+
 template <int TX, int TY, int TZ> constexpr size_t op_df_smem_bytes() {
   return sizeof(cdf) * (size_t)(3 * (TZ + 2) * (TY + 2) * (TX + 2) + 3 * (TZ + 1) * (TY + 1) * (TX + 1) +
                                 (TZ + 1) * (TY + 1) * (TX + 1));
@@ -33,11 +94,11 @@ template <int TX, int TY, int TZ> constexpr size_t op_df_smem_bytes() {
 // Same tiling as op_kernel (stencil.cu): a face tile with a one-point halo, e = M0 A' v on the tile grown upward,
 // c = B v on the tile grown downward, then y = A e + gamma B' c. The grid spacing factor ih = N is a power of two,
 // so scaling by it is exact in double-float.
-template <int TX, int TY, int TZ>
+template <int TX, int TY, int TZ, bool RES>
 __global__ void __launch_bounds__(256) op_df_kernel(const double2 *__restrict__ X, long sx, double2 *__restrict__ Y,
                                                     long sy, const double *__restrict__ m0,
                                                     const KParam *__restrict__ kp, const int *__restrict__ act,
-                                                    int logN) {
+                                                    int logN, const ResidArgs ra) {
   constexpr int VX = TX + 2, VY = TY + 2, VZ = TZ + 2;
   constexpr int EX = TX + 1, EY = TY + 1, EZ = TZ + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -95,6 +156,7 @@ __global__ void __launch_bounds__(256) op_df_kernel(const double2 *__restrict__ 
     c[eo] = cc;
   }
   __syncthreads();
+  float sr = 0.f, sxx = 0.f;
   for (int i = threadIdx.x; i < TZ * TY * TX; i += blockDim.x) {
     const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
 #define EE(comp, dz, dy, dx) e[(((comp) * EZ + lz + (dz)) * EY + ly + (dy)) * EX + lx + (dx)]
@@ -110,25 +172,37 @@ __global__ void __launch_bounds__(256) op_df_kernel(const double2 *__restrict__ 
 #undef EE
 #undef CC
     const long gi = ((long)(z0 + lz) << (2 * logN)) + ((long)(y0 + ly) << logN) + x0 + lx;
-    Yb[gi] = cdf_to(y1);
-    Yb[n + gi] = cdf_to(y2);
-    Yb[2 * n + gi] = cdf_to(y3);
+    if constexpr (RES) {
+#define XV(comp) v[(((comp) * VZ + lz + 1) * VY + ly + 1) * VX + lx + 1]
+      const cdf yv[3] = {y1, y2, y3}, xv[3] = {XV(0), XV(1), XV(2)};
+#undef XV
+      resid_point(ra, b, j, n, gi, df_from(ra.theta[(long)b * ra.m + j]), yv, xv, sr, sxx);
+    } else {
+      Yb[gi] = cdf_to(y1);
+      Yb[n + gi] = cdf_to(y2);
+      Yb[2 * n + gi] = cdf_to(y3);
+    }
   }
+  if constexpr (RES) resid_block_sum(ra, sr, sxx);
 }
 
-template <int TX, int TY, int TZ>
-static int launch_op_df_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act) {
+template <int TX, int TY, int TZ, bool RES>
+static int launch_op_df_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act,
+                          const ResidArgs &ra, int *nchunk) {
   constexpr size_t smem = op_df_smem_bytes<TX, TY, TZ>();
   static bool configured = false;
   if (!configured) {
-    PC_CK(cudaFuncSetAttribute(op_df_kernel<TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CK(cudaFuncSetAttribute(op_df_kernel<TX, TY, TZ, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem));
     configured = true;
   }
   const int N = ctx->N;
   dim3 grid((N / TX) * (N / TY) * (N / TZ), m, nb);
-  op_df_kernel<TX, TY, TZ><<<grid, 256, smem, ctx->stream>>>(static_cast<const double2 *>(X), sx,
-                                                              static_cast<double2 *>(Y), sy, ctx->m0d.as<double>(),
-                                                              ctx->kparam.as<KParam>(), act, ctx->logN);
+  *nchunk = (int)grid.x;
+  if (RES && ra.part == nullptr) return PC_OK;  // sizing call
+  op_df_kernel<TX, TY, TZ, RES><<<grid, 256, smem, ctx->stream>>>(static_cast<const double2 *>(X), sx,
+                                                                   static_cast<double2 *>(Y), sy, ctx->m0d.as<double>(),
+                                                                   ctx->kparam.as<KParam>(), act, ctx->logN, ra);
   PC_CK_LAUNCH();
   return PC_OK;
 }
@@ -139,12 +213,12 @@ template <int TX, int TY> constexpr size_t opz_df_smem_bytes() {
   return sizeof(cdf) * (size_t)(2 * 3 * (TY + 2) * (TX + 2) + 2 * 3 * (TY + 1) * (TX + 1) + 2 * (TY + 1) * (TX + 1));
 }
 
-template <int TX, int TY>
+template <int TX, int TY, bool RES>
 __global__ void __launch_bounds__(TX * TY) opz_df_kernel(const double2 *__restrict__ X, long sx,
                                                          double2 *__restrict__ Y, long sy,
                                                          const double *__restrict__ m0,
                                                          const KParam *__restrict__ kp, const int *__restrict__ act,
-                                                         int logN, int ZC) {
+                                                         int logN, int ZC, const ResidArgs ra) {
   constexpr int VX = TX + 2, VY = TY + 2, VP = VX * VY;
   constexpr int EX = TX + 1, EY = TY + 1, EP = EX * EY;
   constexpr int NT = TX * TY;
@@ -216,6 +290,8 @@ __global__ void __launch_bounds__(TX * TY) opz_df_kernel(const double2 *__restri
   make_e(0, zb, 1, 0);
   make_c(0, 0, 1);
   int sv = 1, se = 0, sc = 0;
+  float sr = 0.f, sxx = 0.f;
+  const df th = RES ? df_from(ra.theta[(long)b * ra.m + j]) : df{0.f, 0.f};
   for (int z = zb; z < zb + ZC; ++z) {
     __syncthreads();
     load_v(1 - sv, z + 1);
@@ -238,22 +314,31 @@ __global__ void __launch_bounds__(TX * TY) opz_df_kernel(const double2 *__restri
       cdf y3 = cdf_sub(dfwd_df(e2, e0[EP + eo + 1], ih, kh0), dfwd_df(e1, e0[eo + EX], ih, kh1));
       y3 = cdf_add(y3, cdf_scale(dbwd_df(cm[co], c0, ih, kh2), gam));
       const long gi = (long)z * plane + ((long)(y0 + ly) << logN) + x0 + lx;
-      Yb[gi] = cdf_to(y1);
-      Yb[n + gi] = cdf_to(y2);
-      Yb[2 * n + gi] = cdf_to(y3);
+      if constexpr (RES) {
+        const cdf *v0 = vbuf + sv * 3 * VP;  // plane z
+        const int o = (ly + 1) * VX + lx + 1;
+        const cdf yv[3] = {y1, y2, y3}, xv[3] = {v0[o], v0[VP + o], v0[2 * VP + o]};
+        resid_point(ra, b, j, n, gi, th, yv, xv, sr, sxx);
+      } else {
+        Yb[gi] = cdf_to(y1);
+        Yb[n + gi] = cdf_to(y2);
+        Yb[2 * n + gi] = cdf_to(y3);
+      }
     }
     sv = 1 - sv;
     se = 1 - se;
     sc = 1 - sc;
   }
+  if constexpr (RES) resid_block_sum(ra, sr, sxx);
 }
 
-template <int TX, int TY>
-static int launch_opz_df_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act) {
+template <int TX, int TY, bool RES>
+static int launch_opz_df_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act,
+                           const ResidArgs &ra, int *nchunk) {
   constexpr size_t smem = opz_df_smem_bytes<TX, TY>();
   static bool configured = false;
   if (!configured) {
-    PC_CK(cudaFuncSetAttribute(opz_df_kernel<TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CK(cudaFuncSetAttribute(opz_df_kernel<TX, TY, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = true;
   }
   const int N = ctx->N;
@@ -261,19 +346,52 @@ static int launch_opz_df_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, v
   int ZC = N;
   while (ZC > 4 && tiles * (N / ZC) < 4L * 152 * 4) ZC >>= 1;
   dim3 grid((N / TX) * (N / TY) * (N / ZC), m, nb);
-  opz_df_kernel<TX, TY><<<grid, TX * TY, smem, ctx->stream>>>(static_cast<const double2 *>(X), sx,
-                                                               static_cast<double2 *>(Y), sy, ctx->m0d.as<double>(),
-                                                               ctx->kparam.as<KParam>(), act, ctx->logN, ZC);
+  *nchunk = (int)grid.x;
+  if (RES && ra.part == nullptr) return PC_OK;  // sizing call
+  opz_df_kernel<TX, TY, RES><<<grid, TX * TY, smem, ctx->stream>>>(static_cast<const double2 *>(X), sx,
+                                                                    static_cast<double2 *>(Y), sy, ctx->m0d.as<double>(),
+                                                                    ctx->kparam.as<KParam>(), act, ctx->logN, ZC, ra);
   PC_CK_LAUNCH();
   return PC_OK;
 }
 
+template <bool RES>
+static int op_df_dispatch(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act,
+                          const ResidArgs &ra, int *nchunk) {
+  const int N = ctx->N;
+  if (N >= 32) return launch_opz_df_t<32, 8, RES>(ctx, nb, m, X, sx, Y, sy, act, ra, nchunk);
+  if (N == 16) return launch_op_df_t<16, 4, 4, RES>(ctx, nb, m, X, sx, Y, sy, act, ra, nchunk);
+  return launch_op_df_t<8, 4, 4, RES>(ctx, nb, m, X, sx, Y, sy, act, ra, nchunk);
+}
+
 int launch_apply_op_df(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act) {
   if (nb == 0 || m == 0) return PC_OK;
-  const int N = ctx->N;
-  if (N >= 32) return launch_opz_df_t<32, 8>(ctx, nb, m, X, sx, Y, sy, act);
-  if (N == 16) return launch_op_df_t<16, 4, 4>(ctx, nb, m, X, sx, Y, sy, act);
-  return launch_op_df_t<8, 4, 4>(ctx, nb, m, X, sx, Y, sy, act);
+  int nchunk = 0;
+  return op_df_dispatch<false>(ctx, nb, m, X, sx, Y, sy, act, ResidArgs{}, &nchunk);
+}
+
+size_t op_df_resid_scratch_bytes(pc_ctx *ctx, int nb, int m) {
+  int nchunk = 0;
+  op_df_dispatch<true>(ctx, nb, m, nullptr, 0, nullptr, 0, nullptr, ResidArgs{}, &nchunk);
+  return sizeof(double) * 2 * (size_t)nb * m * nchunk;
+}
+
+int launch_op_df_resid(pc_ctx *ctx, int nb, int m, const void *X, long sx, const double *theta, void *R1, long sr1,
+                       void *R2, long sr2, void *X32, long sx32, void *AX32, long sax32, double *norms, void *scratch,
+                       size_t scratch_bytes, const int *act) {
+  if (nb == 0 || m == 0) return PC_OK;
+  if (op_df_resid_scratch_bytes(ctx, nb, m) > scratch_bytes) {
+    set_error("op_df_resid: scratch too small");
+    return PC_EINVAL;
+  }
+  ResidArgs ra{theta, m, static_cast<float2 *>(R1), static_cast<float2 *>(R2), static_cast<float2 *>(X32),
+               static_cast<float2 *>(AX32), sr1, sr2, sx32, sax32, static_cast<double *>(scratch)};
+  int nchunk = 0;
+  int rc = op_df_dispatch<true>(ctx, nb, m, X, sx, nullptr, 0, act, ra, &nchunk);
+  if (rc) return rc;
+  launch_residual_reduce(nb, nchunk, m, static_cast<const double *>(scratch), act, norms, ctx->stream);
+  PC_CK_LAUNCH();
+  return PC_OK;
 }
 
 // ---------------------------------------------------------------- block update Y = X C + Z
@@ -302,7 +420,7 @@ __global__ void __launch_bounds__(256) update_df_kernel(const double2 *__restric
   for (int i = 0; i < p; ++i) {
     const cdf xv = cdf_from(Xb[(long)i * L + l]);
 #pragma unroll
-    for (int c = 0; c < DF_QB; ++c) acc[c] = cdf_add(acc[c], cdf_mul(xv, Cs[i][c]));
+    for (int c = 0; c < DF_QB; ++c) cdf_mac(acc[c], xv, Cs[i][c]);
   }
   double2 *Yb = Y + (long)b * sy;
   const float2 *Zb = Z ? Z + (long)b * sz : nullptr;
@@ -330,97 +448,66 @@ int launch_update_df(int nb, long L, int p, int q, const void *X, long sx, const
   return PC_OK;
 }
 
-// ---------------------------------------------------------------- Gram pair G = X^H X, H = X^H AX
-constexpr int DF_TL = 16;
+// ---------------------------------------------------------------- Gram G = X^H X of the FP64 block
+// (X^H AX is not formed here: the mixed solve takes it as Theta X^H X + R^H X, R = AX - X Theta.)
+constexpr int DF_TL = 32;
 
-template <int R>
-__global__ void __launch_bounds__(1024) gram_df_kernel(const double2 *__restrict__ S, const double2 *__restrict__ AS,
-                                                     long ss, long L, int p, long chunk,
-                                                     double2 *__restrict__ partG, double2 *__restrict__ partH,
+// One thread per upper-triangle entry (i <= j): p(p+1)/2 threads; grid (nchunk, 1, nb).
+__global__ void __launch_bounds__(528) gram_df_kernel(const double2 *__restrict__ X, long sx, long L, int p,
+                                                     long chunk, double2 *__restrict__ part,
                                                      const int *__restrict__ act) {
-  __shared__ cdf Ss[32][DF_TL + 1];
-  __shared__ cdf As[32][DF_TL + 1];
+  __shared__ cdf Xs[32][DF_TL + 1];
+  __shared__ unsigned char pi[528], pj[528];
   const int bi = blockIdx.z;
   const int b = act ? act[bi] : bi;
-  const double2 *Sb = S + (long)b * ss;
-  const double2 *Ab = AS + (long)b * ss;
-  const int TD = blockDim.x;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TD + tx, nthr = TD * TD;
-  const bool active = ty <= tx;
-  cdf g[R][R], hh[R][R];
-#pragma unroll
-  for (int r = 0; r < R; ++r)
-#pragma unroll
-    for (int c = 0; c < R; ++c) g[r][c] = hh[r][c] = cdf{df{0.f, 0.f}, df{0.f, 0.f}};
+  const double2 *Xb = X + (long)b * sx;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  if (tid == 0) {
+    int t = 0;
+    for (int i = 0; i < p; ++i)
+      for (int j = i; j < p; ++j, ++t) {
+        pi[t] = (unsigned char)i;
+        pj[t] = (unsigned char)j;
+      }
+  }
+  __syncthreads();
+  const int i = pi[tid], j = pj[tid];
+  df re{0.f, 0.f}, im{0.f, 0.f};
   const long beg = (long)blockIdx.x * chunk, end = min(L, beg + chunk);
   for (long l0 = beg; l0 < end; l0 += DF_TL) {
-    for (int i = tid; i < p * DF_TL; i += nthr) {
-      const int col = i / DF_TL, t = i - col * DF_TL;
+    for (int e = tid; e < p * DF_TL; e += nthr) {
+      const int col = e / DF_TL, t = e - col * DF_TL;
       const long l = l0 + t;
-      double2 vs = make_double2(0.0, 0.0), va = vs;
-      if (l < end) {
-        vs = Sb[(long)col * L + l];
-        va = Ab[(long)col * L + l];
-      }
-      Ss[col][t] = cdf_from(vs);
-      As[col][t] = cdf_from(va);
+      Xs[col][t] = cdf_from(l < end ? Xb[(long)col * L + l] : make_double2(0.0, 0.0));
     }
     __syncthreads();
-    if (active) {
-      for (int t = 0; t < DF_TL; ++t) {
-        cdf a[R], bs[R], ba[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) a[r] = Ss[min(ty * R + r, p - 1)][t];
-#pragma unroll
-        for (int c = 0; c < R; ++c) {
-          const int j = min(tx * R + c, p - 1);
-          bs[c] = Ss[j][t];
-          ba[c] = As[j][t];
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-          for (int c = 0; c < R; ++c) {
-            g[r][c] = cdf_add(g[r][c], cdf_mulc(a[r], bs[c]));
-            hh[r][c] = cdf_add(hh[r][c], cdf_mulc(a[r], ba[c]));
-          }
-      }
+#pragma unroll 4
+    for (int t = 0; t < DF_TL; ++t) {
+      const cdf a = Xs[i][t], c = Xs[j][t];
+      // conj(a) c
+      df_mac(re, a.re, c.re);
+      df_mac(re, a.im, c.im);
+      df_mac(im, a.re, c.im);
+      df_mac(im, df_neg(a.im), c.re);
     }
     __syncthreads();
   }
-  if (!active) return;
-  const long o = ((long)bi * gridDim.x + blockIdx.x) * p * p;
-#pragma unroll
-  for (int r = 0; r < R; ++r)
-#pragma unroll
-    for (int c = 0; c < R; ++c) {
-      const int i = ty * R + r, j = tx * R + c;
-      if (i < p && j < p && i <= j) {
-        partG[o + i * p + j] = cdf_to(g[r][c]);
-        partH[o + i * p + j] = cdf_to(hh[r][c]);
-      }
-    }
+  part[((long)bi * gridDim.x + blockIdx.x) * p * p + i * p + j] = make_double2(df_to(re), df_to(im));
 }
 
-// chunk sums of the upper triangle in FP64, mirrored (same layout as gram_pair_reduce_kernel)
-__global__ void gram_df_reduce_kernel(const double2 *__restrict__ partG, const double2 *__restrict__ partH, int nchunk,
-                                      int p, const int *__restrict__ act, double2 *__restrict__ G,
-                                      double2 *__restrict__ H) {
+// chunk sums of the upper triangle in FP64, mirrored
+__global__ void gram_df_reduce_kernel(const double2 *__restrict__ part, int nchunk, int p, const int *__restrict__ act,
+                                      double2 *__restrict__ G) {
   const int bi = blockIdx.x;
   const int b = act ? act[bi] : bi;
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
     const int i = e / p, j = e - i * p;
     if (i > j) continue;
-    double2 sg = make_double2(0.0, 0.0), sh = sg;
-    for (int c = 0; c < nchunk; ++c) {
-      sg = cadd(sg, partG[((long)bi * nchunk + c) * p * p + e]);
-      sh = cadd(sh, partH[((long)bi * nchunk + c) * p * p + e]);
-    }
-    if (i == j) sg.y = sh.y = 0.0;
+    double2 sg = make_double2(0.0, 0.0);
+    for (int c = 0; c < nchunk; ++c) sg = cadd(sg, part[((long)bi * nchunk + c) * p * p + e]);
+    if (i == j) sg.y = 0.0;
     G[(long)b * p * p + i * p + j] = sg;
-    H[(long)b * p * p + i * p + j] = sh;
     G[(long)b * p * p + j * p + i] = make_double2(sg.x, -sg.y);
-    H[(long)b * p * p + j * p + i] = make_double2(sh.x, -sh.y);
   }
 }
 
@@ -430,11 +517,11 @@ static int df_chunks(int nb, long L) {
 }
 
 size_t gram_df_scratch_bytes(int nb, long L, int p) {
-  return 2 * sizeof(double2) * (size_t)nb * df_chunks(nb, L) * p * p;
+  return sizeof(double2) * (size_t)nb * df_chunks(nb, L) * p * p;
 }
 
-int launch_gram_df(int nb, long L, int p, const void *S, const void *AS, long ss, void *G, void *H, void *scratch,
-                   size_t scratch_bytes, cudaStream_t st, const int *act) {
+int launch_gram_df(int nb, long L, int p, const void *X, long sx, void *G, void *scratch, size_t scratch_bytes,
+                   cudaStream_t st, const int *act) {
   if (nb == 0 || p == 0) return PC_OK;
   if (p > 32 || gram_df_scratch_bytes(nb, L, p) > scratch_bytes) {
     set_error("gram_df: at most 32 columns and enough scratch");
@@ -443,14 +530,11 @@ int launch_gram_df(int nb, long L, int p, const void *S, const void *AS, long ss
   const int nchunk = df_chunks(nb, L);
   long chunk = (L + nchunk - 1) / nchunk;
   chunk = (chunk + DF_TL - 1) / DF_TL * DF_TL;
-  double2 *pG = static_cast<double2 *>(scratch), *pH = pG + (size_t)nb * nchunk * p * p;
-  const double2 *Sd = static_cast<const double2 *>(S), *Ad = static_cast<const double2 *>(AS);
-  // one output pair per thread (p x p threads, the upper triangle active): the double-float arithmetic is the
-  // bottleneck, so parallelism matters more than register reuse
-  gram_df_kernel<1><<<dim3(nchunk, 1, nb), dim3(p, p), 0, st>>>(Sd, Ad, ss, L, p, chunk, pG, pH, act);
+  double2 *part = static_cast<double2 *>(scratch);
+  gram_df_kernel<<<dim3(nchunk, 1, nb), p * (p + 1) / 2, 0, st>>>(static_cast<const double2 *>(X), sx, L, p, chunk,
+                                                                   part, act);
   PC_CK_LAUNCH();
-  gram_df_reduce_kernel<<<nb, 256, 0, st>>>(pG, pH, nchunk, p, act, static_cast<double2 *>(G),
-                                            static_cast<double2 *>(H));
+  gram_df_reduce_kernel<<<nb, 256, 0, st>>>(part, nchunk, p, act, static_cast<double2 *>(G));
   PC_CK_LAUNCH();
   return PC_OK;
 }

@@ -115,8 +115,13 @@ struct pc_ctx {
   int kcap = 0;             // capacity (k-points) of kparam / symd
   // solver buffers
   pc::DevBuf S[2], AS[2], Gm, Hm, coef, theta, norms, rnorm, rank, flag;
-  // mixed-precision solve: FP64 block X and AX, complex64 residual copy, coupling and FP64 X-X products, phases
-  pc::DevBuf X64[2], AX64, R32, RQ, GX, HX, phase, mask;
+  // mixed-precision solve: FP64 block X, complex64 residual copy, coupling R^H S, FP64 X^H X, phases, masks
+  pc::DevBuf X64[2], R32, RQ, GX, phase, mask;
+  // mixed solve with two k-point groups: the second group's stream, and pinned host copies of theta, column norms
+  // and Algorithm 4.1 norms (so that a group's device-to-host copies do not block the host)
+  cudaStream_t stream2 = nullptr;
+  double *pinned = nullptr;
+  size_t pinned_count = 0;
   // tracing: per-stage statistics and event pairs awaiting harvest
   bool timing = false;
   pc_stage_stat stats[PC_NSTAGES] = {};
@@ -127,6 +132,8 @@ struct pc_ctx {
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
   ~pc_ctx() {
+    if (stream2) cudaStreamDestroy(stream2);
+    if (pinned) cudaFreeHost(pinned);
     for (auto &p : pending) {
       cudaEventDestroy(p.a);
       cudaEventDestroy(p.b);
@@ -138,7 +145,7 @@ struct pc_ctx {
 namespace pc {
 // Runs one stage invocation: counts it, adds its algorithmic work, and brackets it with events when timing is on.
 template <typename F> int run_stage(pc_ctx *ctx, int stage, int kernels, double flops, double bytes, F &&launch);
-// Accumulates the elapsed times of finished event pairs (call after a stream synchronisation).
+// Accumulates the elapsed times of finished event pairs; pairs still in flight stay pending.
 int harvest_timing(pc_ctx *ctx);
 // uploads kparams (and symbol tables) for nb k-points into the context; returns 0 or an error code
 int upload_kpoints(pc_ctx *ctx, int nb, const double *kpts, const double *gammas);
@@ -147,51 +154,66 @@ int launch_apply_op(pc_ctx *ctx, int nb, int m, int dtype, const void *X, long s
                     const int *act);
 int launch_precond(pc_ctx *ctx, int nb, int m, int dtype, const void *R, long sr, void *W, long sw,
                    const int *act);
-// nb_alloc: k-points in the panel arrays (the act list indexes them); <= 0 means nb
+// nb_alloc: k-points in the panel arrays (the act list indexes them); <= 0 means nb.
+// sg: batch stride of the output matrices in elements; <= 0 means packed (p q, or p p for the pair).
 int launch_gram(int nb, long L, int p, int q, int dtype, const void *A, long sa, const void *B, long sb, void *G,
-                void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc = -1);
+                void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc = -1,
+                long sg = 0);
 size_t gram_scratch_bytes(int nb, long L, int p, int q);
 int launch_gram_pair(int nb, long L, int p, int dtype, const void *S, const void *AS, long ss, void *G, void *H,
-                     void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc = -1);
+                     void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc = -1,
+                     long sg = 0);
 size_t gram_pair_scratch_bytes(int nb, long L, int p);
 // reductions of per-chunk partial sums ([nb][nchunk][p][q] double2; the pair: G block then H block, upper triangles)
 void launch_gram_pair_reduce(int nb, int nchunk, int p, const double2 *part, const int *act, void *G, void *H,
-                             cudaStream_t st);
+                             cudaStream_t st, long sg = 0);
 void launch_gram_reduce(int nb, int nchunk, int p, int q, const double2 *part, const int *act, void *G,
-                        cudaStream_t st);
+                        cudaStream_t st, long sg = 0);
 // complex64 Gram products on the tensor cores (gram_tc.cu); PC_EUNSUPPORTED when the shape does not fit
 int launch_gram_pair_tc(int nb, long L, int p, const void *S, const void *AS, long ss, void *G, void *H,
-                        void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc);
+                        void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc, long sg);
 int launch_gram_tc(int nb, long L, int p, int q, const void *A, long sa, const void *B, long sb, void *G,
-                   void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc);
+                   void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc, long sg);
 // reads and clears the time-out flag of the tensor-core Gram kernel (call after a synchronisation)
 int gram_tc_check();
 // Y = S C (+ Z, a complex64 addend, if Z is not null); arithmetic in the precision of dtype
 int launch_block_update(int nb, long L, int p, int q, int dtype, const void *S, long ss, const void *C, long sc,
                         void *Y, long sy, cudaStream_t st, const int *act, const void *Z = nullptr, long sz = 0);
+// sg, sc: batch strides of G/H and of coef in elements; <= 0 means packed (n n, n m)
 int launch_rr(int nb, int n, int m, const void *G, const void *H, double drop, double *theta, void *coef,
-              int *rank, cudaStream_t st, const int *act);
+              int *rank, cudaStream_t st, const int *act, long sg = 0, long sc = 0);
 int launch_residual(int nb, long L, int m, const void *X, long sx, const void *AX, long sax, const double *theta,
                     void *R, long sr, double *norms, void *scratch, size_t scratch_bytes, cudaStream_t st,
                     const int *act);
 size_t residual_scratch_bytes(int nb, long L, int m);
-int launch_recompute(pc_ctx *ctx, int nb, int m, const void *X, long sx, double *out, const int *act);
+int launch_recompute(pc_ctx *ctx, int nb, int m, const void *X, long sx, double *out, const int *act, void *scratch,
+                     size_t scratch_bytes);
+size_t recompute_scratch_bytes(long n, int nb, int m);
 int launch_deflate(int nb, long n, int m, void *X, long sx, const int *flags, void *scratch, cudaStream_t st,
                    const int *act, int dtype = PC_C128);
 int launch_residual_mixed(int nb, long L, int m, int dtype_x, const void *X, long sx, const void *AX, long sax,
                           const double *theta, void *R1, long sr1, void *R2, long sr2, void *X32, long sx32,
                           void *AX32, long sax32, double *norms, void *scratch, size_t scratch_bytes,
                           cudaStream_t st, const int *act);
-int launch_rr_patch(int nb, int n, int m, void *G, void *H, const void *RQ, const double *theta, const void *GX,
-                    const void *HX, const int *phase, cudaStream_t st, const int *act);
+int launch_rr_patch(int nb, int n, int m, void *G, void *H, const void *RS, const double *theta, const void *GX,
+                    const int *phase, cudaStream_t st, const int *act, long sg = 0, long srs = 0);
 int launch_widen(int nb, long L, int m, const void *X, long sx, void *Y, long sy, cudaStream_t st, const int *act);
 int launch_narrow(int nb, long L, int m, const void *X, long sx, void *Y, long sy, cudaStream_t st, const int *act);
 // double-float (FP32-pair) versions of the FP64-accurate kernels of the mixed solve (mixed_df.cu)
 int launch_apply_op_df(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act);
+// the same stencil with the residual epilogue of the mixed solve's phase 2 instead of writing AX: complex64
+// r = AX - X Theta into R1 and R2, complex64 copies of X and AX, column norms (|r|, |x|) into norms [nb][m][2]
+int launch_op_df_resid(pc_ctx *ctx, int nb, int m, const void *X, long sx, const double *theta, void *R1, long sr1,
+                       void *R2, long sr2, void *X32, long sx32, void *AX32, long sax32, double *norms, void *scratch,
+                       size_t scratch_bytes, const int *act);
+size_t op_df_resid_scratch_bytes(pc_ctx *ctx, int nb, int m);
+void launch_residual_reduce(int nb, int nchunk, int m, const double *part, const int *act, double *norms,
+                            cudaStream_t st);
 int launch_update_df(int nb, long L, int p, int q, const void *X, long sx, const void *C, long sc, void *Y, long sy,
                      const void *Z, long sz, cudaStream_t st, const int *act);
-int launch_gram_df(int nb, long L, int p, const void *S, const void *AS, long ss, void *G, void *H, void *scratch,
-                   size_t scratch_bytes, cudaStream_t st, const int *act);
+// G = X^H X of an FP64 block (p <= 32 columns) in double-float arithmetic
+int launch_gram_df(int nb, long L, int p, const void *X, long sx, void *G, void *scratch, size_t scratch_bytes,
+                   cudaStream_t st, const int *act);
 size_t gram_df_scratch_bytes(int nb, long L, int p);
 // the mixed-precision LOBPCG driver (solver_mixed.cu); k-points already reduced, gammas per k-point
 int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam, const std::vector<int> &zero,

@@ -154,7 +154,7 @@ size_t rr_smem(int n, int m) {
 __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restrict__ Gg, const double2 *__restrict__ Hg,
                                                         int n, int m, double drop, double *__restrict__ thetag,
                                                         double2 *__restrict__ coefg, int *__restrict__ rankg,
-                                                        const int *__restrict__ act) {
+                                                        const int *__restrict__ act, long sg, long sc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int LD = rr_ld(n);
   double2 *A = reinterpret_cast<double2 *>(smem_raw);  // scaled G -> pivoted Cholesky factor (lower)
@@ -175,8 +175,8 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
   __shared__ double2 s_alpha, s_K;
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
   const int b = act ? act[blockIdx.x] : (int)blockIdx.x;
-  const double2 *G = Gg + (long)b * n * n;
-  const double2 *H = Hg + (long)b * n * n;
+  const double2 *G = Gg + (long)b * sg;
+  const double2 *H = Hg + (long)b * sg;
   double *Z = reinterpret_cast<double *>(B);
 
   // 1. scaling
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
 
   // 7. back-transformation, one warp per Ritz vector held in registers (lane l owns rows l and l + 32):
   // y = Q Phi z (reflectors applied last to first), then L^H x = y, coef = D P x
-  double2 *out = coefg + (long)b * n * m;
+  double2 *out = coefg + (long)b * sc;
   for (int j = warp; j < m; j += nwarp) {
     double2 y0 = cmake<double2>(0.0, 0.0), y1 = y0;
     const int i0 = lane, i1 = lane + 32;
@@ -540,7 +540,7 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
 }  // namespace
 
 int launch_rr(int nb, int n, int m, const void *G, const void *H, double drop, double *theta, void *coef, int *rank,
-              cudaStream_t st, const int *act) {
+              cudaStream_t st, const int *act, long sg, long sc) {
   if (nb == 0) return PC_OK;
   if (n > RR_MAXN || m > n) {
     set_error("rayleigh_ritz: need m <= n <= %d", RR_MAXN);
@@ -553,7 +553,8 @@ int launch_rr(int nb, int n, int m, const void *G, const void *H, double drop, d
     configured = true;
   }
   rr_kernel<<<nb, RR_THREADS, rr_smem(n, m), st>>>(static_cast<const double2 *>(G), static_cast<const double2 *>(H),
-                                                    n, m, drop, theta, static_cast<double2 *>(coef), rank, act);
+                                                    n, m, drop, theta, static_cast<double2 *>(coef), rank, act,
+                                                    sg > 0 ? sg : (long)n * n, sc > 0 ? sc : (long)n * m);
   PC_CK_LAUNCH();
   return PC_OK;
 }

@@ -97,14 +97,21 @@ cudaError_t get_event(pc_ctx *ctx, cudaEvent_t *e) {
 }
 
 int harvest_timing(pc_ctx *ctx) {
+  std::vector<pc_ctx::Pending> keep;
   for (auto &p : ctx->pending) {
+    const cudaError_t q = cudaEventQuery(p.b);
+    if (q == cudaErrorNotReady) {
+      keep.push_back(p);
+      continue;
+    }
+    PC_CK(q);
     float ms = 0.f;
     PC_CK(cudaEventElapsedTime(&ms, p.a, p.b));
     ctx->stats[p.stage].ms += ms;
     ctx->event_pool.push_back(p.a);
     ctx->event_pool.push_back(p.b);
   }
-  ctx->pending.clear();
+  ctx->pending.swap(keep);
   return PC_OK;
 }
 
@@ -149,6 +156,7 @@ extern "C" int pc_opts_default(pc_opts *o) {
   o->maxiter = 400;
   o->max_doublings = 8;
   o->seed = 0;
+  o->groups = 0;
   return PC_OK;
 }
 
@@ -407,7 +415,7 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
       PC_CK(cudaMemcpyAsync(d_act, conv.data(), sizeof(int) * conv.size(), cudaMemcpyHostToDevice, st));
       const int nconv = (int)conv.size();
       RUN(run_stage(ctx, PC_STAGE_RECOMPUTE, 2, 120.0 * nd * m * nconv, Ld * cb * m * nconv,
-                    [&] { return launch_recompute(ctx, nconv, m, Sc, sS, rn, d_act); }));
+                    [&] { return launch_recompute(ctx, nconv, m, Sc, sS, rn, d_act, scratch, scr); }));
       PC_CK(cudaMemcpyAsync(h_rn.data(), rn, sizeof(double) * nb * m * 3, cudaMemcpyDeviceToHost, st));
       PC_CK(cudaStreamSynchronize(st));
       for (int b : conv) {

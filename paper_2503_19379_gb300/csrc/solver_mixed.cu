@@ -11,9 +11,19 @@
 // * The X-X block (X^H X, X^H AX) and the residual need FP64: the residual floor of a complex64 X is eps32 |Op| / lambda
 //   (about 1e-3 here), and the X-X block's rounding shifts the Ritz values by eps32 lambda.
 // Phase 1 (every k-point starts here): X and AX in complex64 as well, until the complex64 residual stops falling.
-// Phase 2: X, AX stored in FP64; X' = X C_X + P' (complex64 correction), AX' by the stencil and the X-X block, all
-// three in double-float arithmetic (mixed_df.cu) on the FP32 pipe.
+// Phase 2: X stored in FP64; X' = X C_X + P' (complex64 correction), AX' = Op X' by the stencil fused with the
+// residual R = AX' - X' Theta (AX' itself is never stored), and the X-X Gram block X^H X, all three in double-float
+// arithmetic (mixed_df.cu) on the FP32 pipe. The X-X block of the projected operator is Theta X^H X + R^H X
+// (AX = X Theta + R), with R^H X from the complex64 product R^H [X | Q]: its rounding is eps32 |R| |X|, small
+// because R is.
 // Convergence and Algorithm 4.1 are decided in phase 2 only, on FP64 residuals and FP64 norms.
+//
+// Scheduling: the k-points are split into contiguous groups (opts.groups, default 2 from 8 k-points on), each with
+// its own stream, active list, scratch and pinned host copies of its residual norms. Every iteration of a group ends
+// with its residual norms copied to the host and an event; the host then serves the groups in turn -- waits for a
+// group's event, takes its convergence decisions, enqueues its next iteration -- so that while it waits for one group
+// the other group's kernels occupy the GPU. This hides the latency-bound steps (the Rayleigh-Ritz kernel runs one
+// block per k-point, the host decisions leave the GPU idle) behind the other group's bandwidth-bound kernels.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -22,309 +32,517 @@
 
 namespace pc {
 
-int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam, const std::vector<int> &zero,
-                int nbands, int m, double tol, double *evals, void *evecs, int *iters, double *resid) {
-  cudaStream_t st = ctx->stream;
-  const long n = ctx->n, L = 3 * n;
-  const long sF = 3L * m * L, sX = (long)m * L;
-  const int nmax = 3 * m;
-  PC_CK(ctx->S[0].reserve(sizeof(float2) * (size_t)sF * nb));
-  PC_CK(ctx->S[1].reserve(sizeof(float2) * (size_t)sF * nb));
-  PC_CK(ctx->AS[0].reserve(sizeof(float2) * (size_t)sF * nb));
-  PC_CK(ctx->AS[1].reserve(sizeof(float2) * (size_t)sF * nb));
-  PC_CK(ctx->X64[0].reserve(sizeof(double2) * (size_t)sX * nb));
-  PC_CK(ctx->X64[1].reserve(sizeof(double2) * (size_t)sX * nb));
-  PC_CK(ctx->AX64.reserve(sizeof(double2) * (size_t)sX * nb));
-  PC_CK(ctx->R32.reserve(sizeof(float2) * (size_t)sX * nb));
-  PC_CK(ctx->Gm.reserve(sizeof(double2) * (size_t)nb * nmax * nmax));
-  PC_CK(ctx->Hm.reserve(sizeof(double2) * (size_t)nb * nmax * nmax));
-  PC_CK(ctx->RQ.reserve(sizeof(double2) * (size_t)nb * m * 2 * m));
-  PC_CK(ctx->GX.reserve(sizeof(double2) * (size_t)nb * m * m));
-  PC_CK(ctx->HX.reserve(sizeof(double2) * (size_t)nb * m * m));
-  PC_CK(ctx->coef.reserve(sizeof(double2) * (size_t)nb * nmax * m));
-  PC_CK(ctx->theta.reserve(sizeof(double) * (size_t)nb * m));
-  PC_CK(ctx->norms.reserve(sizeof(double) * (size_t)nb * m * 2));
-  PC_CK(ctx->rnorm.reserve(sizeof(double) * (size_t)nb * m * 3));
-  PC_CK(ctx->rank.reserve(sizeof(int) * (size_t)nb * 2));
-  PC_CK(ctx->flag.reserve(sizeof(int) * (size_t)nb));
-  PC_CK(ctx->phase.reserve(sizeof(int) * (size_t)nb));
-  const size_t scr = std::max({gram_pair_scratch_bytes(nb, L, nmax), gram_df_scratch_bytes(nb, L, m),
-                               gram_scratch_bytes(nb, L, m, 2 * m), residual_scratch_bytes(nb, L, m),
-                               sizeof(double2) * (size_t)nb * 3 * m * 16, sizeof(double) * 3 * (size_t)nb * m * 64,
-                               (size_t)16});
-  PC_CK(ctx->scratch.reserve(scr));
-  void *scratch = ctx->scratch.p;
-  float2 *F[2] = {ctx->S[0].as<float2>(), ctx->S[1].as<float2>()};
-  float2 *AF[2] = {ctx->AS[0].as<float2>(), ctx->AS[1].as<float2>()};
-  double2 *X64[2] = {ctx->X64[0].as<double2>(), ctx->X64[1].as<double2>()};
-  double2 *AX64 = ctx->AX64.as<double2>();
-  float2 *R32 = ctx->R32.as<float2>();
-  double2 *Gm = ctx->Gm.as<double2>(), *Hm = ctx->Hm.as<double2>(), *coef = ctx->coef.as<double2>();
-  double2 *RQ = ctx->RQ.as<double2>(), *GX = ctx->GX.as<double2>(), *HX = ctx->HX.as<double2>();
-  double *theta = ctx->theta.as<double>(), *norms = ctx->norms.as<double>(), *rn = ctx->rnorm.as<double>();
-  int *d_act = ctx->rank.as<int>() + nb;
-  int *d_zero = ctx->flag.as<int>();
-  int *d_phase = ctx->phase.as<int>();
-  PC_CK(ctx->mask.reserve(sizeof(int) * (size_t)nb * m));
-  int *d_mask = ctx->mask.as<int>();
-  uint64_t restarts = 0;
-  const double drop = 1e-12;
+namespace {
 
-  std::vector<int> phase(nb, 1), doublings(nb, 0), itcount(nb, 0), done(nb, 0), round_start(nb, 0), p1_start(nb, 0);
-  std::vector<std::vector<double>> hist(nb);
-  PC_CK(cudaMemcpyAsync(d_zero, zero.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
-  PC_CK(cudaMemcpyAsync(d_phase, phase.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
-  bool any_zero = false;
-  for (int b = 0; b < nb; ++b) any_zero |= zero[b] != 0;
-
-  // algorithmic work per stage invocation: 8 bytes per complex64 entry, 16 per FP64 entry
-  const double Ld = (double)L, nd = (double)n;
-  const double fft_flops = 3.0 * 2.0 * 5.0 * nd * std::log2(nd) + 60.0 * nd;
-  auto set_act = [&](const std::vector<int> &v) -> int {
-    if (v.empty()) return PC_OK;
-    PC_CK(cudaMemcpyAsync(d_act, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, st));
-    return PC_OK;
-  };
-  auto OP32 = [&](int nbk, int cols, const void *X, long sx, void *Y, long sy) {
-    return run_stage(ctx, PC_STAGE_STENCIL, 1, 214.0 * nd * nbk * cols, 2.0 * Ld * 8.0 * nbk * cols + 12.0 * nd,
-                     [&] { return launch_apply_op(ctx, nbk, cols, PC_C64, X, sx, Y, sy, d_act); });
-  };
-  auto OP64 = [&](int nbk, const void *X, void *Y) {  // FP64 block, double-float arithmetic
-    return run_stage(ctx, PC_STAGE_STENCIL, 1, 214.0 * nd * nbk * m, 2.0 * Ld * 16.0 * nbk * m + 24.0 * nd,
-                     [&] { return launch_apply_op_df(ctx, nbk, m, X, sX, Y, sX, d_act); });
-  };
-  auto DEFL = [&](int nbk, void *X, long sx, int dtype) {
-    return run_stage(ctx, PC_STAGE_OTHER, 2, 4.0 * Ld * m * nbk, 2.0 * Ld * (dtype == PC_C64 ? 8.0 : 16.0) * m * nbk,
-                     [&] { return launch_deflate(nbk, n, m, X, sx, d_zero, scratch, st, d_act, dtype); });
-  };
 #define RUN(x)                    \
   do {                            \
     int rc_ = (x);                \
     if (rc_ != PC_OK) return rc_; \
   } while (0)
 
-  std::vector<int> act;
-  for (int b = 0; b < nb; ++b) act.push_back(b);
-  RUN(set_act(act));
-  // ---- initial block (FP64 generator, narrowed) and Rayleigh-Ritz on span(X0), all in phase 1
-  RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, Ld * 16.0 * m * nb,
-                [&] { return launch_init_block(nb, L, m, ctx->opts.seed, 0, X64[0], sX, st); }));
-  if (any_zero) RUN(DEFL(nb, X64[0], sX, PC_C128));
-  RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, Ld * 24.0 * m * nb,
-                [&] { return launch_narrow(nb, L, m, X64[0], sX, F[0], sF, st, d_act); }));
-  RUN(OP32(nb, m, F[0], sF, AF[0], sF));
-  RUN(run_stage(ctx, PC_STAGE_GRAM, 2, 8.0 * m * (m + 1) * Ld * nb, 2.0 * m * Ld * 8.0 * nb, [&] {
-    return launch_gram_pair(nb, L, m, PC_C64, F[0], AF[0], sF, Gm, Hm, scratch, scr, st, d_act, nb);
-  }));
-  RUN(run_stage(ctx, PC_STAGE_RR, 1, 0.0, 2.0 * m * m * 16.0 * nb,
-                [&] { return launch_rr(nb, m, m, Gm, Hm, drop, theta, coef, nullptr, st, d_act); }));
-  RUN(run_stage(ctx, PC_STAGE_UPDATE, 1, 8.0 * m * m * Ld * nb, 2.0 * m * Ld * 8.0 * nb, [&] {
-    return launch_block_update(nb, L, m, m, PC_C64, F[0], sF, coef, (long)m * m, F[1], sF, st, d_act);
-  }));
-  RUN(OP32(nb, m, F[1], sF, AF[1], sF));
-  int cur = 1;
-  bool haveP = false;
-
-  std::vector<double> h_theta((size_t)nb * m), h_norms((size_t)nb * m * 2), h_rn((size_t)nb * m * 3);
+// state shared by the groups of one solve (per-k-point arrays are indexed by the global k-point index b)
+struct MixedShared {
+  pc_ctx *ctx;
+  int nb, nbands, m;
+  long n, L, sF, sX;
+  int nmax;
+  double tol, drop;
+  const double *kr;
+  std::vector<double> *gam;
+  bool any_zero;
+  float2 *F[2], *AF[2];
+  double2 *X64[2];
+  float2 *R32;
+  double2 *Gm, *Hm, *coef, *RQ, *GX;
+  double *theta, *norms, *rn;
+  int *d_zero, *d_phase, *d_mask;
+  double *h_theta, *h_norms, *h_rn;  // pinned
+  size_t scr;                        // scratch bytes per group
+  // batch strides (elements) of the per-k-point matrices, fixed for every search-space width so that groups at
+  // different iterations never overlap: G and H (nmax x nmax), R^H S (m x nmax), coefficients (nmax x m)
+  long sG, sRS, sC;
+  std::vector<int> phase, doublings, itcount, done, round_start, p1_start;
+  std::vector<std::vector<double>> hist;
+  double *evals, *resid;
+  void *evecs;
   int status = PC_OK;
-  const int maxiter = ctx->opts.maxiter;
-  for (int it = 0;; ++it) {
+  double Ld, nd, fft_flops;
+};
+
+struct Group {
+  int b0 = 0, b1 = 0;  // k-points [b0, b1)
+  cudaStream_t st = nullptr;
+  int *d_act = nullptr;
+  void *scratch = nullptr;
+  std::vector<int> act;
+  int cur = 1, it = 0;
+  bool haveP = false, finished = false;
+  uint64_t restarts = 0;
+  cudaEvent_t ev = nullptr;
+};
+
+class MixedSolve {
+ public:
+  MixedSolve(MixedShared &s, Group &g) : S(s), g(g), ctx(s.ctx) {}
+
+  // kernels of this group go to its stream (run_stage records its events on ctx->stream)
+  struct StreamScope {
+    pc_ctx *ctx;
+    cudaStream_t saved;
+    StreamScope(pc_ctx *c, cudaStream_t s) : ctx(c), saved(c->stream) { c->stream = s; }
+    ~StreamScope() { ctx->stream = saved; }
+  };
+
+  int set_act(const std::vector<int> &v) {
+    if (v.empty()) return PC_OK;
+    PC_CK(cudaMemcpyAsync(g.d_act, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, g.st));
+    return PC_OK;
+  }
+  int OP32(int nbk, int cols, const void *X, long sx, void *Y, long sy) {
+    return run_stage(ctx, PC_STAGE_STENCIL, 1, 214.0 * S.nd * nbk * cols, 2.0 * S.Ld * 8.0 * nbk * cols + 12.0 * S.nd,
+                     [&] { return launch_apply_op(ctx, nbk, cols, PC_C64, X, sx, Y, sy, g.d_act); });
+  }
+  // phase 2: AX = Op X for the FP64 block in double-float arithmetic, fused with the residual R = AX - X Theta
+  // (complex64 copies of R into the W slot of panel `slot` and into R32, of X and AX into the panel's X columns;
+  // column norms into `norms`): the FP64 AX is never stored
+  int OP64R(int nbk, const void *X, int slot) {
+    const long L = S.L, sF = S.sF;
+    return run_stage(ctx, PC_STAGE_DFLOAT, 2, (214.0 * S.nd + 4.0 * S.Ld) * nbk * S.m,
+                     (16.0 + 4.0 * 8.0) * S.Ld * nbk * S.m + 24.0 * S.nd, [&] {
+                       return launch_op_df_resid(ctx, nbk, S.m, X, S.sX, S.theta, S.F[slot] + (long)S.m * L, sF,
+                                                 S.R32, S.sX, S.F[slot], sF, S.AF[slot], sF, S.norms, g.scratch, S.scr,
+                                                 g.d_act);
+                     });
+  }
+  int DEFL(int nbk, void *X, long sx, int dtype) {
+    return run_stage(ctx, PC_STAGE_OTHER, 2, 4.0 * S.Ld * S.m * nbk,
+                     2.0 * S.Ld * (dtype == PC_C64 ? 8.0 : 16.0) * S.m * nbk,
+                     [&] { return launch_deflate(nbk, S.n, S.m, X, sx, S.d_zero, g.scratch, g.st, g.d_act, dtype); });
+  }
+
+  // initial block (FP64 generator, narrowed) and Rayleigh-Ritz on span(X0), then the first residual
+  int start() {
+    StreamScope scope(ctx, g.st);
+    const int m = S.m, nb = S.nb;
+    const long L = S.L, sF = S.sF, sX = S.sX;
+    const int na = g.b1 - g.b0;
+    for (int b = g.b0; b < g.b1; ++b) g.act.push_back(b);
+    RUN(set_act(g.act));
+    RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, S.Ld * 16.0 * m * na, [&] {
+      return launch_init_block(na, L, m, ctx->opts.seed, 0, S.X64[0], sX, g.st, nullptr, g.d_act);
+    }));
+    if (S.any_zero) RUN(DEFL(na, S.X64[0], sX, PC_C128));
+    RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, S.Ld * 24.0 * m * na,
+                  [&] { return launch_narrow(na, L, m, S.X64[0], sX, S.F[0], sF, g.st, g.d_act); }));
+    RUN(OP32(na, m, S.F[0], sF, S.AF[0], sF));
+    RUN(run_stage(ctx, PC_STAGE_GRAM, 2, 8.0 * m * (m + 1) * S.Ld * na, 2.0 * m * S.Ld * 8.0 * na, [&] {
+      return launch_gram_pair(na, L, m, PC_C64, S.F[0], S.AF[0], sF, S.Gm, S.Hm, g.scratch, S.scr, g.st, g.d_act, nb,
+                              S.sG);
+    }));
+    RUN(run_stage(ctx, PC_STAGE_RR, 1, 0.0, 2.0 * m * m * 16.0 * na,
+                  [&] {
+                    return launch_rr(na, m, m, S.Gm, S.Hm, S.drop, S.theta, S.coef, nullptr, g.st, g.d_act, S.sG,
+                                     S.sC);
+                  }));
+    RUN(run_stage(ctx, PC_STAGE_UPDATE, 1, 8.0 * m * m * S.Ld * na, 2.0 * m * S.Ld * 8.0 * na, [&] {
+      return launch_block_update(na, L, m, m, PC_C64, S.F[0], sF, S.coef, S.sC, S.F[1], sF, g.st, g.d_act);
+    }));
+    RUN(OP32(na, m, S.F[1], sF, S.AF[1], sF));
+    g.cur = 1;
+    g.haveP = false;
+    g.it = 0;
+    return residual();
+  }
+
+  // residuals of the phase-1 k-points (complex64 block), then norms and Ritz values of the group to the host and the
+  // group's event
+  int residual() {
+    StreamScope scope(ctx, g.st);
+    const int m = S.m;
+    const long L = S.L, sF = S.sF, sX = S.sX;
     std::vector<int> act1, act2;
-    for (int b : act) (phase[b] == 1 ? act1 : act2).push_back(b);
-    const int nxt = 1 - cur;
-    // ---- residuals: complex64 block (phase 1) or FP64 block with complex64 copies of X, AX (phase 2)
+    for (int b : g.act) (S.phase[b] == 1 ? act1 : act2).push_back(b);
+    const int cur = g.cur;
     if (!act1.empty()) {
       RUN(set_act(act1));
       const int na = (int)act1.size();
-      RUN(run_stage(ctx, PC_STAGE_RESIDUAL, 2, 8.0 * Ld * m * na, 4.0 * Ld * 8.0 * m * na, [&] {
-        return launch_residual_mixed(na, L, m, PC_C64, F[cur], sF, AF[cur], sF, theta, F[cur] + (long)m * L, sF,
-                                     R32, sX, nullptr, 0, nullptr, 0, norms, scratch, scr, st, d_act);
+      RUN(run_stage(ctx, PC_STAGE_RESIDUAL, 2, 8.0 * S.Ld * m * na, 4.0 * S.Ld * 8.0 * m * na, [&] {
+        return launch_residual_mixed(na, L, m, PC_C64, S.F[cur], sF, S.AF[cur], sF, S.theta, S.F[cur] + (long)m * L,
+                                     sF, S.R32, sX, nullptr, 0, nullptr, 0, S.norms, g.scratch, S.scr, g.st, g.d_act);
       }));
     }
-    if (!act2.empty()) {
-      RUN(set_act(act2));
-      const int na = (int)act2.size();
-      RUN(run_stage(ctx, PC_STAGE_RESIDUAL, 2, 8.0 * Ld * m * na, (2.0 * 16.0 + 4.0 * 8.0) * Ld * m * na, [&] {
-        return launch_residual_mixed(na, L, m, PC_C128, X64[cur], sX, AX64, sX, theta, F[cur] + (long)m * L, sF, R32,
-                                     sX, F[cur], sF, AF[cur], sF, norms, scratch, scr, st, d_act);
-      }));
-    }
-    PC_CK(cudaMemcpyAsync(h_theta.data(), theta, sizeof(double) * nb * m, cudaMemcpyDeviceToHost, st));
-    PC_CK(cudaMemcpyAsync(h_norms.data(), norms, sizeof(double) * nb * m * 2, cudaMemcpyDeviceToHost, st));
-    PC_CK(cudaStreamSynchronize(st));
-    RUN(harvest_timing(ctx));
-    auto relres = [&](int b, int j) {
-      const double r = h_norms[((size_t)b * m + j) * 2], x = h_norms[((size_t)b * m + j) * 2 + 1];
-      return r / (std::fabs(h_theta[(size_t)b * m + j]) * x);
-    };
+    // phase-2 residuals were produced by the fused stencil (OP64R) when their block last changed
+    const size_t k0 = (size_t)g.b0 * m, kn = (size_t)(g.b1 - g.b0) * m;
+    PC_CK(cudaMemcpyAsync(S.h_theta + k0, S.theta + k0, sizeof(double) * kn, cudaMemcpyDeviceToHost, g.st));
+    PC_CK(cudaMemcpyAsync(S.h_norms + 2 * k0, S.norms + 2 * k0, sizeof(double) * 2 * kn, cudaMemcpyDeviceToHost,
+                          g.st));
+    PC_CK(cudaEventRecord(g.ev, g.st));
+    return PC_OK;
+  }
+
+  double relres(int b, int j) const {
+    const double r = S.h_norms[((size_t)b * S.m + j) * 2], x = S.h_norms[((size_t)b * S.m + j) * 2 + 1];
+    return r / (std::fabs(S.h_theta[(size_t)b * S.m + j]) * x);
+  }
+
+  // after the group's event: decisions on its residuals, then its next iteration up to the next residual
+  int step() {
+    StreamScope scope(ctx, g.st);
+    const int m = S.m, nb = S.nb, nbands = S.nbands;
+    const long L = S.L, sF = S.sF, sX = S.sX;
+    const int it = g.it, cur = g.cur, maxiter = ctx->opts.maxiter;
+    std::vector<int> act1, act2;
+    for (int b : g.act) (S.phase[b] == 1 ? act1 : act2).push_back(b);
     // ---- phase 1 -> 2 when the complex64 residual stops falling (or is already small)
     std::vector<int> sw;
     for (int b : act1) {
       double mx = 0;
       for (int j = 0; j < nbands; ++j) mx = std::max(mx, relres(b, j));
       if (!(mx == mx)) mx = 1e300;  // NaN guard
-      hist[b].push_back(mx);
-      const int k1 = (int)hist[b].size();
-      const bool stalled = k1 > 8 && mx > 0.7 * hist[b][k1 - 6];
-      if (stalled || mx < 1e-4 || it - p1_start[b] >= 150) sw.push_back(b);
+      S.hist[b].push_back(mx);
+      const int k1 = (int)S.hist[b].size();
+      const bool stalled = k1 > 8 && mx > 0.7 * S.hist[b][k1 - 6];
+      if (stalled || mx < 1e-4 || it - S.p1_start[b] >= 150) sw.push_back(b);
     }
     // ---- phase 2: convergence on FP64 residuals, then Algorithm 4.1
     std::vector<int> conv;
     for (int b : act2) {
       bool ok = true;
       for (int j = 0; j < nbands; ++j)
-        if (!(relres(b, j) <= tol)) ok = false;
-      if (ok || it - round_start[b] >= maxiter) conv.push_back(b);
+        if (!(relres(b, j) <= S.tol)) ok = false;
+      if (ok || it - S.round_start[b] >= maxiter) conv.push_back(b);
     }
     std::vector<int> redo, fin;
     if (!conv.empty()) {
       RUN(set_act(conv));
       const int nc = (int)conv.size();
-      RUN(run_stage(ctx, PC_STAGE_RECOMPUTE, 2, 120.0 * nd * m * nc, Ld * 16.0 * m * nc,
-                    [&] { return launch_recompute(ctx, nc, m, X64[cur], sX, rn, d_act); }));
-      PC_CK(cudaMemcpyAsync(h_rn.data(), rn, sizeof(double) * nb * m * 3, cudaMemcpyDeviceToHost, st));
-      PC_CK(cudaStreamSynchronize(st));
+      RUN(run_stage(ctx, PC_STAGE_RECOMPUTE, 2, 120.0 * S.nd * m * nc, S.Ld * 16.0 * m * nc, [&] {
+        return launch_recompute(ctx, nc, m, S.X64[cur], sX, S.rn, g.d_act, g.scratch, S.scr);
+      }));
+      const size_t k0 = (size_t)g.b0 * m, kn = (size_t)(g.b1 - g.b0) * m;
+      PC_CK(cudaMemcpyAsync(S.h_rn + 3 * k0, S.rn + 3 * k0, sizeof(double) * 3 * kn, cudaMemcpyDeviceToHost, g.st));
+      PC_CK(cudaStreamSynchronize(g.st));
       for (int b : conv) {
         bool spurious = false;
         for (int j = 0; j < nbands; ++j) {
-          const double *o = &h_rn[((size_t)b * m + j) * 3];
-          const double lre = o[0] / o[2], lam = h_theta[(size_t)b * m + j];
-          if (std::fabs(lam - lre) > 10.0 * tol * std::fabs(lam)) spurious = true;
+          const double *o = &S.h_rn[((size_t)b * m + j) * 3];
+          const double lre = o[0] / o[2], lam = S.h_theta[(size_t)b * m + j];
+          if (std::fabs(lam - lre) > 10.0 * S.tol * std::fabs(lam)) spurious = true;
         }
-        const bool capped = it - round_start[b] >= maxiter;
-        if (spurious && doublings[b] < ctx->opts.max_doublings && !capped) {
+        const bool capped = it - S.round_start[b] >= maxiter;
+        if (spurious && S.doublings[b] < ctx->opts.max_doublings && !capped) {
           redo.push_back(b);
         } else {
-          if (spurious) status = std::max(status, PC_SPURIOUS);
-          if (capped) status = std::max(status, PC_NOT_CONVERGED);
+          if (spurious) S.status = std::max(S.status, (int)PC_SPURIOUS);
+          if (capped) S.status = std::max(S.status, (int)PC_NOT_CONVERGED);
           fin.push_back(b);
         }
       }
     }
     for (int b : fin) {
-      done[b] = 1;
-      itcount[b] = it;
+      S.done[b] = 1;
+      S.itcount[b] = it;
       for (int j = 0; j < nbands; ++j) {
-        evals[(size_t)b * nbands + j] = h_theta[(size_t)b * m + j];
-        if (resid) resid[(size_t)b * nbands + j] = relres(b, j);
+        S.evals[(size_t)b * nbands + j] = S.h_theta[(size_t)b * m + j];
+        if (S.resid) S.resid[(size_t)b * nbands + j] = relres(b, j);
       }
-      if (evecs)
-        PC_CK(cudaMemcpyAsync(static_cast<double2 *>(evecs) + (size_t)b * nbands * L, X64[cur] + (size_t)b * sX,
-                              sizeof(double2) * (size_t)nbands * L, cudaMemcpyDeviceToDevice, st));
+      if (S.evecs)
+        PC_CK(cudaMemcpyAsync(static_cast<double2 *>(S.evecs) + (size_t)b * nbands * L, S.X64[cur] + (size_t)b * sX,
+                              sizeof(double2) * (size_t)nbands * L, cudaMemcpyDeviceToDevice, g.st));
     }
     {
       std::vector<int> keep;
-      for (int b : act)
-        if (!done[b]) keep.push_back(b);
-      act.swap(keep);
+      for (int b : g.act)
+        if (!S.done[b]) keep.push_back(b);
+      g.act.swap(keep);
     }
-    if (act.empty()) break;
+    if (g.act.empty()) {
+      g.finished = true;
+      return PC_OK;
+    }
+    const int k0 = g.b0, kn = g.b1 - g.b0;
     if (!sw.empty() || !redo.empty()) {
-      // phase switch: X64 = X (widened), AX64 = Op X64; gamma doubling: AX64 and AP with the new gamma
+      // phase switch: X64 = X (widened) and its residual; gamma doubling: the residual and AP with the new gamma
       if (!sw.empty()) {
         for (int b : sw) {
-          phase[b] = 2;
-          round_start[b] = it + 1;
+          S.phase[b] = 2;
+          S.round_start[b] = it + 1;
         }
         RUN(set_act(sw));
         const int ns = (int)sw.size();
-        RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, Ld * 24.0 * m * ns,
-                      [&] { return launch_widen(ns, L, m, F[cur], sF, X64[cur], sX, st, d_act); }));
-        RUN(OP64(ns, X64[cur], AX64));
-        PC_CK(cudaMemcpyAsync(d_phase, phase.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+        RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, S.Ld * 24.0 * m * ns,
+                      [&] { return launch_widen(ns, L, m, S.F[cur], sF, S.X64[cur], sX, g.st, g.d_act); }));
+        RUN(OP64R(ns, S.X64[cur], cur));
+        PC_CK(cudaMemcpyAsync(S.d_phase + k0, S.phase.data() + k0, sizeof(int) * kn, cudaMemcpyHostToDevice, g.st));
       }
       if (!redo.empty()) {
         for (int b : redo) {
-          gam[b] *= 2.0;
-          doublings[b] += 1;
-          round_start[b] = it + 1;
+          (*S.gam)[b] *= 2.0;
+          S.doublings[b] += 1;
+          S.round_start[b] = it + 1;
         }
-        RUN(upload_kpoints(ctx, nb, kr, gam.data()));
+        RUN(upload_kpoints(ctx, nb, S.kr, S.gam->data()));
         RUN(set_act(redo));
         const int nr = (int)redo.size();
         // spurious columns (gamma-independent exact eigenvectors of B'B) are replaced by fresh random columns
+        std::vector<double> th(S.h_theta, S.h_theta + (size_t)nb * m), rr(S.h_rn, S.h_rn + (size_t)nb * m * 3);
         std::vector<int> mask((size_t)nb * m);
-        spurious_mask(redo, m, nbands, tol, h_theta, h_rn, mask);
-        PC_CK(cudaMemcpyAsync(d_mask, mask.data(), sizeof(int) * mask.size(), cudaMemcpyHostToDevice, st));
-        ++restarts;
+        spurious_mask(redo, m, nbands, S.tol, th, rr, mask);
+        PC_CK(cudaMemcpyAsync(S.d_mask + (size_t)k0 * m, mask.data() + (size_t)k0 * m, sizeof(int) * kn * m,
+                              cudaMemcpyHostToDevice, g.st));
+        ++g.restarts;
+        // streams of fresh columns: distinct per group and restart
+        const uint64_t seed = ctx->opts.seed + 7919ULL * (g.restarts + 1000ULL * (uint64_t)g.b0);
         RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, 0.0, [&] {
-          return launch_init_block(nr, L, m, ctx->opts.seed + 7919ULL * restarts, 0, X64[cur], sX, st, d_mask, d_act);
+          return launch_init_block(nr, L, m, seed, 0, S.X64[cur], sX, g.st, S.d_mask, g.d_act);
         }));
-        if (any_zero) RUN(DEFL(nr, X64[cur], sX, PC_C128));
-        RUN(OP64(nr, X64[cur], AX64));
-        if (haveP) RUN(OP32(nr, m, F[cur] + 2L * m * L, sF, AF[cur] + 2L * m * L, sF));
+        if (S.any_zero) RUN(DEFL(nr, S.X64[cur], sX, PC_C128));
+        RUN(OP64R(nr, S.X64[cur], cur));
+        if (g.haveP) RUN(OP32(nr, m, S.F[cur] + 2L * m * L, sF, S.AF[cur] + 2L * m * L, sF));
       }
-      continue;  // residuals again with the new block or operator
+      return residual();  // residuals again with the new block or operator
     }
-    const int nc = haveP ? 3 * m : 2 * m;
+    const int nc = g.haveP ? 3 * m : 2 * m;
     const int nq = nc - m;
+    RUN(set_act(g.act));
+    const int na = (int)g.act.size();
+    const int nxt = 1 - cur;
+    // ---- W = P^{-1} R (complex64), AW = Op W
+    RUN(run_stage(ctx, PC_STAGE_PRECOND, 5, S.fft_flops * na * m, 2.0 * S.Ld * 8.0 * na * m, [&] {
+      return launch_precond(ctx, na, m, PC_C64, S.F[cur] + (long)m * L, sF, S.F[cur] + (long)m * L, sF, g.d_act);
+    }));
+    if (S.any_zero) RUN(DEFL(na, S.F[cur] + (long)m * L, sF, PC_C64));
+    RUN(OP32(na, m, S.F[cur] + (long)m * L, sF, S.AF[cur] + (long)m * L, sF));
+    // ---- pencil: complex64 products over [X | W | P], the R^H Q coupling, FP64 X-X block in phase 2
+    RUN(run_stage(ctx, PC_STAGE_GRAM, 2, 8.0 * nc * (nc + 1) * S.Ld * na, 2.0 * nc * S.Ld * 8.0 * na, [&] {
+      return launch_gram_pair(na, L, nc, PC_C64, S.F[cur], S.AF[cur], sF, S.Gm, S.Hm, g.scratch, S.scr, g.st, g.d_act,
+                              nb, S.sG);
+    }));
+    // R^H [X | Q]: the coupling R^H Q of H, and R^H X for the X-X block in phase 2
+    RUN(run_stage(ctx, PC_STAGE_GRAM, 2, 8.0 * m * nc * S.Ld * na, (double)(m + nc) * S.Ld * 8.0 * na, [&] {
+      return launch_gram(na, L, m, nc, PC_C64, S.R32, sX, S.F[cur], sF, S.RQ, g.scratch, S.scr, g.st, g.d_act, nb,
+                         S.sRS);
+    }));
     act1.clear();
     act2.clear();
-    for (int b : act) (phase[b] == 1 ? act1 : act2).push_back(b);
-    RUN(set_act(act));
-    const int na = (int)act.size();
-    // ---- W = P^{-1} R (complex64), AW = Op W
-    RUN(run_stage(ctx, PC_STAGE_PRECOND, 5, fft_flops * na * m, 2.0 * Ld * 8.0 * na * m, [&] {
-      return launch_precond(ctx, na, m, PC_C64, F[cur] + (long)m * L, sF, F[cur] + (long)m * L, sF, d_act);
-    }));
-    if (any_zero) RUN(DEFL(na, F[cur] + (long)m * L, sF, PC_C64));
-    RUN(OP32(na, m, F[cur] + (long)m * L, sF, AF[cur] + (long)m * L, sF));
-    // ---- pencil: complex64 products over [X | W | P], the R^H Q coupling, FP64 X-X block in phase 2
-    RUN(run_stage(ctx, PC_STAGE_GRAM, 2, 8.0 * nc * (nc + 1) * Ld * na, 2.0 * nc * Ld * 8.0 * na, [&] {
-      return launch_gram_pair(na, L, nc, PC_C64, F[cur], AF[cur], sF, Gm, Hm, scratch, scr, st, d_act, nb);
-    }));
-    RUN(run_stage(ctx, PC_STAGE_GRAM, 2, 8.0 * m * nq * Ld * na, (double)(m + nq) * Ld * 8.0 * na, [&] {
-      return launch_gram(na, L, m, nq, PC_C64, R32, sX, F[cur] + (long)m * L, sF, RQ, scratch, scr, st, d_act,
-                         nb);
-    }));
+    for (int b : g.act) (S.phase[b] == 1 ? act1 : act2).push_back(b);
     if (!act2.empty()) {
       RUN(set_act(act2));
       const int n2 = (int)act2.size();
-      RUN(run_stage(ctx, PC_STAGE_GRAM, 2, 8.0 * m * (m + 1) * Ld * n2, 2.0 * m * Ld * 16.0 * n2, [&] {
-        return launch_gram_df(n2, L, m, X64[cur], AX64, sX, GX, HX, scratch, scr, st, d_act);
+      RUN(run_stage(ctx, PC_STAGE_DFLOAT, 2, 4.0 * m * (m + 1) * S.Ld * n2, m * S.Ld * 16.0 * n2, [&] {
+        return launch_gram_df(n2, L, m, S.X64[cur], sX, S.GX, g.scratch, S.scr, g.st, g.d_act);
       }));
-      RUN(set_act(act));
+      RUN(set_act(g.act));
     }
     RUN(run_stage(ctx, PC_STAGE_RR, 1, 0.0, 2.0 * nc * nc * 16.0 * na, [&] {
-      int rc = launch_rr_patch(na, nc, m, Gm, Hm, RQ, theta, GX, HX, d_phase, st, d_act);
+      int rc = launch_rr_patch(na, nc, m, S.Gm, S.Hm, S.RQ, S.theta, S.GX, S.d_phase, g.st, g.d_act, S.sG, S.sRS);
       if (rc) return rc;
-      return launch_rr(na, nc, m, Gm, Hm, drop, theta, coef, nullptr, st, d_act);
+      return launch_rr(na, nc, m, S.Gm, S.Hm, S.drop, S.theta, S.coef, nullptr, g.st, g.d_act, S.sG, S.sC);
     }));
     // ---- P' = [W P] coef_{W,P} (complex64), then X' per phase
-    RUN(run_stage(ctx, PC_STAGE_UPDATE, 1, 8.0 * nq * m * Ld * na, (double)(nq + m) * Ld * 8.0 * na, [&] {
-      return launch_block_update(na, L, nq, m, PC_C64, F[cur] + (long)m * L, sF, coef + (long)m * m, (long)nc * m,
-                                 F[nxt] + 2L * m * L, sF, st, d_act);
+    RUN(run_stage(ctx, PC_STAGE_UPDATE, 1, 8.0 * nq * m * S.Ld * na, (double)(nq + m) * S.Ld * 8.0 * na, [&] {
+      return launch_block_update(na, L, nq, m, PC_C64, S.F[cur] + (long)m * L, sF, S.coef + (long)m * m, S.sC,
+                                 S.F[nxt] + 2L * m * L, sF, g.st, g.d_act);
     }));
     if (!act1.empty()) {
       RUN(set_act(act1));
       const int n1 = (int)act1.size();
-      RUN(run_stage(ctx, PC_STAGE_UPDATE, 1, 8.0 * nc * m * Ld * n1, (double)(nc + m) * Ld * 8.0 * n1, [&] {
-        return launch_block_update(n1, L, nc, m, PC_C64, F[cur], sF, coef, (long)nc * m, F[nxt], sF, st, d_act);
+      RUN(run_stage(ctx, PC_STAGE_UPDATE, 1, 8.0 * nc * m * S.Ld * n1, (double)(nc + m) * S.Ld * 8.0 * n1, [&] {
+        return launch_block_update(n1, L, nc, m, PC_C64, S.F[cur], sF, S.coef, S.sC, S.F[nxt], sF, g.st,
+                                   g.d_act);
       }));
-      if (any_zero) RUN(DEFL(n1, F[nxt], sF, PC_C64));
-      RUN(OP32(n1, m, F[nxt], sF, AF[nxt], sF));
+      if (S.any_zero) RUN(DEFL(n1, S.F[nxt], sF, PC_C64));
+      RUN(OP32(n1, m, S.F[nxt], sF, S.AF[nxt], sF));
     }
     if (!act2.empty()) {
       RUN(set_act(act2));
       const int n2 = (int)act2.size();
-      RUN(run_stage(ctx, PC_STAGE_UPDATE, 1, 8.0 * m * m * Ld * n2, (2.0 * 16.0 + 8.0) * m * Ld * n2, [&] {
-        return launch_update_df(n2, L, m, m, X64[cur], sX, coef, (long)nc * m, X64[nxt], sX, F[nxt] + 2L * m * L,
-                                sF, st, d_act);
+      RUN(run_stage(ctx, PC_STAGE_DFLOAT, 1, 8.0 * m * m * S.Ld * n2, (2.0 * 16.0 + 8.0) * m * S.Ld * n2, [&] {
+        return launch_update_df(n2, L, m, m, S.X64[cur], sX, S.coef, S.sC, S.X64[nxt], sX,
+                                S.F[nxt] + 2L * m * L, sF, g.st, g.d_act);
       }));
-      if (any_zero) RUN(DEFL(n2, X64[nxt], sX, PC_C128));
-      RUN(OP64(n2, X64[nxt], AX64));
+      if (S.any_zero) RUN(DEFL(n2, S.X64[nxt], sX, PC_C128));
+      RUN(OP64R(n2, S.X64[nxt], nxt));
     }
-    RUN(set_act(act));
-    if (any_zero) RUN(DEFL(na, F[nxt] + 2L * m * L, sF, PC_C64));
-    RUN(OP32(na, m, F[nxt] + 2L * m * L, sF, AF[nxt] + 2L * m * L, sF));
-    cur = nxt;
-    haveP = true;
+    RUN(set_act(g.act));
+    if (S.any_zero) RUN(DEFL(na, S.F[nxt] + 2L * m * L, sF, PC_C64));
+    RUN(OP32(na, m, S.F[nxt] + 2L * m * L, sF, S.AF[nxt] + 2L * m * L, sF));
+    g.cur = nxt;
+    g.haveP = true;
+    g.it = it + 1;
+    return residual();
   }
-#undef RUN
-  PC_CK(cudaStreamSynchronize(st));
+
+ private:
+  MixedShared &S;
+  Group &g;
+  pc_ctx *ctx;
+};
+
+}  // namespace
+
+int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam, const std::vector<int> &zero,
+                int nbands, int m, double tol, double *evals, void *evecs, int *iters, double *resid) {
+  const long n = ctx->n, L = 3 * n;
+  const long sF = 3L * m * L, sX = (long)m * L;
+  const int nmax = 3 * m;
+  int ngroups = ctx->opts.groups > 0 ? ctx->opts.groups : (nb >= 8 ? 2 : 1);
+  ngroups = std::max(1, std::min(ngroups, std::min(nb, 2)));
+  PC_CK(ctx->S[0].reserve(sizeof(float2) * (size_t)sF * nb));
+  PC_CK(ctx->S[1].reserve(sizeof(float2) * (size_t)sF * nb));
+  PC_CK(ctx->AS[0].reserve(sizeof(float2) * (size_t)sF * nb));
+  PC_CK(ctx->AS[1].reserve(sizeof(float2) * (size_t)sF * nb));
+  PC_CK(ctx->X64[0].reserve(sizeof(double2) * (size_t)sX * nb));
+  PC_CK(ctx->X64[1].reserve(sizeof(double2) * (size_t)sX * nb));
+  PC_CK(ctx->R32.reserve(sizeof(float2) * (size_t)sX * nb));
+  PC_CK(ctx->Gm.reserve(sizeof(double2) * (size_t)nb * nmax * nmax));
+  PC_CK(ctx->Hm.reserve(sizeof(double2) * (size_t)nb * nmax * nmax));
+  PC_CK(ctx->RQ.reserve(sizeof(double2) * (size_t)nb * m * nmax));
+  PC_CK(ctx->GX.reserve(sizeof(double2) * (size_t)nb * m * m));
+  PC_CK(ctx->coef.reserve(sizeof(double2) * (size_t)nb * nmax * m));
+  PC_CK(ctx->theta.reserve(sizeof(double) * (size_t)nb * m));
+  PC_CK(ctx->norms.reserve(sizeof(double) * (size_t)nb * m * 2));
+  PC_CK(ctx->rnorm.reserve(sizeof(double) * (size_t)nb * m * 3));
+  PC_CK(ctx->rank.reserve(sizeof(int) * (size_t)nb * (1 + ngroups)));
+  PC_CK(ctx->flag.reserve(sizeof(int) * (size_t)nb));
+  PC_CK(ctx->phase.reserve(sizeof(int) * (size_t)nb));
+  PC_CK(ctx->mask.reserve(sizeof(int) * (size_t)nb * m));
+  // scratch per group, sized for the group's largest k-point count
+  const int gmax = (nb + ngroups - 1) / ngroups;
+  size_t scr = std::max({gram_pair_scratch_bytes(gmax, L, nmax), gram_df_scratch_bytes(gmax, L, m),
+                         gram_scratch_bytes(gmax, L, m, nmax), residual_scratch_bytes(gmax, L, m),
+                         recompute_scratch_bytes(n, gmax, m), op_df_resid_scratch_bytes(ctx, gmax, m),
+                         sizeof(double2) * (size_t)gmax * 3 * m * 16,
+                         (size_t)16});
+  scr = (scr + 255) / 256 * 256;
+  PC_CK(ctx->scratch.reserve(scr * ngroups));
+  const size_t npin = (size_t)nb * m * 6;
+  if (ctx->pinned_count < npin) {
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    ctx->pinned = nullptr;
+    ctx->pinned_count = 0;
+    PC_CK(cudaMallocHost(&ctx->pinned, sizeof(double) * npin));
+    ctx->pinned_count = npin;
+  }
+  if (ngroups > 1 && !ctx->stream2) PC_CK(cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking));
+
+  MixedShared S;
+  S.ctx = ctx;
+  S.nb = nb;
+  S.nbands = nbands;
+  S.m = m;
+  S.n = n;
+  S.L = L;
+  S.sF = sF;
+  S.sX = sX;
+  S.nmax = nmax;
+  S.tol = tol;
+  S.drop = 1e-12;
+  S.kr = kr;
+  S.gam = &gam;
+  S.any_zero = false;
+  for (int b = 0; b < nb; ++b) S.any_zero |= zero[b] != 0;
+  for (int i = 0; i < 2; ++i) {
+    S.F[i] = ctx->S[i].as<float2>();
+    S.AF[i] = ctx->AS[i].as<float2>();
+    S.X64[i] = ctx->X64[i].as<double2>();
+  }
+  S.R32 = ctx->R32.as<float2>();
+  S.Gm = ctx->Gm.as<double2>();
+  S.Hm = ctx->Hm.as<double2>();
+  S.coef = ctx->coef.as<double2>();
+  S.RQ = ctx->RQ.as<double2>();
+  S.GX = ctx->GX.as<double2>();
+  S.theta = ctx->theta.as<double>();
+  S.norms = ctx->norms.as<double>();
+  S.rn = ctx->rnorm.as<double>();
+  S.d_zero = ctx->flag.as<int>();
+  S.d_phase = ctx->phase.as<int>();
+  S.d_mask = ctx->mask.as<int>();
+  S.h_theta = ctx->pinned;
+  S.h_norms = ctx->pinned + (size_t)nb * m;
+  S.h_rn = ctx->pinned + (size_t)nb * m * 3;
+  S.scr = scr;
+  S.sG = (long)nmax * nmax;
+  S.sRS = (long)m * nmax;
+  S.sC = (long)nmax * m;
+  S.phase.assign(nb, 1);
+  S.doublings.assign(nb, 0);
+  S.itcount.assign(nb, 0);
+  S.done.assign(nb, 0);
+  S.round_start.assign(nb, 0);
+  S.p1_start.assign(nb, 0);
+  S.hist.assign(nb, {});
+  S.evals = evals;
+  S.resid = resid;
+  S.evecs = evecs;
+  S.Ld = (double)L;
+  S.nd = (double)n;
+  S.fft_flops = 3.0 * 2.0 * 5.0 * S.nd * std::log2(S.nd) + 60.0 * S.nd;
+
+  cudaStream_t st0 = ctx->stream;
+  PC_CK(cudaMemcpyAsync(S.d_zero, zero.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st0));
+  PC_CK(cudaMemcpyAsync(S.d_phase, S.phase.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st0));
+
+  std::vector<Group> groups(ngroups);
+  cudaEvent_t ready = nullptr;
+  int rc = PC_OK;
+  for (int gi = 0; gi < ngroups; ++gi) {
+    Group &g = groups[gi];
+    g.b0 = (int)((long)nb * gi / ngroups);
+    g.b1 = (int)((long)nb * (gi + 1) / ngroups);
+    g.st = gi == 0 ? st0 : ctx->stream2;
+    g.d_act = ctx->rank.as<int>() + (size_t)nb * (1 + gi);
+    g.scratch = static_cast<char *>(ctx->scratch.p) + scr * gi;
+    PC_CK(cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming));
+  }
+  // the second stream starts after everything the caller's stream holds (setup, uploads above)
+  if (ngroups > 1) {
+    PC_CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    PC_CK(cudaEventRecord(ready, st0));
+    PC_CK(cudaStreamWaitEvent(ctx->stream2, ready, 0));
+  }
+  for (int gi = 0; gi < ngroups && rc == PC_OK; ++gi) rc = MixedSolve(S, groups[gi]).start();
+  // serve the groups in turn until all have finished
+  while (rc == PC_OK) {
+    bool any = false;
+    for (int gi = 0; gi < ngroups && rc == PC_OK; ++gi) {
+      Group &g = groups[gi];
+      if (g.finished) continue;
+      any = true;
+      const cudaError_t e = cudaEventSynchronize(g.ev);
+      if (e != cudaSuccess) {
+        rc = cuda_fail(e, "cudaEventSynchronize(group)", __FILE__, __LINE__);
+        break;
+      }
+      rc = harvest_timing(ctx);
+      if (rc == PC_OK) rc = MixedSolve(S, g).step();
+    }
+    if (!any) break;
+  }
+  // join: the caller's stream waits for the second group's work
+  if (ngroups > 1) {
+    cudaEvent_t fin = nullptr;
+    if (cudaEventCreateWithFlags(&fin, cudaEventDisableTiming) == cudaSuccess) {
+      cudaEventRecord(fin, ctx->stream2);
+      cudaStreamWaitEvent(st0, fin, 0);
+      cudaEventDestroy(fin);
+    }
+    cudaEventDestroy(ready);
+  }
+  const cudaError_t e0 = cudaStreamSynchronize(st0);
+  for (auto &g : groups)
+    if (g.ev) cudaEventDestroy(g.ev);
+  if (rc != PC_OK) return rc;
+  PC_CK(e0);
+  PC_CK(cudaStreamSynchronize(st0));
+  rc = harvest_timing(ctx);
+  if (rc != PC_OK) return rc;
   if (iters)
-    for (int b = 0; b < nb; ++b) iters[b] = itcount[b];
-  return status;
+    for (int b = 0; b < nb; ++b) iters[b] = S.itcount[b];
+  return S.status;
 }
+
+#undef RUN
 
 }  // namespace pc

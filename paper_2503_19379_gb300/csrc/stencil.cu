@@ -412,18 +412,27 @@ int launch_apply_op(pc_ctx *ctx, int nb, int m, int dtype, const void *X, long s
   return launch_op_t<float, 8, 4, 4>(ctx, nb, m, X, sx, Y, sy, act);
 }
 
-int launch_recompute(pc_ctx *ctx, int nb, int m, const void *X, long sx, double *out, const int *act) {
+size_t recompute_scratch_bytes(long n, int nb, int m) {
+  const int nchunk = (int)std::min<long>(64, (n + 4095) / 4096);
+  return sizeof(double) * 3 * (size_t)nb * m * nchunk;
+}
+
+int launch_recompute(pc_ctx *ctx, int nb, int m, const void *X, long sx, double *out, const int *act, void *scratch,
+                     size_t scratch_bytes) {
   if (nb == 0 || m == 0) return PC_OK;
   const long n = ctx->n;
   const int nchunk = (int)std::min<long>(64, (n + 4095) / 4096);
   const long chunk = (n + nchunk - 1) / nchunk;
-  const size_t need = sizeof(double) * 3 * (size_t)nb * m * nchunk;
-  PC_CK(ctx->scratch.reserve(need));
+  if (recompute_scratch_bytes(n, nb, m) > scratch_bytes) {
+    set_error("recompute: scratch too small");
+    return PC_EINVAL;
+  }
+  double *part = static_cast<double *>(scratch);
   recompute_partial_kernel<<<dim3(nchunk, m, nb), 256, 0, ctx->stream>>>(
       static_cast<const double2 *>(X), sx, ctx->m0d.as<double>(), ctx->kparam.as<KParam>(), act, ctx->logN,
-      (double)ctx->N, chunk, ctx->scratch.as<double>());
+      (double)ctx->N, chunk, part);
   PC_CK_LAUNCH();
-  recompute_reduce_kernel<<<nb, 64, 0, ctx->stream>>>(ctx->scratch.as<double>(), nchunk, m, act, out);
+  recompute_reduce_kernel<<<nb, 64, 0, ctx->stream>>>(part, nchunk, m, act, out);
   PC_CK_LAUNCH();
   return PC_OK;
 }
@@ -465,5 +474,6 @@ extern "C" int pc_recompute_norms(pc_ctx *ctx, int nb, const double *kpts, int m
   std::vector<double> g(nb, 1.0);
   int rc = upload_kpoints(ctx, nb, kpts, g.data());
   if (rc) return rc;
-  return launch_recompute(ctx, nb, m, X, (long)m * 3 * ctx->n, out, nullptr);
+  PC_CK(ctx->scratch.reserve(recompute_scratch_bytes(ctx->n, nb, m)));
+  return launch_recompute(ctx, nb, m, X, (long)m * 3 * ctx->n, out, nullptr, ctx->scratch.p, ctx->scratch.bytes);
 }

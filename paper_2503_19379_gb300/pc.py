@@ -23,7 +23,7 @@ class PCError(RuntimeError):
     pass
 
 
-STAGES = ("stencil", "precond", "gram", "rr", "update", "residual", "recompute", "other")
+STAGES = ("stencil", "precond", "gram", "rr", "update", "residual", "recompute", "other", "dfloat")
 
 
 class StageStat(C.Structure):
@@ -33,7 +33,8 @@ class StageStat(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("order", C.c_int), ("gamma_override", C.c_double), ("precond", C.c_int), ("precision", C.c_int),
-                ("guard", C.c_int), ("maxiter", C.c_int), ("max_doublings", C.c_int), ("seed", C.c_uint64)]
+                ("guard", C.c_int), ("maxiter", C.c_int), ("max_doublings", C.c_int), ("seed", C.c_uint64),
+                ("groups", C.c_int)]
 
 
 _LIB = None
