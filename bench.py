@@ -219,7 +219,10 @@ def kernel_case(args):
     g = torch.Generator(device="cuda").manual_seed(0)
     X = torch.randn((nb, m, 3, N, N, N), dtype=dt, device="cuda", generator=g)
     L = 3 * N ** 3
-    if args.kernel_case.startswith("stencil"):
+    if args.kernel_case == "stencil_df":
+        X = torch.randn((nb, m, 3, N, N, N), dtype=torch.complex128, device="cuda", generator=g)
+        run = lambda: solver.apply_op(kp, gam, X, double_float=True)
+    elif args.kernel_case.startswith("stencil"):
         run = lambda: solver.apply_op(kp, gam, X)
     elif args.kernel_case.startswith("precond"):
         Y = torch.empty_like(X)
@@ -273,7 +276,8 @@ def main():
                          "are split across ranks")
     ap.add_argument("--ref-iters", type=int, default=12)
     ap.add_argument("--kernel-case", default=None,
-                    choices=["stencil64", "stencil32", "precond64", "precond32", "gram64", "gram32", "rr"],
+                    choices=["stencil64", "stencil32", "stencil_df", "precond64", "precond32", "gram64", "gram32",
+                             "rr"],
                     help="run one hot kernel alone on a small batch (profiling) instead of the benchmark")
     args = ap.parse_args()
     if args.kernel_case:
@@ -372,6 +376,8 @@ def main():
         s64.close()
     sten = st["stencil"]
     sten_gbs = sten["bytes"] / max(sten["ms"], 1e-9) / 1e6
+    # stage times are CUDA-event intervals on the stream that ran them; the solve's two k-point groups run on two
+    # streams, so stage times of different groups overlap and their sum can exceed the wall time
     # stage times are CUDA-event intervals on the stream that ran them; the solve's two k-point groups run on two
     # streams, so stage times of different groups overlap and their sum can exceed the wall time
     stages = {k: {"ms_per_step": v["ms"] / args.steps, "calls_per_step": v["calls"] / args.steps,

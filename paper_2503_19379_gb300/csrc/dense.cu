@@ -139,7 +139,7 @@ __global__ void gram_reduce_kernel(const double2 *__restrict__ part, int nchunk,
                                    const int *__restrict__ act, double2 *__restrict__ G, long sg) {
   const int bi = blockIdx.x;
   const int b = act ? act[bi] : bi;
-  for (int i = threadIdx.x; i < p * q; i += blockDim.x) {
+  for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < p * q; i += gridDim.y * blockDim.x) {
     double2 s = cmake<double2>(0.0, 0.0);
     for (int c = 0; c < nchunk; ++c) s = cadd(s, part[((long)bi * nchunk + c) * p * q + i]);
     G[(long)b * sg + i] = s;
@@ -186,7 +186,8 @@ int launch_gram(int nb, long L, int p, int q, int dtype, const void *A, long sa,
     gram_partial_kernel<float><<<dim3(nchunk, 1, nb), 256, 0, st>>>(
         static_cast<const float2 *>(A), sa, static_cast<const float2 *>(B), sb, L, p, q, chunk, part, act);
   PC_CK_LAUNCH();
-  gram_reduce_kernel<<<nb, 256, 0, st>>>(part, nchunk, p, q, act, static_cast<double2 *>(G), sg > 0 ? sg : (long)p * q);
+  gram_reduce_kernel<<<dim3(nb, (p * q + 255) / 256), 256, 0, st>>>(part, nchunk, p, q, act, static_cast<double2 *>(G),
+                                                                    sg > 0 ? sg : (long)p * q);
   PC_CK_LAUNCH();
   return PC_OK;
 }
@@ -276,7 +277,7 @@ __global__ void gram_pair_reduce_kernel(const double2 *__restrict__ partG, const
                                         double2 *__restrict__ H, long sgb) {
   const int bi = blockIdx.x;
   const int b = act ? act[bi] : bi;
-  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < p * p; e += gridDim.y * blockDim.x) {
     const int i = e / p, j = e - i * p;
     if (i > j) continue;
     double2 sg = cmake<double2>(0.0, 0.0), sh = sg;
@@ -301,14 +302,15 @@ size_t gram_pair_scratch_bytes(int nb, long L, int p) {
 
 void launch_gram_pair_reduce(int nb, int nchunk, int p, const double2 *part, const int *act, void *G, void *H,
                              cudaStream_t st, long sg) {
-  gram_pair_reduce_kernel<<<nb, 256, 0, st>>>(part, part + (size_t)nb * nchunk * p * p, nchunk, p, act,
-                                              static_cast<double2 *>(G), static_cast<double2 *>(H),
-                                              sg > 0 ? sg : (long)p * p);
+  gram_pair_reduce_kernel<<<dim3(nb, (p * p + 255) / 256), 256, 0, st>>>(
+      part, part + (size_t)nb * nchunk * p * p, nchunk, p, act, static_cast<double2 *>(G), static_cast<double2 *>(H),
+      sg > 0 ? sg : (long)p * p);
 }
 
 void launch_gram_reduce(int nb, int nchunk, int p, int q, const double2 *part, const int *act, void *G,
                         cudaStream_t st, long sg) {
-  gram_reduce_kernel<<<nb, 256, 0, st>>>(part, nchunk, p, q, act, static_cast<double2 *>(G), sg > 0 ? sg : (long)p * q);
+  gram_reduce_kernel<<<dim3(nb, (p * q + 255) / 256), 256, 0, st>>>(part, nchunk, p, q, act, static_cast<double2 *>(G),
+                                                                    sg > 0 ? sg : (long)p * q);
 }
 
 template <typename T>
@@ -353,9 +355,9 @@ int launch_gram_pair(int nb, long L, int p, int dtype, const void *S, const void
   int rc = dtype == PC_C128 ? launch_gram_pair_t<double>(nb, L, p, S, AS, ss, part, nchunk, chunk, st, act)
                             : launch_gram_pair_t<float>(nb, L, p, S, AS, ss, part, nchunk, chunk, st, act);
   if (rc) return rc;
-  gram_pair_reduce_kernel<<<nb, 256, 0, st>>>(part, part + (size_t)nb * nchunk * p * p, nchunk, p, act,
-                                              static_cast<double2 *>(G), static_cast<double2 *>(H),
-                                              sg > 0 ? sg : (long)p * p);
+  gram_pair_reduce_kernel<<<dim3(nb, (p * p + 255) / 256), 256, 0, st>>>(
+      part, part + (size_t)nb * nchunk * p * p, nchunk, p, act, static_cast<double2 *>(G), static_cast<double2 *>(H),
+      sg > 0 ? sg : (long)p * p);
   PC_CK_LAUNCH();
   return PC_OK;
 }
@@ -923,8 +925,9 @@ extern "C" int pc_gram_pair_noalloc(int nb, long L, int p, int dtype, const void
   rc = dtype == PC_C128 ? launch_gram_pair_t<double>(nb, L, p, S, AS, ss, part, nchunk, chunk, st, nullptr)
                         : launch_gram_pair_t<float>(nb, L, p, S, AS, ss, part, nchunk, chunk, st, nullptr);
   if (rc) return rc;
-  gram_pair_reduce_kernel<<<nb, 256, 0, st>>>(part, part + (size_t)nb * nchunk * p * p, nchunk, p, nullptr,
-                                              static_cast<double2 *>(G), static_cast<double2 *>(H), (long)p * p);
+  gram_pair_reduce_kernel<<<dim3(nb, (p * p + 255) / 256), 256, 0, st>>>(
+      part, part + (size_t)nb * nchunk * p * p, nchunk, p, nullptr, static_cast<double2 *>(G),
+      static_cast<double2 *>(H), (long)p * p);
   PC_CK_LAUNCH();
   return PC_OK;
 }

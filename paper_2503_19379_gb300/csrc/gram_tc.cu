@@ -18,7 +18,7 @@
 //
 // Structure (one CTA per (k-point, K-chunk), 16 warps):
 //   warp 0       one thread issues 2D tensor-map copies (cp.async.bulk.tensor, 128-byte swizzle) of the A and B1
-//                tiles (32 floats x rows) into a 4-stage staging ring;
+//                tiles (32 floats x rows) into a staging ring of up to 4 stages of 2 K tiles each;
 //   warp 1       one thread issues the tcgen05.mma chain (12 per 32-float K tile) into the TMEM accumulators;
 //   warps 2..7   turn each staged tile into the hi/lo operand tiles of the K-major layout the tensor core reads
 //                (rows of 128 bytes, 16-byte chunks XOR-ed with the row index mod 8, as the copy left them; every
@@ -44,6 +44,7 @@ namespace {
 
 constexpr int TC_THREADS = 512;
 constexpr int TC_KT = 32;     // floats of K per tile (one 128-byte swizzle row)
+constexpr int TC_SPT = 2;     // K tiles per staging stage: each row arrives as a 256-byte run
 constexpr int TC_M = 128;     // MMA rows
 constexpr int TC_GROUP = 2;   // K tiles per accumulator drain
 constexpr int TC_NTR = 6;     // transform warps (2..7)
@@ -182,7 +183,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a, 
   const int ns = a.ns;
   const uint32_t region = (uint32_t)(a.QB + TC_M) * 128u;  // bytes of one hi (or lo) operand region
   const uint32_t opbuf = 2u * region;                       // hi + lo
-  const uint32_t stage_bytes = (uint32_t)(a.PB + a.QB) * 128u;
+  const uint32_t tile_bytes = (uint32_t)(a.PB + a.QB) * 128u;  // one staged K tile: A rows, then B1 rows
+  const uint32_t stage_bytes = TC_SPT * tile_bytes;
   const uint32_t off_stage = 2u * opbuf;
   const uint32_t off_bar = off_stage + (uint32_t)ns * stage_bytes;
   // barriers: full[ns], empty[ns], opready[2], opfree[2], accfull[2], accempty[2], done
@@ -234,25 +236,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a, 
 
   if (warp == 0) {
     // ------------------------------------------------ producer
-    const uint32_t tx = (uint32_t)(a.PB + a.QB) * 128u;  // whole boxes (rows past the tensor are zero-filled)
+    // whole boxes, TC_SPT tiles per stage (rows or tiles past the tensor are zero-filled; a last stage's second tile
+    // past the chunk is loaded and not used)
+    const uint32_t tx = stage_bytes;
     const int yA = (int)(b * a.cppA), yB = (int)(b * a.cppB);
+    const int nstage = (ntile + TC_SPT - 1) / TC_SPT;
     int issued = 0;
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-      for (int t = 0; t < ntile; ++t) {
-        const int s = t % ns;
-        if (!bar_wait(bar_empty + 8u * s, ((t / ns) & 1) ^ 1, abort)) break;
+      for (int q = 0; q < nstage; ++q) {
+        const int s = q % ns;
+        if (!bar_wait(bar_empty + 8u * s, ((q / ns) & 1) ^ 1, abort)) break;
         bar_expect_tx(bar_full + 8u * s, tx);
-        const int x = (t_begin + t) * TC_KT;  // float offset: a multiple of 32 (128 bytes)
         const uint32_t st = base + off_stage + (uint32_t)s * stage_bytes;
-        tma_load_2d(st, &tmA, x, yA, bar_full + 8u * s);
-        tma_load_2d(st + (uint32_t)a.PB * 128u, &tmB, x, yB, bar_full + 8u * s);
-        issued = t + 1;
+#pragma unroll
+        for (int h = 0; h < TC_SPT; ++h) {
+          const int x = (t_begin + q * TC_SPT + h) * TC_KT;  // float offset: a multiple of 32 (128 bytes)
+          tma_load_2d(st + h * tile_bytes, &tmA, x, yA, bar_full + 8u * s);
+          tma_load_2d(st + h * tile_bytes + (uint32_t)a.PB * 128u, &tmB, x, yB, bar_full + 8u * s);
+        }
+        issued = q + 1;
       }
       // drain: the last use of every stage must have landed before the CTA may exit
-      for (int t = max(0, issued - ns); t < issued; ++t)
-        bar_wait(bar_full + 8u * (t % ns), (t / ns) & 1, abort, false);
+      for (int q = max(0, issued - ns); q < issued; ++q)
+        bar_wait(bar_full + 8u * (q % ns), (q / ns) & 1, abort, false);
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -298,10 +306,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a, 
     const int tt = threadIdx.x - 64;
     const int nel = (a.PB + a.QB) * 8;  // 16-byte chunks per staged tile
     for (int t = 0; t < ntile; ++t) {
-      const int s = t % ns, u = t & 1;
-      if (!bar_wait(bar_full + 8u * s, (t / ns) & 1, abort)) break;
+      const int q = t / TC_SPT, hsub = t - q * TC_SPT;
+      const int s = q % ns, u = t & 1;
+      if (!bar_wait(bar_full + 8u * s, (q / ns) & 1, abort)) break;
       if (!bar_wait(bar_free + 8u * u, ((t >> 1) & 1) ^ 1, abort)) break;
-      const unsigned char *st = sm + off_stage + (size_t)s * stage_bytes;
+      const unsigned char *st = sm + off_stage + (size_t)s * stage_bytes + (size_t)hsub * tile_bytes;
       unsigned char *hi = sm + (size_t)u * opbuf, *lo = hi + region;
       for (int e = tt; e < nel; e += 32 * TC_NTR) {
         const int row = e >> 3, pc = e & 7;  // physical 16-byte chunk, kept in every row it is copied to
@@ -333,7 +342,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a, 
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) {
-        bar_arrive(bar_empty + 8u * s);
+        if (hsub == TC_SPT - 1 || t == ntile - 1) bar_arrive(bar_empty + 8u * s);  // stage consumed
         bar_arrive(bar_ready + 8u * u);
       }
     }
@@ -425,7 +434,7 @@ int sm_count() {
 constexpr int TC_SMEM_MAX = 232448;  // opt-in shared memory per block
 
 size_t tc_smem(int PB, int QB, int ns) {
-  return 1024 + 4 * (size_t)(QB + TC_M) * 128 + (size_t)ns * (PB + QB) * 128 + 8 * (2 * ns + 9) + 16;
+  return 1024 + 4 * (size_t)(QB + TC_M) * 128 + (size_t)ns * TC_SPT * (PB + QB) * 128 + 8 * (2 * ns + 9) + 16;
 }
 
 // chunks per k-point: whole waves of one CTA per SM where possible, within the partial-sum scratch

@@ -17,13 +17,16 @@
 // A GB300 SM retires about 2 FP64 FMA per clock, and a block's FP64 work here is a few hundred thousand operations,
 // so the kernel is bound by the length of its dependent chains. Every phase is therefore spread over the block:
 // substitutions column-oriented (one rank-1 row update per step for all threads), norms and dot products as warp
-// reductions, the back-transformation one warp per Ritz vector with the vector in registers, shared matrices with
-// an odd leading dimension (row-wise access by consecutive threads hits distinct banks), reciprocals of pivots
-// taken once. Bisection (step 5) runs two lanes per eigenvalue (trisection: each lane counts at one interior
-// point), first in FP32 down to ~30 eps32 |T| (backward-stable Sturm counts make the FP32 bracket exact for a
-// matrix within a few eps32 |T|; the bracket is widened by 16 eps32 |T| and verified by two FP64 counts, with the
-// Gershgorin interval as fallback), then in FP64 to the absolute width eps64 |T| (LAPACK's default for bisection,
-// below which the FP64 Sturm count itself is not accurate).
+// reductions only where a single value is needed (the FP64 pipe is the scarce unit: a 32-wide reduction spends 5
+// full-width FP64 additions on one sum, so matrix-vector products run one thread per row instead), the
+// back-transformation for all wanted vectors at once (partial dot products over row chunks, one short reduction
+// per vector, a parallel update), shared matrices with an odd leading dimension (row-wise access by consecutive
+// threads hits distinct banks), reciprocals of pivots taken once. Bisection (step 5) runs a group of 8 lanes per
+// eigenvalue (multisection: each lane counts at one of 8 interior points), first in FP32 down to ~30 eps32 |T|
+// (backward-stable Sturm counts make the FP32 bracket exact for a matrix within a few eps32 |T|; the bracket is
+// widened by 16 eps32 |T| and verified by two FP64 counts, with the Gershgorin interval as fallback), then in FP64
+// to the absolute width eps64 |T| (LAPACK's default for bisection, below which the FP64 Sturm count itself is not
+// accurate).
 #include <cfloat>
 #include <cmath>
 
@@ -117,28 +120,28 @@ __device__ __forceinline__ int sturm_count(const R *d, const R *e2, int r, R x, 
   return c;
 }
 
-// Trisection on the pair of lanes (2j, 2j+1): lane `side` counts at the interior point lo + (side + 1) (hi - lo) / 3;
-// both lanes apply the same update. Runs while any pair of the warp is still wider than its tolerance.
+// Multisection on a group of G lanes (G a power of two <= 32) per eigenvalue j: lane s of the group counts at the
+// interior point lo + (s + 1) (hi - lo) / (G + 1); the leading run of lanes whose count is <= j gives the new bracket
+// (the invariant count(lo) <= j < count(hi) holds whether or not the computed counts are monotone). All lanes of a
+// group apply the same update. Runs while any group of the warp is still wider than its tolerance.
 template <typename R>
-__device__ void trisect(const R *d, const R *e2, int r, R pivmin, int j, int side, bool active, R &lo, R &hi,
-                        R atol, R rtol, int maxit) {
+__device__ void multisect(const R *d, const R *e2, int r, R pivmin, int j, int s, int G, bool active, R &lo, R &hi,
+                          R atol, R rtol, int maxit) {
+  const int lane = threadIdx.x & 31, base = lane & ~(G - 1);
+  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
   for (int it = 0; it < maxit; ++it) {
     const bool open = active && !(hi - lo <= fmax(atol, rtol * fmax(fabs(lo), fabs(hi))) + pivmin);
     if (!__any_sync(0xffffffffu, open)) break;
-    const R third = (hi - lo) / R(3);
-    const R x1 = lo + third, x2 = lo + R(2) * third;
-    const int mine = open ? sturm_count<R>(d, e2, r, side ? x2 : x1, pivmin) : 0;
-    const int other = __shfl_xor_sync(0xffffffffu, mine, 1);
-    const int c1 = side ? other : mine, c2 = side ? mine : other;
+    const R step = (hi - lo) / R(G + 1);
+    const R x = lo + R(s + 1) * step;
+    const int c = open ? sturm_count<R>(d, e2, r, x, pivmin) : 0;
+    const unsigned bits = (__ballot_sync(0xffffffffu, c <= j) >> base) & gmask;
+    const int q = __ffs(~bits) - 1;  // leading lanes with count <= j (G when all)
     if (open) {
-      if (c1 > j) {
-        hi = x1;
-      } else if (c2 > j) {
-        lo = x1;
-        hi = x2;
-      } else {
-        lo = x2;
-      }
+      const R nlo = q > 0 ? lo + R(q) * step : lo;
+      const R nhi = q < G ? lo + R(q + 1) * step : hi;
+      lo = nlo;
+      hi = nhi;
     }
   }
 }
@@ -350,13 +353,17 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
     for (int i = 1 + tid; i < t; i += nt) vv[i] = B[(k + 1 + i) * LD + k];
     __syncthreads();
     for (int i = tid; i < t; i += nt) Vh[k * LD + i] = vv[i];
-    // p = tau B_sub v: one warp per row, lanes across the row
-    for (int i = warp; i < t; i += nwarp) {
+    // p = tau B_sub v: one thread per row (two accumulators; consecutive rows hit distinct banks, LD odd)
+    for (int i = tid; i < t; i += nt) {
       const double2 *row = B + (k + 1 + i) * LD + k + 1;
-      double2 s = cmake<double2>(0.0, 0.0);
-      for (int j = lane; j < t; j += 32) s = cadd(s, cmul(row[j], vv[j]));
-      s = warp_sum_d2(s);
-      if (lane == 0) pv[i] = cscale(s, tk);
+      double2 s0 = cmake<double2>(0.0, 0.0), s1 = s0;
+      int j = 0;
+      for (; j + 1 < t; j += 2) {
+        s0 = cadd(s0, cmul(row[j], vv[j]));
+        s1 = cadd(s1, cmul(row[j + 1], vv[j + 1]));
+      }
+      if (j < t) s0 = cadd(s0, cmul(row[j], vv[j]));
+      pv[i] = cscale(cadd(s0, s1), tk);
     }
     __syncthreads();
     if (warp == 0) {
@@ -428,32 +435,35 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
   }
   __syncthreads();
 
-  // 5. bisection: eigenvalue j (ascending) of T on lanes (2j, 2j+1)
+  // 5. bisection: eigenvalue j (ascending) of T on a group of G lanes (G = 8 up to 32 wanted eigenvalues)
   const int mm = m < r ? m : r;
-  if (tid < ((2 * mm + 31) & ~31)) {
-    const int j = tid >> 1, side = tid & 1;
-    const bool active = j < mm;
-    const int jj = active ? j : 0;
-    const double tn = s_tn, pivmin = s_pivmin;
-    // FP32 bracket
-    const float tn32 = (float)tn;
-    const float pivmin32 = 1e-30f * fmaxf(1.0f, tn32 * tn32);
-    float lo32 = (float)s_gl, hi32 = (float)s_gu;
-    lo32 -= fabsf(lo32) * 1e-6f + FLT_MIN;
-    hi32 += fabsf(hi32) * 1e-6f + FLT_MIN;
-    trisect<float>(d32, e232, r, pivmin32, jj, side, active, lo32, hi32, 32.0f * FLT_EPSILON * tn32, 0.0f, 60);
-    // widen, verify in FP64 (one count per lane), fall back to the Gershgorin interval
-    const double margin = 16.0 * FLT_EPSILON * tn + pivmin;
-    double lo = (double)lo32 - margin, hi = (double)hi32 + margin;
-    const int cnt = active ? sturm_count<double>(dd, e2, r, side ? hi : lo, pivmin) : 0;
-    const int cnt_o = __shfl_xor_sync(0xffffffffu, cnt, 1);
-    const int clo = side ? cnt_o : cnt, chi = side ? cnt : cnt_o;
-    if (!(clo <= jj && chi > jj)) {
-      lo = s_gl;
-      hi = s_gu;
+  {
+    const int G = mm <= nt / 8 ? 8 : (mm <= nt / 4 ? 4 : (mm <= nt / 2 ? 2 : 1));
+    if (tid < ((mm * G + 31) & ~31)) {
+      const int j = tid / G, s = tid % G, base = (tid & 31) & ~(G - 1);
+      const bool active = j < mm;
+      const int jj = active ? j : 0;
+      const double tn = s_tn, pivmin = s_pivmin;
+      // FP32 bracket
+      const float tn32 = (float)tn;
+      const float pivmin32 = 1e-30f * fmaxf(1.0f, tn32 * tn32);
+      float lo32 = (float)s_gl, hi32 = (float)s_gu;
+      lo32 -= fabsf(lo32) * 1e-6f + FLT_MIN;
+      hi32 += fabsf(hi32) * 1e-6f + FLT_MIN;
+      multisect<float>(d32, e232, r, pivmin32, jj, s, G, active, lo32, hi32, 32.0f * FLT_EPSILON * tn32, 0.0f, 60);
+      // widen, verify in FP64 (lanes 0 and 1 of the group count at the ends), fall back to the Gershgorin interval
+      const double margin = 16.0 * FLT_EPSILON * tn + pivmin;
+      double lo = (double)lo32 - margin, hi = (double)hi32 + margin;
+      const int cnt = (active && s < 2) ? sturm_count<double>(dd, e2, r, s == 0 ? lo : hi, pivmin) : 0;
+      const int clo = __shfl_sync(0xffffffffu, cnt, base), chi = __shfl_sync(0xffffffffu, cnt, base + (G > 1 ? 1 : 0));
+      const int chi1 = G > 1 ? chi : (active ? sturm_count<double>(dd, e2, r, hi, pivmin) : 0);
+      if (!(clo <= jj && chi1 > jj)) {
+        lo = s_gl;
+        hi = s_gu;
+      }
+      multisect<double>(dd, e2, r, pivmin, jj, s, G, active, lo, hi, RR_EPS * tn, 2.0 * RR_EPS, 200);
+      if (active && s == 0) w[j] = 0.5 * (lo + hi);
     }
-    trisect<double>(dd, e2, r, pivmin, jj, side, active, lo, hi, RR_EPS * tn, 2.0 * RR_EPS, 200);
-    if (active && side == 0) w[j] = 0.5 * (lo + hi);
   }
   __syncthreads();
   if (tid == 0) {
@@ -495,9 +505,64 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
     __syncthreads();
   }
 
-  // 7. back-transformation, one warp per Ritz vector held in registers (lane l owns rows l and l + 32):
-  // y = Q Phi z (reflectors applied last to first), then L^H x = y, coef = D P x
+  // 7. back-transformation y = Q Phi z (reflectors applied last to first), then L^H x = y, coef = D P x.
   double2 *out = coefg + (long)b * sc;
+  // Block-parallel form for all wanted vectors at once when the work space fits behind Z in B: Y (r x mm,
+  // row-major), per-step partial dot products (C chunks of rows x mm) and the reflector coefficients s (mm).
+  const long zsz = ((long)r * mm + 1) / 2;
+  const int C = mm > 0 ? nt / mm : 0;
+  if (mm > 0 && zsz + (long)r * mm + (long)C * mm + mm <= (long)n * LD) {
+    double2 *Y = B + zsz, *part = Y + (long)r * mm, *sj = part + (long)C * mm;
+    for (int e = tid; e < r * mm; e += nt) {
+      const int i = e / mm, j = e - i * mm;
+      Y[e] = cscale(phi[i], Z[(long)j * r + i]);
+    }
+    __syncthreads();
+    for (int k = r - 3; k >= 0; --k) {
+      const double tk = tau[k];
+      if (tk == 0.0) continue;  // uniform over the block
+      const int t = r - k - 1;
+      // s_j = tau v_k^H Y[k+1:, j]: thread (c, j) sums rows k+1+c, k+1+c+C, ...
+      if (tid < C * mm) {
+        const int c = tid / mm, j = tid - c * mm;
+        double2 acc = cmake<double2>(0.0, 0.0);
+        for (int i = c; i < t; i += C) acc = cadd(acc, cmulc(Vh[k * LD + i], Y[(long)(k + 1 + i) * mm + j]));
+        part[tid] = acc;
+      }
+      __syncthreads();
+      if (tid < mm) {
+        double2 acc = cmake<double2>(0.0, 0.0);
+        for (int c = 0; c < C; ++c) acc = cadd(acc, part[c * mm + tid]);
+        sj[tid] = cscale(acc, tk);
+      }
+      __syncthreads();
+      for (int e = tid; e < t * mm; e += nt) {
+        const int i = e / mm, j = e - i * mm;
+        Y[(long)(k + 1 + i) * mm + j] = csub(Y[(long)(k + 1 + i) * mm + j], cmul(Vh[k * LD + i], sj[j]));
+      }
+      __syncthreads();
+    }
+    // L^H x = y, column-oriented from the last row: row i, final once all rows below have been applied, updates the
+    // rows above it (the scaling by 1/L_ii is folded into the coefficient and applied to row i at the end)
+    for (int i = r - 1; i > 0; --i) {
+      for (int e = tid; e < i * mm; e += nt) {
+        const int l = e / mm, j = e - l * mm;
+        const double2 c = cscale(A[i * LD + l], dinv[i]);  // L_il / L_ii, used conjugated
+        Y[(long)l * mm + j] = csub(Y[(long)l * mm + j], cmulc(c, Y[(long)i * mm + j]));
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < n * m; e += nt) out[e] = cmake<double2>(0.0, 0.0);
+    __syncthreads();
+    for (int e = tid; e < r * mm; e += nt) {
+      const int i = e / mm, j = e - i * mm;
+      out[perm[i] * m + j] = cscale(Y[e], dinv[i] * dsc[perm[i]]);
+    }
+    for (int j = tid; j < m; j += nt) thetag[(long)b * m + j] = j < mm ? w[j] : 0.0;
+    if (rankg && tid == 0) rankg[b] = r;
+    return;
+  }
+  // Otherwise one warp per Ritz vector held in registers (lane l owns rows l and l + 32).
   for (int j = warp; j < m; j += nwarp) {
     double2 y0 = cmake<double2>(0.0, 0.0), y1 = y0;
     const int i0 = lane, i1 = lane + 32;

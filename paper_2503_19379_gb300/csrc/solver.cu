@@ -294,9 +294,11 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
   PC_CK(ctx->rnorm.reserve(sizeof(double) * (size_t)nb * m * 3));
   PC_CK(ctx->rank.reserve(sizeof(int) * (size_t)nb * 2));
   PC_CK(ctx->flag.reserve(sizeof(int) * (size_t)nb));
-  const size_t scr = std::max({gram_pair_scratch_bytes(nb, L, nmax), residual_scratch_bytes(nb, L, m),
-                               sizeof(double2) * (size_t)nb * 3 * m * 16, sizeof(double) * 3 * (size_t)nb * m * 64,
-                               (size_t)16});
+  // the chunked reductions' partial sums depend on the active count (not monotonically): size for every count
+  size_t scr = 16;
+  for (int na = 1; na <= nb; ++na)
+    scr = std::max({scr, gram_pair_scratch_bytes(na, L, nmax), residual_scratch_bytes(na, L, m),
+                    sizeof(double2) * (size_t)na * 3 * m * 16, sizeof(double) * 3 * (size_t)na * m * 64});
   PC_CK(ctx->scratch.reserve(scr));
   int *d_act = ctx->rank.as<int>() + nb;
   int *d_zero = ctx->flag.as<int>();

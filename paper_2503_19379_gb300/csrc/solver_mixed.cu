@@ -26,6 +26,9 @@
 // block per k-point, the host decisions leave the GPU idle) behind the other group's bandwidth-bound kernels.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <utility>
 #include <vector>
 
 #include "pc_internal.cuh"
@@ -50,6 +53,7 @@ struct MixedShared {
   const double *kr;
   std::vector<double> *gam;
   bool any_zero;
+  std::vector<int> zero;  // per k-point: k reduced to 0 (the constant fields are projected out)
   float2 *F[2], *AF[2];
   double2 *X64[2];
   float2 *R32;
@@ -62,11 +66,13 @@ struct MixedShared {
   // different iterations never overlap: G and H (nmax x nmax), R^H S (m x nmax), coefficients (nmax x m)
   long sG, sRS, sC;
   std::vector<int> phase, doublings, itcount, done, round_start, p1_start;
-  std::vector<std::vector<double>> hist;
+  std::vector<std::vector<std::pair<int, double>>> hist;  // per k-point: (iteration, largest relative residual)
+  double p1_floor = 3e-3, p1_stall = 0.25;                // phase switch thresholds (see step())
   double *evals, *resid;
   void *evecs;
   int status = PC_OK;
   double Ld, nd, fft_flops;
+  bool verbose = false;  // host-side trace of the iteration (stderr), PC_VERBOSE set
 };
 
 struct Group {
@@ -114,10 +120,19 @@ class MixedSolve {
                                                  g.d_act);
                      });
   }
-  int DEFL(int nbk, void *X, long sx, int dtype) {
-    return run_stage(ctx, PC_STAGE_OTHER, 2, 4.0 * S.Ld * S.m * nbk,
-                     2.0 * S.Ld * (dtype == PC_C64 ? 8.0 : 16.0) * S.m * nbk,
-                     [&] { return launch_deflate(nbk, S.n, S.m, X, sx, S.d_zero, g.scratch, g.st, g.d_act, dtype); });
+  // projection of the constant fields, on the k = 0 points of `list` only (the active list of the launches around
+  // it, restored afterwards)
+  int DEFL(const std::vector<int> &list, void *X, long sx, int dtype) {
+    if (!S.any_zero) return PC_OK;
+    std::vector<int> z;
+    for (int b : list)
+      if (S.zero[b]) z.push_back(b);
+    if (z.empty()) return PC_OK;
+    RUN(set_act(z));
+    const int nz = (int)z.size();
+    RUN(run_stage(ctx, PC_STAGE_OTHER, 2, 4.0 * S.Ld * S.m * nz, 2.0 * S.Ld * (dtype == PC_C64 ? 8.0 : 16.0) * S.m * nz,
+                  [&] { return launch_deflate(nz, S.n, S.m, X, sx, S.d_zero, g.scratch, g.st, g.d_act, dtype); }));
+    return set_act(list);
   }
 
   // initial block (FP64 generator, narrowed) and Rayleigh-Ritz on span(X0), then the first residual
@@ -131,7 +146,7 @@ class MixedSolve {
     RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, S.Ld * 16.0 * m * na, [&] {
       return launch_init_block(na, L, m, ctx->opts.seed, 0, S.X64[0], sX, g.st, nullptr, g.d_act);
     }));
-    if (S.any_zero) RUN(DEFL(na, S.X64[0], sX, PC_C128));
+    RUN(DEFL(g.act, S.X64[0], sX, PC_C128));
     RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, S.Ld * 24.0 * m * na,
                   [&] { return launch_narrow(na, L, m, S.X64[0], sX, S.F[0], sF, g.st, g.d_act); }));
     RUN(OP32(na, m, S.F[0], sF, S.AF[0], sF));
@@ -193,16 +208,34 @@ class MixedSolve {
     const int it = g.it, cur = g.cur, maxiter = ctx->opts.maxiter;
     std::vector<int> act1, act2;
     for (int b : g.act) (S.phase[b] == 1 ? act1 : act2).push_back(b);
-    // ---- phase 1 -> 2 when the complex64 residual stops falling (or is already small)
+    if (S.verbose)
+      for (int b : g.act) {
+        double mx = 0;
+        for (int j = 0; j < nbands; ++j) mx = std::max(mx, relres(b, j));
+        std::fprintf(stderr, "[pc-mixed] it %d k %d phase %d maxres %.3e\n", it, b, S.phase[b], mx);
+      }
+    // ---- phase 1 -> 2 once the complex64 residual stops falling, at its floor. The floor is eps32 times the stencil's
+    // magnitude over lambda: ~3e-3 for most k-points here, but ~6e-2 near Gamma where the penalty gamma = 2 / |k|^2
+    // is large, so a stall is accepted at any level below 0.25 (the early iterations, whose residual plateaus near 1
+    // while the search space builds up, are not a floor). Stalled: the best residual of the last 5 iterations is not
+    // 30% below the best of the 5 before. The history holds one entry per iteration: a decision pass that repeats an
+    // iteration (phase switch, gamma doubling) does not add one. Also switch below 3e-3, or after 150 iterations.
     std::vector<int> sw;
     for (int b : act1) {
       double mx = 0;
       for (int j = 0; j < nbands; ++j) mx = std::max(mx, relres(b, j));
       if (!(mx == mx)) mx = 1e300;  // NaN guard
-      S.hist[b].push_back(mx);
-      const int k1 = (int)S.hist[b].size();
-      const bool stalled = k1 > 8 && mx > 0.7 * S.hist[b][k1 - 6];
-      if (stalled || mx < 1e-4 || it - S.p1_start[b] >= 150) sw.push_back(b);
+      auto &h = S.hist[b];
+      if (h.empty() || h.back().first != it) h.push_back({it, mx});
+      const int k1 = (int)h.size();
+      bool stalled = false;
+      if (k1 >= 10 && mx < S.p1_stall) {
+        double recent = 1e300, before = 1e300;
+        for (int q = k1 - 5; q < k1; ++q) recent = std::min(recent, h[q].second);
+        for (int q = k1 - 10; q < k1 - 5; ++q) before = std::min(before, h[q].second);
+        stalled = recent > 0.7 * before;
+      }
+      if (stalled || mx < S.p1_floor || it - S.p1_start[b] >= 150) sw.push_back(b);
     }
     // ---- phase 2: convergence on FP64 residuals, then Algorithm 4.1
     std::vector<int> conv;
@@ -296,7 +329,7 @@ class MixedSolve {
         RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, 0.0, [&] {
           return launch_init_block(nr, L, m, seed, 0, S.X64[cur], sX, g.st, S.d_mask, g.d_act);
         }));
-        if (S.any_zero) RUN(DEFL(nr, S.X64[cur], sX, PC_C128));
+        RUN(DEFL(redo, S.X64[cur], sX, PC_C128));
         RUN(OP64R(nr, S.X64[cur], cur));
         if (g.haveP) RUN(OP32(nr, m, S.F[cur] + 2L * m * L, sF, S.AF[cur] + 2L * m * L, sF));
       }
@@ -311,7 +344,7 @@ class MixedSolve {
     RUN(run_stage(ctx, PC_STAGE_PRECOND, 5, S.fft_flops * na * m, 2.0 * S.Ld * 8.0 * na * m, [&] {
       return launch_precond(ctx, na, m, PC_C64, S.F[cur] + (long)m * L, sF, S.F[cur] + (long)m * L, sF, g.d_act);
     }));
-    if (S.any_zero) RUN(DEFL(na, S.F[cur] + (long)m * L, sF, PC_C64));
+    RUN(DEFL(g.act, S.F[cur] + (long)m * L, sF, PC_C64));
     RUN(OP32(na, m, S.F[cur] + (long)m * L, sF, S.AF[cur] + (long)m * L, sF));
     // ---- pencil: complex64 products over [X | W | P], the R^H Q coupling, FP64 X-X block in phase 2
     RUN(run_stage(ctx, PC_STAGE_GRAM, 2, 8.0 * nc * (nc + 1) * S.Ld * na, 2.0 * nc * S.Ld * 8.0 * na, [&] {
@@ -351,7 +384,7 @@ class MixedSolve {
         return launch_block_update(n1, L, nc, m, PC_C64, S.F[cur], sF, S.coef, S.sC, S.F[nxt], sF, g.st,
                                    g.d_act);
       }));
-      if (S.any_zero) RUN(DEFL(n1, S.F[nxt], sF, PC_C64));
+      RUN(DEFL(act1, S.F[nxt], sF, PC_C64));
       RUN(OP32(n1, m, S.F[nxt], sF, S.AF[nxt], sF));
     }
     if (!act2.empty()) {
@@ -361,11 +394,11 @@ class MixedSolve {
         return launch_update_df(n2, L, m, m, S.X64[cur], sX, S.coef, S.sC, S.X64[nxt], sX,
                                 S.F[nxt] + 2L * m * L, sF, g.st, g.d_act);
       }));
-      if (S.any_zero) RUN(DEFL(n2, S.X64[nxt], sX, PC_C128));
+      RUN(DEFL(act2, S.X64[nxt], sX, PC_C128));
       RUN(OP64R(n2, S.X64[nxt], nxt));
     }
     RUN(set_act(g.act));
-    if (S.any_zero) RUN(DEFL(na, S.F[nxt] + 2L * m * L, sF, PC_C64));
+    RUN(DEFL(g.act, S.F[nxt] + 2L * m * L, sF, PC_C64));
     RUN(OP32(na, m, S.F[nxt] + 2L * m * L, sF, S.AF[nxt] + 2L * m * L, sF));
     g.cur = nxt;
     g.haveP = true;
@@ -409,11 +442,13 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
   PC_CK(ctx->mask.reserve(sizeof(int) * (size_t)nb * m));
   // scratch per group, sized for the group's largest k-point count
   const int gmax = (nb + ngroups - 1) / ngroups;
-  size_t scr = std::max({gram_pair_scratch_bytes(gmax, L, nmax), gram_df_scratch_bytes(gmax, L, m),
-                         gram_scratch_bytes(gmax, L, m, nmax), residual_scratch_bytes(gmax, L, m),
-                         recompute_scratch_bytes(n, gmax, m), op_df_resid_scratch_bytes(ctx, gmax, m),
-                         sizeof(double2) * (size_t)gmax * 3 * m * 16,
-                         (size_t)16});
+  // the chunked reductions' partial sums depend on the active count (not monotonically): size for every count
+  size_t scr = 16;
+  for (int na = 1; na <= gmax; ++na)
+    scr = std::max({scr, gram_pair_scratch_bytes(na, L, nmax), gram_df_scratch_bytes(na, L, m),
+                    gram_scratch_bytes(na, L, m, nmax), residual_scratch_bytes(na, L, m),
+                    recompute_scratch_bytes(n, na, m), op_df_resid_scratch_bytes(ctx, na, m),
+                    sizeof(double2) * (size_t)na * 3 * m * 16});
   scr = (scr + 255) / 256 * 256;
   PC_CK(ctx->scratch.reserve(scr * ngroups));
   const size_t npin = (size_t)nb * m * 6;
@@ -437,11 +472,14 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
   S.sX = sX;
   S.nmax = nmax;
   S.tol = tol;
-  S.drop = 1e-12;
+  // rank decision of the Rayleigh-Ritz (pivots of the unit-diagonal Gram): the complex64 products carry errors of
+  // ~1e-7, so directions whose independent part has a pivot below 1e-6 are noise and are dropped
+  S.drop = 1e-6;
   S.kr = kr;
   S.gam = &gam;
   S.any_zero = false;
   for (int b = 0; b < nb; ++b) S.any_zero |= zero[b] != 0;
+  S.zero = zero;
   for (int i = 0; i < 2; ++i) {
     S.F[i] = ctx->S[i].as<float2>();
     S.AF[i] = ctx->AS[i].as<float2>();
@@ -479,6 +517,7 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
   S.Ld = (double)L;
   S.nd = (double)n;
   S.fft_flops = 3.0 * 2.0 * 5.0 * S.nd * std::log2(S.nd) + 60.0 * S.nd;
+  S.verbose = std::getenv("PC_VERBOSE") != nullptr;
 
   cudaStream_t st0 = ctx->stream;
   PC_CK(cudaMemcpyAsync(S.d_zero, zero.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st0));
