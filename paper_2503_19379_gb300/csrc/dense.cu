@@ -655,21 +655,43 @@ int launch_rr_patch(int nb, int n, int m, void *G, void *H, const void *RS, cons
   return PC_OK;
 }
 
-// Y (FP64) = X (complex64) for m columns of length L per k-point.
-__global__ void widen_kernel(const float2 *__restrict__ X, long sx, double2 *__restrict__ Y, long sy, long L,
+// Y (double-float pairs, PC_DFS) = X (complex64) for m columns of length L per k-point: (x, 0) is exact.
+__global__ void widen_kernel(const float2 *__restrict__ X, long sx, float4 *__restrict__ Y, long sy, long L,
                              const int *__restrict__ act) {
   const int b = act ? act[blockIdx.z] : (int)blockIdx.z, j = blockIdx.y;
   const float2 *x = X + (long)b * sx + (long)j * L;
-  double2 *y = Y + (long)b * sy + (long)j * L;
-  for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < L; l += (long)gridDim.x * blockDim.x)
-    y[l] = cmake<double2>((double)x[l].x, (double)x[l].y);
+  float4 *y = Y + (long)b * sy + (long)j * L;
+  for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < L; l += (long)gridDim.x * blockDim.x) {
+    const float2 v = x[l];
+    y[l] = make_float4(v.x, 0.f, v.y, 0.f);
+  }
 }
 
 int launch_widen(int nb, long L, int m, const void *X, long sx, void *Y, long sy, cudaStream_t st, const int *act) {
   if (nb == 0 || m == 0) return PC_OK;
   const unsigned gx = (unsigned)std::min<long>(256, (L + 255) / 256);
-  widen_kernel<<<dim3(gx, m, nb), 256, 0, st>>>(static_cast<const float2 *>(X), sx, static_cast<double2 *>(Y), sy, L,
+  widen_kernel<<<dim3(gx, m, nb), 256, 0, st>>>(static_cast<const float2 *>(X), sx, static_cast<float4 *>(Y), sy, L,
                                                 act);
+  PC_CK_LAUNCH();
+  return PC_OK;
+}
+
+// Y (complex128) = hi + lo of X (double-float pairs) for m columns of length L per k-point.
+__global__ void pairs_to_c128_kernel(const float4 *__restrict__ X, long sx, double2 *__restrict__ Y, long sy, long L,
+                                     const int *__restrict__ act) {
+  const int b = act ? act[blockIdx.z] : (int)blockIdx.z, j = blockIdx.y;
+  const float4 *x = X + (long)b * sx + (long)j * L;
+  double2 *y = Y + (long)b * sy + (long)j * L;
+  for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < L; l += (long)gridDim.x * blockDim.x)
+    y[l] = ld_c128(x + l);
+}
+
+int launch_pairs_to_c128(int nb, long L, int m, const void *X, long sx, void *Y, long sy, cudaStream_t st,
+                         const int *act) {
+  if (nb == 0 || m == 0) return PC_OK;
+  const unsigned gx = (unsigned)std::min<long>(256, (L + 255) / 256);
+  pairs_to_c128_kernel<<<dim3(gx, m, nb), 256, 0, st>>>(static_cast<const float4 *>(X), sx, static_cast<double2 *>(Y),
+                                                        sy, L, act);
   PC_CK_LAUNCH();
   return PC_OK;
 }
@@ -695,19 +717,21 @@ int launch_narrow(int nb, long L, int m, const void *X, long sx, void *Y, long s
 
 // ------------------------------------------------------------------------------------------------ k = 0 projection
 // Removes the mean of each component of each column for k-points with flags[b] != 0 (the constant kernel fields).
-template <typename T>
-__global__ void __launch_bounds__(256) mean_partial_kernel(const cplx<T> *__restrict__ X, long sx, long n, long chunk,
+// S: the element storage, float2 (complex64), double2 (complex128) or float4 (double-float pairs)
+template <typename S>
+__global__ void __launch_bounds__(256) mean_partial_kernel(const S *__restrict__ X, long sx, long n, long chunk,
                                                           const int *__restrict__ flags, double2 *__restrict__ part,
                                                           const int *__restrict__ act) {
   const int bi = blockIdx.z, col = blockIdx.y;  // col = j * 3 + comp
   const int b = act ? act[bi] : bi;
   if (!flags[b]) return;
-  const cplx<T> *x = X + (long)b * sx + (long)col * n;
+  const S *x = X + (long)b * sx + (long)col * n;
   double sr = 0, si = 0;
   const long beg = (long)blockIdx.x * chunk, end = min(n, beg + chunk);
   for (long l = beg + threadIdx.x; l < end; l += blockDim.x) {
-    sr += (double)x[l].x;
-    si += (double)x[l].y;
+    const double2 v = ld_c128(x + l);
+    sr += v.x;
+    si += v.y;
   }
   __shared__ double red[2][256];
   red[0][threadIdx.x] = sr;
@@ -723,8 +747,8 @@ __global__ void __launch_bounds__(256) mean_partial_kernel(const cplx<T> *__rest
   if (threadIdx.x == 0) part[((long)bi * gridDim.y + col) * gridDim.x + blockIdx.x] = cmake<double2>(red[0][0], red[1][0]);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) mean_subtract_kernel(cplx<T> *__restrict__ X, long sx, long n, int nchunk,
+template <typename S>
+__global__ void __launch_bounds__(256) mean_subtract_kernel(S *__restrict__ X, long sx, long n, int nchunk,
                                                            const int *__restrict__ flags,
                                                            const double2 *__restrict__ part,
                                                            const int *__restrict__ act) {
@@ -738,12 +762,34 @@ __global__ void __launch_bounds__(256) mean_subtract_kernel(cplx<T> *__restrict_
     mean = cmake<double2>(s.x / (double)n, s.y / (double)n);
   }
   __syncthreads();
-  cplx<T> *x = X + (long)b * sx + (long)col * n;
-  const T mr = (T)mean.x, mi = (T)mean.y;
-  for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x) {
-    x[l].x -= mr;
-    x[l].y -= mi;
+  S *x = X + (long)b * sx + (long)col * n;
+  if constexpr (std::is_same<S, float4>::value) {
+    const df mr = df_from(mean.x), mi = df_from(mean.y);
+    for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x) {
+      cdf v = ld_cdf(x + l);
+      v.re = df_sub(v.re, mr);
+      v.im = df_sub(v.im, mi);
+      st_cdf(x + l, v);
+    }
+  } else {
+    using T = decltype(S{}.x);
+    const T mr = (T)mean.x, mi = (T)mean.y;
+    for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x) {
+      x[l].x -= mr;
+      x[l].y -= mi;
+    }
   }
+}
+
+template <typename S>
+static int deflate_t(int nb, long n, int m, void *X, long sx, const int *flags, double2 *part, int nchunk, long chunk,
+                     unsigned gx, cudaStream_t st, const int *act) {
+  mean_partial_kernel<S><<<dim3(nchunk, 3 * m, nb), 256, 0, st>>>(static_cast<const S *>(X), sx, n, chunk, flags, part,
+                                                                  act);
+  PC_CK_LAUNCH();
+  mean_subtract_kernel<S><<<dim3(gx, 3 * m, nb), 256, 0, st>>>(static_cast<S *>(X), sx, n, nchunk, flags, part, act);
+  PC_CK_LAUNCH();
+  return PC_OK;
 }
 
 int launch_deflate(int nb, long n, int m, void *X, long sx, const int *flags, void *scratch, cudaStream_t st,
@@ -753,21 +799,9 @@ int launch_deflate(int nb, long n, int m, void *X, long sx, const int *flags, vo
   const long chunk = (n + nchunk - 1) / nchunk;
   double2 *part = static_cast<double2 *>(scratch);
   const unsigned gx = (unsigned)std::min<long>(64, (n + 255) / 256);
-  if (dtype == PC_C128) {
-    mean_partial_kernel<double><<<dim3(nchunk, 3 * m, nb), 256, 0, st>>>(static_cast<const double2 *>(X), sx, n, chunk,
-                                                                        flags, part, act);
-    PC_CK_LAUNCH();
-    mean_subtract_kernel<double><<<dim3(gx, 3 * m, nb), 256, 0, st>>>(static_cast<double2 *>(X), sx, n, nchunk, flags,
-                                                                     part, act);
-  } else {
-    mean_partial_kernel<float><<<dim3(nchunk, 3 * m, nb), 256, 0, st>>>(static_cast<const float2 *>(X), sx, n, chunk,
-                                                                       flags, part, act);
-    PC_CK_LAUNCH();
-    mean_subtract_kernel<float><<<dim3(gx, 3 * m, nb), 256, 0, st>>>(static_cast<float2 *>(X), sx, n, nchunk, flags,
-                                                                    part, act);
-  }
-  PC_CK_LAUNCH();
-  return PC_OK;
+  if (dtype == PC_C128) return deflate_t<double2>(nb, n, m, X, sx, flags, part, nchunk, chunk, gx, st, act);
+  if (dtype == PC_DFS) return deflate_t<float4>(nb, n, m, X, sx, flags, part, nchunk, chunk, gx, st, act);
+  return deflate_t<float2>(nb, n, m, X, sx, flags, part, nchunk, chunk, gx, st, act);
 }
 
 // ------------------------------------------------------------------------------------------------ initial blocks
@@ -780,14 +814,15 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z;
 }
 
-__global__ void init_block_kernel(double2 *__restrict__ X, long sx, long L, uint64_t seed, int kidx0,
+template <typename S>
+__global__ void init_block_kernel(S *__restrict__ X, long sx, long L, uint64_t seed, int kidx0,
                                   const int *__restrict__ mask, int m, const int *__restrict__ act) {
   const uint64_t G = 0x9E3779B97F4A7C15ULL;
   const int b = act ? act[blockIdx.z] : (int)blockIdx.z, j = blockIdx.y;
   if (mask && !mask[b * m + j]) return;
   const uint64_t stream = (uint64_t)(kidx0 + b) * 4096ULL + (uint64_t)j;
   const uint64_t key = mix64(seed + G * (stream + 1ULL));
-  double2 *x = X + (long)b * sx + (long)j * L;
+  S *x = X + (long)b * sx + (long)j * L;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += (long)gridDim.x * blockDim.x) {
     const uint64_t d1 = mix64(key + G * (2ULL * (uint64_t)e + 1ULL));
     const uint64_t d2 = mix64(key + G * (2ULL * (uint64_t)e + 2ULL));
@@ -796,15 +831,23 @@ __global__ void init_block_kernel(double2 *__restrict__ X, long sx, long L, uint
     const double rad = sqrt(-2.0 * log(u1));
     double s, c;
     sincospi(2.0 * u2, &s, &c);
-    x[e] = cmake<double2>(rad * c, rad * s);
+    if constexpr (std::is_same<S, float4>::value)
+      st_cdf(x + e, cdf_from(cmake<double2>(rad * c, rad * s)));
+    else
+      x[e] = cmake<double2>(rad * c, rad * s);
   }
 }
 
 int launch_init_block(int nb, long L, int m, uint64_t seed, int kidx0, void *X, long sx, cudaStream_t st,
-                      const int *mask, const int *act) {
+                      const int *mask, const int *act, int dtype) {
   if (nb == 0 || m == 0) return PC_OK;
   const unsigned gx = (unsigned)std::min<long>(256, (L + 255) / 256);
-  init_block_kernel<<<dim3(gx, m, nb), 256, 0, st>>>(static_cast<double2 *>(X), sx, L, seed, kidx0, mask, m, act);
+  if (dtype == PC_DFS)
+    init_block_kernel<float4><<<dim3(gx, m, nb), 256, 0, st>>>(static_cast<float4 *>(X), sx, L, seed, kidx0, mask, m,
+                                                               act);
+  else
+    init_block_kernel<double2><<<dim3(gx, m, nb), 256, 0, st>>>(static_cast<double2 *>(X), sx, L, seed, kidx0, mask,
+                                                                m, act);
   PC_CK_LAUNCH();
   return PC_OK;
 }

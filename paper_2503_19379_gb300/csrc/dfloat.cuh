@@ -90,5 +90,32 @@ __device__ __forceinline__ void cdf_mac(cdf &s, cdf a, cdf b) {
   df_mac(s.im, a.im, b.re);
 }
 __device__ __forceinline__ cdf cdf_scale2(cdf a, float s) { return cdf{df_scale2(a.re, s), df_scale2(a.im, s)}; }
+// x + f for a double-float x and an FP32 f
+__device__ __forceinline__ df df_addf(df x, float f) {
+  const df s = two_sum(x.hi, f);
+  return quick_two_sum(s.hi, s.lo + x.lo);
+}
+
+// Storage of complex double-float blocks. The solver keeps its FP64-accurate block as pairs (re.hi, re.lo, im.hi,
+// im.lo) in one float4 (16 bytes, like complex128), so that its kernels read and write it without conversions:
+// converting a double to a pair costs four FP64-pipe instructions and back three, more FP64 work than the
+// double-float arithmetic does in FP32. complex128 blocks (the public entry points) convert on load and store.
+__device__ __forceinline__ cdf ld_cdf(const double2 *p) { return cdf_from(*p); }
+__device__ __forceinline__ cdf ld_cdf(const float4 *p) {
+  const float4 v = *p;
+  return cdf{df{v.x, v.y}, df{v.z, v.w}};
+}
+__device__ __forceinline__ void st_cdf(double2 *p, cdf z) { *p = cdf_to(z); }
+__device__ __forceinline__ void st_cdf(float4 *p, cdf z) { *p = make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo); }
+// FP64 value of a stored element (for the FP64 checks and conversions off the iteration path)
+__device__ __forceinline__ double2 ld_c128(const double2 *p) { return *p; }
+__device__ __forceinline__ double2 ld_c128(const float2 *p) {
+  const float2 v = *p;
+  return make_double2((double)v.x, (double)v.y);
+}
+__device__ __forceinline__ double2 ld_c128(const float4 *p) {
+  const float4 v = *p;
+  return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
 
 }  // namespace pc

@@ -1,11 +1,14 @@
-// The FP64-accurate kernels of the mixed-precision solve, in double-float arithmetic (dfloat.cuh): the block X and
-// its image AX stay FP64 in memory, every element is split into hi + lo FP32 on load, and all arithmetic runs on
-// the FP32 pipe (GB300: 75 TFLOP/s FP32 against 1.2 TFLOP/s FP64).
-//   op_df_kernel      AX = Op X  (the stencil of stencil.cu; differences, shifts, M0, gamma in double-float)
+// The FP64-accurate kernels of the mixed-precision solve, in double-float arithmetic (dfloat.cuh) on the FP32 pipe
+// (GB300: 75 TFLOP/s FP32 against 1.2 TFLOP/s FP64). The solver's block X is stored as double-float pairs (PC_DFS,
+// one float4 per complex element), so these kernels do no FP64 arithmetic at all; the public stencil entry point
+// takes complex128 and converts on load and store.
+//   op_df_kernel / opz_df_kernel  AX = Op X (the stencil of stencil.cu; differences, shifts, M0, gamma in
+//                     double-float), or, in the solver, the residual epilogue: R = AX - X Theta and complex64 copies
+//                     of R, X and AX, plus column norms (AX itself is not stored)
 //   update_df_kernel  X' = X C + Z  (Z: the complex64 correction [W P] coef_{W,P})
-//   gram_df_kernel    G = X^H X, H = X^H AX  (upper triangles, Hermitian mirrors)
-//   resid_df_kernel   R = AX - X Theta -> complex64 copies, plus complex64 copies of X and AX, and column norms
+//   gram_df_kernel    G = X^H X  (upper triangle, Hermitian mirror)
 #include <cmath>
+#include <type_traits>
 
 #include "dfloat.cuh"
 #include "pc_internal.cuh"
@@ -38,6 +41,10 @@ struct ResidArgs {
 };
 
 __device__ __forceinline__ float2 cdf_round(cdf a) { return make_float2(a.re.hi + a.re.lo, a.im.hi + a.im.lo); }
+__device__ __forceinline__ df ld_m0(const float2 *p) {
+  const float2 v = *p;
+  return df{v.x, v.y};
+}
 
 // writes the three components of one point; returns |r|^2 and |x|^2 contributions
 __device__ __forceinline__ void resid_point(const ResidArgs &ra, int b, int j, long n, long gi, df th, const cdf (&y)[3],
@@ -94,11 +101,18 @@ template <int TX, int TY, int TZ> constexpr size_t op_df_smem_bytes() {
 // Same tiling as op_kernel (stencil.cu): a face tile with a one-point halo, e = M0 A' v on the tile grown upward,
 // c = B v on the tile grown downward, then y = A e + gamma B' c. The grid spacing factor ih = N is a power of two,
 // so scaling by it is exact in double-float.
+// The block is complex128 (converted on load and store) for the public entry point, double-float pairs (PC_DFS) for
+// the solver's fused residual version.
+template <bool RES> using df_store_t = typename std::conditional<RES, float4, double2>::type;
+
+__device__ __forceinline__ df kp_df(float hi, float lo) { return df{hi, lo}; }
+
 template <int TX, int TY, int TZ, bool RES>
-__global__ void __launch_bounds__(256) op_df_kernel(const double2 *__restrict__ X, long sx, double2 *__restrict__ Y,
-                                                    long sy, const double *__restrict__ m0,
-                                                    const KParam *__restrict__ kp, const int *__restrict__ act,
-                                                    int logN, const ResidArgs ra) {
+__global__ void __launch_bounds__(256) op_df_kernel(const df_store_t<RES> *__restrict__ X, long sx,
+                                                    df_store_t<RES> *__restrict__ Y, long sy,
+                                                    const float2 *__restrict__ m0, const KParam *__restrict__ kp,
+                                                    const int *__restrict__ act, int logN, const ResidArgs ra) {
+  using XS = df_store_t<RES>;
   constexpr int VX = TX + 2, VY = TY + 2, VZ = TZ + 2;
   constexpr int EX = TX + 1, EY = TY + 1, EZ = TZ + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -115,11 +129,11 @@ __global__ void __launch_bounds__(256) op_df_kernel(const double2 *__restrict__ 
   t /= tilesX;
   const int y0 = (t % tilesY) * TY;
   const int z0 = (t / tilesY) * TZ;
-  const double2 *Xb = X + (long)b * sx + (long)j * 3 * n;
-  double2 *Yb = Y + (long)b * sy + (long)j * 3 * n;
+  const XS *Xb = X + (long)b * sx + (long)j * 3 * n;
+  XS *Yb = Y + (long)b * sy + (long)j * 3 * n;
   const KParam p = kp[b];
-  const df kh0 = df_from(0.5 * p.k[0]), kh1 = df_from(0.5 * p.k[1]), kh2 = df_from(0.5 * p.k[2]);
-  const df gam = df_from(p.gamma);
+  const df kh0 = kp_df(p.khf[0], p.khl[0]), kh1 = kp_df(p.khf[1], p.khl[1]), kh2 = kp_df(p.khf[2], p.khl[2]);
+  const df gam = kp_df(p.gammaf, p.gammal);
   const float ih = (float)N;
 
   for (int i = threadIdx.x; i < 3 * VZ * VY * VX; i += blockDim.x) {
@@ -128,7 +142,7 @@ __global__ void __launch_bounds__(256) op_df_kernel(const double2 *__restrict__ 
     r /= VY;
     int lz = r % VZ, comp = r / VZ;
     int gx = (x0 + lx - 1) & mask, gy = (y0 + ly - 1) & mask, gz = (z0 + lz - 1) & mask;
-    v[i] = cdf_from(Xb[comp * n + ((long)gz << (2 * logN)) + ((long)gy << logN) + gx]);
+    v[i] = ld_cdf(Xb + comp * n + ((long)gz << (2 * logN)) + ((long)gy << logN) + gx);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < EZ * EY * EX; i += blockDim.x) {
@@ -145,9 +159,9 @@ __global__ void __launch_bounds__(256) op_df_kernel(const double2 *__restrict__ 
     const int gx = (x0 + ex) & mask, gy = (y0 + ey) & mask, gz = (z0 + ez) & mask;
     const long gi = ((long)gz << (2 * logN)) + ((long)gy << logN) + gx;
     const int eo = (ez * EY + ey) * EX + ex;
-    e[eo] = cdf_scale(cdf_sub(d3v2, d2v3), df_from(m0[gi]));
-    e[EZ * EY * EX + eo] = cdf_scale(cdf_sub(d1v3, d3v1), df_from(m0[n + gi]));
-    e[2 * EZ * EY * EX + eo] = cdf_scale(cdf_sub(d2v1, d1v2), df_from(m0[2 * n + gi]));
+    e[eo] = cdf_scale(cdf_sub(d3v2, d2v3), ld_m0(m0 + gi));
+    e[EZ * EY * EX + eo] = cdf_scale(cdf_sub(d1v3, d3v1), ld_m0(m0 + n + gi));
+    e[2 * EZ * EY * EX + eo] = cdf_scale(cdf_sub(d2v1, d1v2), ld_m0(m0 + 2 * n + gi));
 #define WW(comp, dz, dy, dx) v[(((comp) * VZ + ez + (dz)) * VY + ey + (dy)) * VX + ex + (dx)]
     cdf cc = dfwd_df(WW(0, 0, 0, 0), WW(0, 0, 0, 1), ih, kh0);
     cc = cdf_add(cc, dfwd_df(WW(1, 0, 0, 0), WW(1, 0, 1, 0), ih, kh1));
@@ -178,9 +192,9 @@ __global__ void __launch_bounds__(256) op_df_kernel(const double2 *__restrict__ 
 #undef XV
       resid_point(ra, b, j, n, gi, df_from(ra.theta[(long)b * ra.m + j]), yv, xv, sr, sxx);
     } else {
-      Yb[gi] = cdf_to(y1);
-      Yb[n + gi] = cdf_to(y2);
-      Yb[2 * n + gi] = cdf_to(y3);
+      st_cdf(Yb + gi, y1);
+      st_cdf(Yb + n + gi, y2);
+      st_cdf(Yb + 2 * n + gi, y3);
     }
   }
   if constexpr (RES) resid_block_sum(ra, sr, sxx);
@@ -200,9 +214,9 @@ static int launch_op_df_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, vo
   dim3 grid((N / TX) * (N / TY) * (N / TZ), m, nb);
   *nchunk = (int)grid.x;
   if (RES && ra.part == nullptr) return PC_OK;  // sizing call
-  op_df_kernel<TX, TY, TZ, RES><<<grid, 256, smem, ctx->stream>>>(static_cast<const double2 *>(X), sx,
-                                                                   static_cast<double2 *>(Y), sy, ctx->m0d.as<double>(),
-                                                                   ctx->kparam.as<KParam>(), act, ctx->logN, ra);
+  op_df_kernel<TX, TY, TZ, RES><<<grid, 256, smem, ctx->stream>>>(
+      static_cast<const df_store_t<RES> *>(X), sx, static_cast<df_store_t<RES> *>(Y), sy, ctx->m0p.as<float2>(),
+      ctx->kparam.as<KParam>(), act, ctx->logN, ra);
   PC_CK_LAUNCH();
   return PC_OK;
 }
@@ -214,11 +228,12 @@ template <int TX, int TY> constexpr size_t opz_df_smem_bytes() {
 }
 
 template <int TX, int TY, bool RES>
-__global__ void __launch_bounds__(TX * TY) opz_df_kernel(const double2 *__restrict__ X, long sx,
-                                                         double2 *__restrict__ Y, long sy,
-                                                         const double *__restrict__ m0,
+__global__ void __launch_bounds__(TX * TY) opz_df_kernel(const df_store_t<RES> *__restrict__ X, long sx,
+                                                         df_store_t<RES> *__restrict__ Y, long sy,
+                                                         const float2 *__restrict__ m0,
                                                          const KParam *__restrict__ kp, const int *__restrict__ act,
                                                          int logN, int ZC, const ResidArgs ra) {
+  using XS = df_store_t<RES>;
   constexpr int VX = TX + 2, VY = TY + 2, VP = VX * VY;
   constexpr int EX = TX + 1, EY = TY + 1, EP = EX * EY;
   constexpr int NT = TX * TY;
@@ -236,11 +251,11 @@ __global__ void __launch_bounds__(TX * TY) opz_df_kernel(const double2 *__restri
   t /= tilesX;
   const int y0 = (t % tilesY) * TY;
   const int zb = (t / tilesY) * ZC;
-  const double2 *Xb = X + (long)b * sx + (long)j * 3 * n;
-  double2 *Yb = Y + (long)b * sy + (long)j * 3 * n;
+  const XS *Xb = X + (long)b * sx + (long)j * 3 * n;
+  XS *Yb = Y + (long)b * sy + (long)j * 3 * n;
   const KParam &p = kp[b];
-  const df kh0 = df_from(0.5 * p.k[0]), kh1 = df_from(0.5 * p.k[1]), kh2 = df_from(0.5 * p.k[2]);
-  const df gam = df_from(p.gamma);
+  const df kh0 = kp_df(p.khf[0], p.khl[0]), kh1 = kp_df(p.khf[1], p.khl[1]), kh2 = kp_df(p.khf[2], p.khl[2]);
+  const df gam = kp_df(p.gammaf, p.gammal);
   const float ih = (float)N;
   const int tid = threadIdx.x;
   auto load_v = [&](int slot, int z) {
@@ -249,7 +264,7 @@ __global__ void __launch_bounds__(TX * TY) opz_df_kernel(const double2 *__restri
     for (int i = tid; i < 3 * VP; i += NT) {
       const int comp = i / VP, r = i - comp * VP, ly = r / VX, lx = r - ly * VX;
       const int gx = (x0 + lx - 1) & mask, gy = (y0 + ly - 1) & mask;
-      vs[i] = cdf_from(Xb[comp * n + gz * plane + ((long)gy << logN) + gx]);
+      vs[i] = ld_cdf(Xb + comp * n + gz * plane + ((long)gy << logN) + gx);
     }
   };
   auto make_e = [&](int eslot, int z, int sz, int szm) {
@@ -267,9 +282,9 @@ __global__ void __launch_bounds__(TX * TY) opz_df_kernel(const double2 *__restri
       const cdf d2v1 = dbwd_df(v0[o - VX], v1, ih, kh1);
       const cdf d1v2 = dbwd_df(v0[VP + o - 1], v2, ih, kh0);
       const long gi = gz * plane + ((long)((y0 + ey) & mask) << logN) + ((x0 + ex) & mask);
-      es[i] = cdf_scale(cdf_sub(d3v2, d2v3), df_from(m0[gi]));
-      es[EP + i] = cdf_scale(cdf_sub(d1v3, d3v1), df_from(m0[n + gi]));
-      es[2 * EP + i] = cdf_scale(cdf_sub(d2v1, d1v2), df_from(m0[2 * n + gi]));
+      es[i] = cdf_scale(cdf_sub(d3v2, d2v3), ld_m0(m0 + gi));
+      es[EP + i] = cdf_scale(cdf_sub(d1v3, d3v1), ld_m0(m0 + n + gi));
+      es[2 * EP + i] = cdf_scale(cdf_sub(d2v1, d1v2), ld_m0(m0 + 2 * n + gi));
     }
   };
   auto make_c = [&](int cslot, int sz, int szp) {
@@ -320,9 +335,9 @@ __global__ void __launch_bounds__(TX * TY) opz_df_kernel(const double2 *__restri
         const cdf yv[3] = {y1, y2, y3}, xv[3] = {v0[o], v0[VP + o], v0[2 * VP + o]};
         resid_point(ra, b, j, n, gi, th, yv, xv, sr, sxx);
       } else {
-        Yb[gi] = cdf_to(y1);
-        Yb[n + gi] = cdf_to(y2);
-        Yb[2 * n + gi] = cdf_to(y3);
+        st_cdf(Yb + gi, y1);
+        st_cdf(Yb + n + gi, y2);
+        st_cdf(Yb + 2 * n + gi, y3);
       }
     }
     sv = 1 - sv;
@@ -348,9 +363,9 @@ static int launch_opz_df_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, v
   dim3 grid((N / TX) * (N / TY) * (N / ZC), m, nb);
   *nchunk = (int)grid.x;
   if (RES && ra.part == nullptr) return PC_OK;  // sizing call
-  opz_df_kernel<TX, TY, RES><<<grid, TX * TY, smem, ctx->stream>>>(static_cast<const double2 *>(X), sx,
-                                                                    static_cast<double2 *>(Y), sy, ctx->m0d.as<double>(),
-                                                                    ctx->kparam.as<KParam>(), act, ctx->logN, ZC, ra);
+  opz_df_kernel<TX, TY, RES><<<grid, TX * TY, smem, ctx->stream>>>(
+      static_cast<const df_store_t<RES> *>(X), sx, static_cast<df_store_t<RES> *>(Y), sy, ctx->m0p.as<float2>(),
+      ctx->kparam.as<KParam>(), act, ctx->logN, ZC, ra);
   PC_CK_LAUNCH();
   return PC_OK;
 }
@@ -397,9 +412,9 @@ int launch_op_df_resid(pc_ctx *ctx, int nb, int m, const void *X, long sx, const
 // ---------------------------------------------------------------- block update Y = X C + Z
 constexpr int DF_QB = 8;
 
-__global__ void __launch_bounds__(256) update_df_kernel(const double2 *__restrict__ X, long sx,
+__global__ void __launch_bounds__(256) update_df_kernel(const float4 *__restrict__ X, long sx,
                                                        const double2 *__restrict__ Cm, long sc,
-                                                       double2 *__restrict__ Y, long sy,
+                                                       float4 *__restrict__ Y, long sy,
                                                        const float2 *__restrict__ Z, long sz, long L, int p, int q,
                                                        const int *__restrict__ act) {
   __shared__ cdf Cs[64][DF_QB];
@@ -413,27 +428,27 @@ __global__ void __launch_bounds__(256) update_df_kernel(const double2 *__restric
   __syncthreads();
   const long l = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= L) return;
-  const double2 *Xb = X + (long)b * sx;
+  const float4 *Xb = X + (long)b * sx;
   cdf acc[DF_QB];
 #pragma unroll
   for (int c = 0; c < DF_QB; ++c) acc[c] = cdf{df{0.f, 0.f}, df{0.f, 0.f}};
   for (int i = 0; i < p; ++i) {
-    const cdf xv = cdf_from(Xb[(long)i * L + l]);
+    const cdf xv = ld_cdf(Xb + (long)i * L + l);
 #pragma unroll
     for (int c = 0; c < DF_QB; ++c) cdf_mac(acc[c], xv, Cs[i][c]);
   }
-  double2 *Yb = Y + (long)b * sy;
+  float4 *Yb = Y + (long)b * sy;
   const float2 *Zb = Z ? Z + (long)b * sz : nullptr;
 #pragma unroll
   for (int c = 0; c < DF_QB; ++c)
     if (j0 + c < q) {
-      double2 v = cdf_to(acc[c]);
+      cdf v = acc[c];
       if (Zb) {
         const float2 z = Zb[(long)(j0 + c) * L + l];
-        v.x += (double)z.x;
-        v.y += (double)z.y;
+        v.re = df_addf(v.re, z.x);
+        v.im = df_addf(v.im, z.y);
       }
-      Yb[(long)(j0 + c) * L + l] = v;
+      st_cdf(Yb + (long)(j0 + c) * L + l, v);
     }
 }
 
@@ -441,8 +456,8 @@ int launch_update_df(int nb, long L, int p, int q, const void *X, long sx, const
                      const void *Z, long sz, cudaStream_t st, const int *act) {
   if (nb == 0 || q == 0) return PC_OK;
   dim3 grid((unsigned)((L + 255) / 256), (q + DF_QB - 1) / DF_QB, nb);
-  update_df_kernel<<<grid, 256, 0, st>>>(static_cast<const double2 *>(X), sx, static_cast<const double2 *>(C), sc,
-                                         static_cast<double2 *>(Y), sy, static_cast<const float2 *>(Z), sz, L, p, q,
+  update_df_kernel<<<grid, 256, 0, st>>>(static_cast<const float4 *>(X), sx, static_cast<const double2 *>(C), sc,
+                                         static_cast<float4 *>(Y), sy, static_cast<const float2 *>(Z), sz, L, p, q,
                                          act);
   PC_CK_LAUNCH();
   return PC_OK;
@@ -453,14 +468,14 @@ int launch_update_df(int nb, long L, int p, int q, const void *X, long sx, const
 constexpr int DF_TL = 32;
 
 // One thread per upper-triangle entry (i <= j): p(p+1)/2 threads; grid (nchunk, 1, nb).
-__global__ void __launch_bounds__(528) gram_df_kernel(const double2 *__restrict__ X, long sx, long L, int p,
+__global__ void __launch_bounds__(528) gram_df_kernel(const float4 *__restrict__ X, long sx, long L, int p,
                                                      long chunk, double2 *__restrict__ part,
                                                      const int *__restrict__ act) {
   __shared__ cdf Xs[32][DF_TL + 1];
   __shared__ unsigned char pi[528], pj[528];
   const int bi = blockIdx.z;
   const int b = act ? act[bi] : bi;
-  const double2 *Xb = X + (long)b * sx;
+  const float4 *Xb = X + (long)b * sx;
   const int tid = threadIdx.x, nthr = blockDim.x;
   if (tid == 0) {
     int t = 0;
@@ -478,7 +493,7 @@ __global__ void __launch_bounds__(528) gram_df_kernel(const double2 *__restrict_
     for (int e = tid; e < p * DF_TL; e += nthr) {
       const int col = e / DF_TL, t = e - col * DF_TL;
       const long l = l0 + t;
-      Xs[col][t] = cdf_from(l < end ? Xb[(long)col * L + l] : make_double2(0.0, 0.0));
+      Xs[col][t] = l < end ? ld_cdf(Xb + (long)col * L + l) : cdf{df{0.f, 0.f}, df{0.f, 0.f}};
     }
     __syncthreads();
 #pragma unroll 4
@@ -531,7 +546,7 @@ int launch_gram_df(int nb, long L, int p, const void *X, long sx, void *G, void 
   long chunk = (L + nchunk - 1) / nchunk;
   chunk = (chunk + DF_TL - 1) / DF_TL * DF_TL;
   double2 *part = static_cast<double2 *>(scratch);
-  gram_df_kernel<<<dim3(nchunk, 1, nb), p * (p + 1) / 2, 0, st>>>(static_cast<const double2 *>(X), sx, L, p, chunk,
+  gram_df_kernel<<<dim3(nchunk, 1, nb), p * (p + 1) / 2, 0, st>>>(static_cast<const float4 *>(X), sx, L, p, chunk,
                                                                    part, act);
   PC_CK_LAUNCH();
   gram_df_reduce_kernel<<<nb, 256, 0, st>>>(part, nchunk, p, act, static_cast<double2 *>(G));

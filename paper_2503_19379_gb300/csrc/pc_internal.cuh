@@ -44,7 +44,13 @@ struct KParam {
   double gamma;  // penalty of eq. pnt_number
   float khf[3];  // k_i / 2 and gamma rounded to FP32, so that complex64 kernels do no FP64 arithmetic
   float gammaf;
+  float khl[3];  // remainders: (khf, khl) and (gammaf, gammal) are the double-float values of k_i / 2 and gamma
+  float gammal;
 };
+
+// internal dtype of the mixed solve's FP64-accurate block: complex double-float pairs, one float4 per element
+// (re.hi, re.lo, im.hi, im.lo); never passed through the C ABI
+constexpr int PC_DFS = 3;
 
 // ---------------------------------------------------------------- error state
 void set_error(const char *fmt, ...);
@@ -108,6 +114,7 @@ struct pc_ctx {
   pc_opts opts{};
   cudaStream_t stream = nullptr;
   pc::DevBuf m0d, m0f;      // M0 diagonal, double and float copies, [3][N^3]
+  pc::DevBuf m0p;           // M0 diagonal as double-float pairs (hi, lo) float2 [3][N^3]
   pc::DevBuf twd, twf;      // FFT twiddles exp(-2 pi i t / N), t < N/2
   pc::DevBuf kparam;        // KParam [nb]
   pc::DevBuf symd;          // per-k axis symbols d_i(m) complex128 [nb][3][N]
@@ -186,8 +193,9 @@ int launch_residual(int nb, long L, int m, const void *X, long sx, const void *A
                     void *R, long sr, double *norms, void *scratch, size_t scratch_bytes, cudaStream_t st,
                     const int *act);
 size_t residual_scratch_bytes(int nb, long L, int m);
+// X: dtype PC_C128 (complex128) or PC_DFS (double-float pairs)
 int launch_recompute(pc_ctx *ctx, int nb, int m, const void *X, long sx, double *out, const int *act, void *scratch,
-                     size_t scratch_bytes);
+                     size_t scratch_bytes, int dtype = PC_C128);
 size_t recompute_scratch_bytes(long n, int nb, int m);
 int launch_deflate(int nb, long n, int m, void *X, long sx, const int *flags, void *scratch, cudaStream_t st,
                    const int *act, int dtype = PC_C128);
@@ -199,7 +207,11 @@ int launch_rr_patch(int nb, int n, int m, void *G, void *H, const void *RS, cons
                     const int *phase, cudaStream_t st, const int *act, long sg = 0, long srs = 0);
 int launch_widen(int nb, long L, int m, const void *X, long sx, void *Y, long sy, cudaStream_t st, const int *act);
 int launch_narrow(int nb, long L, int m, const void *X, long sx, void *Y, long sy, cudaStream_t st, const int *act);
-// double-float (FP32-pair) versions of the FP64-accurate kernels of the mixed solve (mixed_df.cu)
+// Y (complex128) = X (double-float pairs, PC_DFS): m columns of length L per k-point
+int launch_pairs_to_c128(int nb, long L, int m, const void *X, long sx, void *Y, long sy, cudaStream_t st,
+                         const int *act);
+// double-float (FP32-pair) versions of the FP64-accurate kernels of the mixed solve (mixed_df.cu). launch_apply_op_df
+// takes complex128 blocks; the others take and write blocks of double-float pairs (PC_DFS).
 int launch_apply_op_df(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act);
 // the same stencil with the residual epilogue of the mixed solve's phase 2 instead of writing AX: complex64
 // r = AX - X Theta into R1 and R2, complex64 copies of X and AX, column norms (|r|, |x|) into norms [nb][m][2]
@@ -211,7 +223,7 @@ void launch_residual_reduce(int nb, int nchunk, int m, const double *part, const
                             cudaStream_t st);
 int launch_update_df(int nb, long L, int p, int q, const void *X, long sx, const void *C, long sc, void *Y, long sy,
                      const void *Z, long sz, cudaStream_t st, const int *act);
-// G = X^H X of an FP64 block (p <= 32 columns) in double-float arithmetic
+// G = X^H X of a block of double-float pairs (p <= 32 columns) in double-float arithmetic, G complex128
 int launch_gram_df(int nb, long L, int p, const void *X, long sx, void *G, void *scratch, size_t scratch_bytes,
                    cudaStream_t st, const int *act);
 size_t gram_df_scratch_bytes(int nb, long L, int p);
@@ -219,8 +231,9 @@ size_t gram_df_scratch_bytes(int nb, long L, int p);
 int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam, const std::vector<int> &zero,
                 int nbands, int m, double tol, double *evals, void *evecs, int *iters, double *resid);
 // counter-based initial columns; with mask (int [nb][m]) only the flagged columns of the act k-points are written
+// X: dtype PC_C128 or PC_DFS (the same FP64 values stored as double-float pairs)
 int launch_init_block(int nb, long L, int m, uint64_t seed, int kidx0, void *X, long sx, cudaStream_t st,
-                      const int *mask = nullptr, const int *act = nullptr);
+                      const int *mask = nullptr, const int *act = nullptr, int dtype = PC_C128);
 // Algorithm 4.1 restart: flags (host, [nb][m]) the columns of the redo k-points to replace before the re-solve
 void spurious_mask(const std::vector<int> &redo, int m, int nbands, double tol, const std::vector<double> &theta,
                    const std::vector<double> &rn, std::vector<int> &mask);

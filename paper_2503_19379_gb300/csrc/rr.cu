@@ -271,16 +271,25 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
   const int r = s_r;
   for (int i = tid; i < r; i += nt) dinv[i] = 1.0 / A[i * LD + i].x;
   __syncthreads();
+  // unit lower factor U = L diag(1/L_ii) (column i scaled by 1/L_ii) into Vh, free until step 4
+  for (int e = tid; e < r * r; e += nt) {
+    const int kk = e / r, i = e - kk * r;
+    if (i < kk) Vh[kk * LD + i] = cscale(A[kk * LD + i], dinv[i]);
+  }
+  __syncthreads();
 
-  // 3. H3 = L^{-1} H_r L^{-H}: two column-oriented forward substitutions (row i, once final, updates all rows below
-  // it; the rows are scaled by 1/L_ii at the end), with a conjugate transpose in between
+  // 3. H3 = L^{-1} H_r L^{-H}: two column-oriented forward substitutions with U (row i, once final, updates all rows
+  // below it: four FP64 FMA per entry; the rows are scaled by 1/L_ii at the end), a conjugate transpose in between
   for (int pass = 0; pass < 2; ++pass) {
     for (int i = 0; i + 1 < r; ++i) {
       const int below = r - i - 1;
       for (int e = tid; e < below * r; e += nt) {
-        const int kk = i + 1 + e / r, j = e % r;
-        const double2 c = cscale(A[kk * LD + i], dinv[i]);
-        B[kk * LD + j] = csub(B[kk * LD + j], cmul(c, B[i * LD + j]));
+        const int q = e / r, kk = i + 1 + q, j = e - q * r;
+        const double2 c = Vh[kk * LD + i], y = B[i * LD + j];
+        double2 v = B[kk * LD + j];
+        v.x = fma(-c.x, y.x, fma(c.y, y.y, v.x));
+        v.y = fma(-c.x, y.y, fma(-c.y, y.x, v.y));
+        B[kk * LD + j] = v;
       }
       __syncthreads();
     }
@@ -353,17 +362,21 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
     for (int i = 1 + tid; i < t; i += nt) vv[i] = B[(k + 1 + i) * LD + k];
     __syncthreads();
     for (int i = tid; i < t; i += nt) Vh[k * LD + i] = vv[i];
-    // p = tau B_sub v: one thread per row (two accumulators; consecutive rows hit distinct banks, LD odd)
+    // p = tau B_sub v from the lower triangle of B_sub (the only part kept up to date): one thread per row i, entry
+    // j <= i from row i, j > i as the conjugate of column i (the conjugation flips a sign bit, no FP64 work); the
+    // same trip count on every lane. Consecutive rows hit distinct banks (LD odd), column reads are contiguous.
     for (int i = tid; i < t; i += nt) {
       const double2 *row = B + (k + 1 + i) * LD + k + 1;
-      double2 s0 = cmake<double2>(0.0, 0.0), s1 = s0;
-      int j = 0;
-      for (; j + 1 < t; j += 2) {
-        s0 = cadd(s0, cmul(row[j], vv[j]));
-        s1 = cadd(s1, cmul(row[j + 1], vv[j + 1]));
+      const double2 *col = B + (k + 1) * LD + k + 1 + i;
+      double2 s = cmake<double2>(0.0, 0.0);
+      for (int j = 0; j < t; ++j) {
+        double2 a = j <= i ? row[j] : col[j * LD];
+        a.y = __longlong_as_double(__double_as_longlong(a.y) ^ ((long long)(j > i) << 63));
+        const double2 x = vv[j];
+        s.x = fma(a.x, x.x, fma(-a.y, x.y, s.x));
+        s.y = fma(a.x, x.y, fma(a.y, x.x, s.y));
       }
-      if (j < t) s0 = cadd(s0, cmul(row[j], vv[j]));
-      pv[i] = cscale(cadd(s0, s1), tk);
+      pv[i] = cscale(s, tk);
     }
     __syncthreads();
     if (warp == 0) {
@@ -376,19 +389,21 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
     const double2 K = s_K;
     for (int i = tid; i < t; i += nt) pv[i] = csub(pv[i], cmul(K, vv[i]));
     __syncthreads();
-    for (int e = tid; e < t * t; e += nt) {
-      const int i = e / t, j = e % t;
+    // B_sub -= v q^H + q v^H on the lower triangle only, entries packed row by row (e -> (i, j), j <= i) so that
+    // every warp is full: eight FP64 FMA per entry
+    for (int e = tid; e < t * (t + 1) / 2; e += nt) {
+      int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      if (i * (i + 1) / 2 > e) --i;
+      if ((i + 1) * (i + 2) / 2 <= e) ++i;
+      const int j = e - i * (i + 1) / 2;
       const double2 vi = vv[i], qi = pv[i], vj = vv[j], qj = pv[j];
-      // v_i conj(q_j) + q_i conj(v_j)
-      const double2 upd = cadd(cmake<double2>(vi.x * qj.x + vi.y * qj.y, vi.y * qj.x - vi.x * qj.y),
-                               cmake<double2>(qi.x * vj.x + qi.y * vj.y, qi.y * vj.x - qi.x * vj.y));
-      B[(k + 1 + i) * LD + k + 1 + j] = csub(B[(k + 1 + i) * LD + k + 1 + j], upd);
+      double2 *bp = B + (k + 1 + i) * LD + k + 1 + j;
+      double2 bv = *bp;
+      bv.x = fma(-vi.x, qj.x, fma(-vi.y, qj.y, fma(-qi.x, vj.x, fma(-qi.y, vj.y, bv.x))));
+      bv.y = fma(-vi.y, qj.x, fma(vi.x, qj.y, fma(-qi.y, vj.x, fma(qi.x, vj.y, bv.y))));
+      *bp = bv;
     }
-    for (int i = tid; i < t; i += nt) {
-      const double2 val = i == 0 ? s_alpha : cmake<double2>(0.0, 0.0);
-      B[(k + 1 + i) * LD + k] = val;
-      B[k * LD + k + 1 + i] = cmake<double2>(val.x, -val.y);
-    }
+    for (int i = tid; i < t; i += nt) B[(k + 1 + i) * LD + k] = i == 0 ? s_alpha : cmake<double2>(0.0, 0.0);
     __syncthreads();
   }
 

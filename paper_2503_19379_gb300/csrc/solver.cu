@@ -76,9 +76,11 @@ int upload_kpoints(pc_ctx *ctx, int nb, const double *kpts, const double *gammas
     for (int d = 0; d < 3; ++d) {
       kp[b].k[d] = kpts[3 * b + d];
       kp[b].khf[d] = (float)(0.5 * kpts[3 * b + d]);
+      kp[b].khl[d] = (float)(0.5 * kpts[3 * b + d] - (double)kp[b].khf[d]);
     }
     kp[b].gamma = gammas[b];
     kp[b].gammaf = (float)gammas[b];
+    kp[b].gammal = (float)(gammas[b] - (double)kp[b].gammaf);
     for (int d = 0; d < 3; ++d) axis_symbols(ctx->N, kpts[3 * b + d], &sym[((size_t)b * 3 + d) * ctx->N]);
   }
   PC_CK(cudaMemcpyAsync(ctx->kparam.p, kp.data(), sizeof(KParam) * nb, cudaMemcpyHostToDevice, ctx->stream));
@@ -196,9 +198,11 @@ extern "C" int pc_setup(pc_ctx **out, int N, const double *eps_edges, const doub
   ctx->stream = (cudaStream_t)stream;
   std::vector<double> m0(3 * n);
   std::vector<float> m0f(3 * n);
+  std::vector<float2> m0p(3 * n);  // double-float pairs of m0
   for (long i = 0; i < 3 * n; ++i) {
     m0[i] = 1.0 / eps_edges[i];
     m0f[i] = (float)m0[i];
+    m0p[i] = make_float2(m0f[i], (float)(m0[i] - (double)m0f[i]));
   }
   std::vector<double2> tw(N / 2);
   std::vector<float2> twf(N / 2);
@@ -217,10 +221,12 @@ extern "C" int pc_setup(pc_ctx **out, int N, const double *eps_edges, const doub
   cudaError_t e;
   if ((e = ctx->m0d.reserve(sizeof(double) * 3 * n)) != cudaSuccess) return fail(cuda_fail(e, "m0d", __FILE__, __LINE__));
   if ((e = ctx->m0f.reserve(sizeof(float) * 3 * n)) != cudaSuccess) return fail(cuda_fail(e, "m0f", __FILE__, __LINE__));
+  if ((e = ctx->m0p.reserve(sizeof(float2) * 3 * n)) != cudaSuccess) return fail(cuda_fail(e, "m0p", __FILE__, __LINE__));
   if ((e = ctx->twd.reserve(sizeof(double2) * (N / 2))) != cudaSuccess) return fail(cuda_fail(e, "tw", __FILE__, __LINE__));
   if ((e = ctx->twf.reserve(sizeof(float2) * (N / 2))) != cudaSuccess) return fail(cuda_fail(e, "twf", __FILE__, __LINE__));
   if ((e = cudaMemcpy(ctx->m0d.p, m0.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(ctx->m0f.p, m0f.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(ctx->m0p.p, m0p.data(), sizeof(float2) * 3 * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(ctx->twd.p, tw.data(), sizeof(double2) * (N / 2), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(ctx->twf.p, twf.data(), sizeof(float2) * (N / 2), cudaMemcpyHostToDevice)) != cudaSuccess)
     return fail(cuda_fail(e, "upload", __FILE__, __LINE__));

@@ -11,9 +11,9 @@
 // * The X-X block (X^H X, X^H AX) and the residual need FP64: the residual floor of a complex64 X is eps32 |Op| / lambda
 //   (about 1e-3 here), and the X-X block's rounding shifts the Ritz values by eps32 lambda.
 // Phase 1 (every k-point starts here): X and AX in complex64 as well, until the complex64 residual stops falling.
-// Phase 2: X stored in FP64; X' = X C_X + P' (complex64 correction), AX' = Op X' by the stencil fused with the
-// residual R = AX' - X' Theta (AX' itself is never stored), and the X-X Gram block X^H X, all three in double-float
-// arithmetic (mixed_df.cu) on the FP32 pipe. The X-X block of the projected operator is Theta X^H X + R^H X
+// Phase 2: X stored as double-float pairs (hi + lo FP32, ~48 bits); X' = X C_X + P' (complex64 correction),
+// AX' = Op X' by the stencil fused with the residual R = AX' - X' Theta (AX' itself is never stored), and the X-X
+// Gram block X^H X, all three in double-float arithmetic (mixed_df.cu) on the FP32 pipe. The X-X block of the projected operator is Theta X^H X + R^H X
 // (AX = X Theta + R), with R^H X from the complex64 product R^H [X | Q]: its rounding is eps32 |R| |X|, small
 // because R is.
 // Convergence and Algorithm 4.1 are decided in phase 2 only, on FP64 residuals and FP64 norms.
@@ -55,7 +55,7 @@ struct MixedShared {
   bool any_zero;
   std::vector<int> zero;  // per k-point: k reduced to 0 (the constant fields are projected out)
   float2 *F[2], *AF[2];
-  double2 *X64[2];
+  float4 *X64[2];  // phase-2 block, double-float pairs (PC_DFS); start() uses X64[0] as complex128 scratch
   float2 *R32;
   double2 *Gm, *Hm, *coef, *RQ, *GX;
   double *theta, *norms, *rn;
@@ -250,7 +250,7 @@ class MixedSolve {
       RUN(set_act(conv));
       const int nc = (int)conv.size();
       RUN(run_stage(ctx, PC_STAGE_RECOMPUTE, 2, 120.0 * S.nd * m * nc, S.Ld * 16.0 * m * nc, [&] {
-        return launch_recompute(ctx, nc, m, S.X64[cur], sX, S.rn, g.d_act, g.scratch, S.scr);
+        return launch_recompute(ctx, nc, m, S.X64[cur], sX, S.rn, g.d_act, g.scratch, S.scr, PC_DFS);
       }));
       const size_t k0 = (size_t)g.b0 * m, kn = (size_t)(g.b1 - g.b0) * m;
       PC_CK(cudaMemcpyAsync(S.h_rn + 3 * k0, S.rn + 3 * k0, sizeof(double) * 3 * kn, cudaMemcpyDeviceToHost, g.st));
@@ -279,9 +279,14 @@ class MixedSolve {
         S.evals[(size_t)b * nbands + j] = S.h_theta[(size_t)b * m + j];
         if (S.resid) S.resid[(size_t)b * nbands + j] = relres(b, j);
       }
-      if (S.evecs)
-        PC_CK(cudaMemcpyAsync(static_cast<double2 *>(S.evecs) + (size_t)b * nbands * L, S.X64[cur] + (size_t)b * sX,
-                              sizeof(double2) * (size_t)nbands * L, cudaMemcpyDeviceToDevice, g.st));
+    }
+    if (S.evecs && !fin.empty()) {
+      // the first nbands columns, converted to complex128, into the caller's [nb][nbands][L] block
+      RUN(set_act(fin));
+      RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, S.Ld * 32.0 * nbands * fin.size(), [&] {
+        return launch_pairs_to_c128((int)fin.size(), L, nbands, S.X64[cur], sX, S.evecs, (long)nbands * L, g.st,
+                                    g.d_act);
+      }));
     }
     {
       std::vector<int> keep;
@@ -327,9 +332,9 @@ class MixedSolve {
         // streams of fresh columns: distinct per group and restart
         const uint64_t seed = ctx->opts.seed + 7919ULL * (g.restarts + 1000ULL * (uint64_t)g.b0);
         RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, 0.0, [&] {
-          return launch_init_block(nr, L, m, seed, 0, S.X64[cur], sX, g.st, S.d_mask, g.d_act);
+          return launch_init_block(nr, L, m, seed, 0, S.X64[cur], sX, g.st, S.d_mask, g.d_act, PC_DFS);
         }));
-        RUN(DEFL(redo, S.X64[cur], sX, PC_C128));
+        RUN(DEFL(redo, S.X64[cur], sX, PC_DFS));
         RUN(OP64R(nr, S.X64[cur], cur));
         if (g.haveP) RUN(OP32(nr, m, S.F[cur] + 2L * m * L, sF, S.AF[cur] + 2L * m * L, sF));
       }
@@ -394,7 +399,7 @@ class MixedSolve {
         return launch_update_df(n2, L, m, m, S.X64[cur], sX, S.coef, S.sC, S.X64[nxt], sX,
                                 S.F[nxt] + 2L * m * L, sF, g.st, g.d_act);
       }));
-      RUN(DEFL(act2, S.X64[nxt], sX, PC_C128));
+      RUN(DEFL(act2, S.X64[nxt], sX, PC_DFS));
       RUN(OP64R(n2, S.X64[nxt], nxt));
     }
     RUN(set_act(g.act));
@@ -425,8 +430,8 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
   PC_CK(ctx->S[1].reserve(sizeof(float2) * (size_t)sF * nb));
   PC_CK(ctx->AS[0].reserve(sizeof(float2) * (size_t)sF * nb));
   PC_CK(ctx->AS[1].reserve(sizeof(float2) * (size_t)sF * nb));
-  PC_CK(ctx->X64[0].reserve(sizeof(double2) * (size_t)sX * nb));
-  PC_CK(ctx->X64[1].reserve(sizeof(double2) * (size_t)sX * nb));
+  PC_CK(ctx->X64[0].reserve(sizeof(float4) * (size_t)sX * nb));
+  PC_CK(ctx->X64[1].reserve(sizeof(float4) * (size_t)sX * nb));
   PC_CK(ctx->R32.reserve(sizeof(float2) * (size_t)sX * nb));
   PC_CK(ctx->Gm.reserve(sizeof(double2) * (size_t)nb * nmax * nmax));
   PC_CK(ctx->Hm.reserve(sizeof(double2) * (size_t)nb * nmax * nmax));
@@ -483,7 +488,7 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
   for (int i = 0; i < 2; ++i) {
     S.F[i] = ctx->S[i].as<float2>();
     S.AF[i] = ctx->AS[i].as<float2>();
-    S.X64[i] = ctx->X64[i].as<double2>();
+    S.X64[i] = ctx->X64[i].as<float4>();
   }
   S.R32 = ctx->R32.as<float2>();
   S.Gm = ctx->Gm.as<double2>();

@@ -13,6 +13,7 @@
 // input face value is read from global memory once per tile (plus halo).
 #include <cstdio>
 
+#include "dfloat.cuh"
 #include "pc_internal.cuh"
 
 namespace pc {
@@ -268,11 +269,13 @@ struct HalfOut {
   double2 e[3];
   double2 c;
 };
-__device__ __forceinline__ HalfOut half_at(const double2 *__restrict__ x, long n, int logN, int gx, int gy, int gz,
+// S: complex128 (double2) or double-float pairs (float4), read as FP64 values
+template <typename S>
+__device__ __forceinline__ HalfOut half_at(const S *__restrict__ x, long n, int logN, int gx, int gy, int gz,
                                            double ih, double kh0, double kh1, double kh2) {
   const int mask = (1 << logN) - 1;
   auto at = [&](int comp, int z, int y, int xx) {
-    return x[comp * n + ((long)(z & mask) << (2 * logN)) + ((long)(y & mask) << logN) + (xx & mask)];
+    return ld_c128(x + comp * n + ((long)(z & mask) << (2 * logN)) + ((long)(y & mask) << logN) + (xx & mask));
   };
   const double2 v1 = at(0, gz, gy, gx), v2 = at(1, gz, gy, gx), v3 = at(2, gz, gy, gx);
   HalfOut o;
@@ -305,7 +308,8 @@ __global__ void half_kernel(const double2 *__restrict__ X, double2 *__restrict__
 }
 
 // per-block partial sums of (sum M0 |A'x|^2, sum |Bx|^2, sum |x|^2); grid (nchunk, m, nb)
-__global__ void recompute_partial_kernel(const double2 *__restrict__ X, long sx, const double *__restrict__ m0,
+template <typename S>
+__global__ void recompute_partial_kernel(const S *__restrict__ X, long sx, const double *__restrict__ m0,
                                          const KParam *__restrict__ kp, const int *__restrict__ act, int logN,
                                          double ih, long chunk, double *__restrict__ part) {
   const long n = 1L << (3 * logN);
@@ -314,7 +318,7 @@ __global__ void recompute_partial_kernel(const double2 *__restrict__ X, long sx,
   const int b = act ? act[bi] : bi;
   const int j = blockIdx.y;
   const KParam p = kp[b];
-  const double2 *x = X + (long)b * sx + (long)j * 3 * n;
+  const S *x = X + (long)b * sx + (long)j * 3 * n;
   double s0 = 0, s1 = 0, s2 = 0;
   const long beg = blockIdx.x * chunk, end = min(n, beg + chunk);
   for (long i = beg + threadIdx.x; i < end; i += blockDim.x) {
@@ -322,7 +326,7 @@ __global__ void recompute_partial_kernel(const double2 *__restrict__ X, long sx,
     HalfOut o = half_at(x, n, logN, gx, gy, gz, ih, 0.5 * p.k[0], 0.5 * p.k[1], 0.5 * p.k[2]);
     for (int c = 0; c < 3; ++c) {
       s0 += m0[c * n + i] * (o.e[c].x * o.e[c].x + o.e[c].y * o.e[c].y);
-      const double2 xv = x[c * n + i];
+      const double2 xv = ld_c128(x + c * n + i);
       s2 += xv.x * xv.x + xv.y * xv.y;
     }
     s1 += o.c.x * o.c.x + o.c.y * o.c.y;
@@ -418,7 +422,7 @@ size_t recompute_scratch_bytes(long n, int nb, int m) {
 }
 
 int launch_recompute(pc_ctx *ctx, int nb, int m, const void *X, long sx, double *out, const int *act, void *scratch,
-                     size_t scratch_bytes) {
+                     size_t scratch_bytes, int dtype) {
   if (nb == 0 || m == 0) return PC_OK;
   const long n = ctx->n;
   const int nchunk = (int)std::min<long>(64, (n + 4095) / 4096);
@@ -428,9 +432,14 @@ int launch_recompute(pc_ctx *ctx, int nb, int m, const void *X, long sx, double 
     return PC_EINVAL;
   }
   double *part = static_cast<double *>(scratch);
-  recompute_partial_kernel<<<dim3(nchunk, m, nb), 256, 0, ctx->stream>>>(
-      static_cast<const double2 *>(X), sx, ctx->m0d.as<double>(), ctx->kparam.as<KParam>(), act, ctx->logN,
-      (double)ctx->N, chunk, part);
+  if (dtype == PC_DFS)
+    recompute_partial_kernel<float4><<<dim3(nchunk, m, nb), 256, 0, ctx->stream>>>(
+        static_cast<const float4 *>(X), sx, ctx->m0d.as<double>(), ctx->kparam.as<KParam>(), act, ctx->logN,
+        (double)ctx->N, chunk, part);
+  else
+    recompute_partial_kernel<double2><<<dim3(nchunk, m, nb), 256, 0, ctx->stream>>>(
+        static_cast<const double2 *>(X), sx, ctx->m0d.as<double>(), ctx->kparam.as<KParam>(), act, ctx->logN,
+        (double)ctx->N, chunk, part);
   PC_CK_LAUNCH();
   recompute_reduce_kernel<<<nb, 64, 0, ctx->stream>>>(part, nchunk, m, act, out);
   PC_CK_LAUNCH();
