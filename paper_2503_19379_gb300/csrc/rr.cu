@@ -28,6 +28,7 @@
 // to the absolute width eps64 |T| (LAPACK's default for bisection, below which the FP64 Sturm count itself is not
 // accurate).
 #include <cfloat>
+#include <climits>
 #include <cmath>
 
 #include "pc_internal.cuh"
@@ -38,7 +39,7 @@ namespace {
 
 constexpr double RR_CLUSTER_REL = 1e-7;
 constexpr int RR_MAXN = 64;
-constexpr int RR_THREADS = 256;
+constexpr int RR_THREADS = 256;  // 8 warps: the Householder step splits its products over warp % 4 and warp / 4
 constexpr double RR_EPS = 2.220446049250313e-16;
 
 __device__ __forceinline__ double2 shfl_xor_d2(double2 v, int mask) {
@@ -120,6 +121,25 @@ __device__ __forceinline__ int sturm_count(const R *d, const R *e2, int r, R x, 
   return c;
 }
 
+// FP64 version: the division by q is a multiplication by its correctly rounded reciprocal folded into one FMA, and
+// the tests on q (sign, |q| < pivmin) read its bit pattern with integer instructions: 7 FP64 instructions a step
+// instead of about 11. Each step still rounds with a relative error of a few ulp, which keeps the count backward
+// stable (it is the exact count of a matrix whose d and e^2 differ from T's by a few ulp).
+template <>
+__device__ __forceinline__ int sturm_count<double>(const double *d, const double *e2, int r, double x, double pivmin) {
+  const long long pm = __double_as_longlong(pivmin);
+  double q = d[0] - x;
+  long long qb = __double_as_longlong(q);
+  int c = (qb < 0) & ((qb & LLONG_MAX) != 0);  // q < 0, -0.0 excluded
+  for (int i = 1; i < r; ++i) {
+    if ((qb & LLONG_MAX) < pm) q = -pivmin;
+    q = fma(-e2[i - 1], __drcp_rn(q), d[i] - x);
+    qb = __double_as_longlong(q);
+    c += (qb < 0) & ((qb & LLONG_MAX) != 0);
+  }
+  return c;
+}
+
 // Multisection on a group of G lanes (G a power of two <= 32) per eigenvalue j: lane s of the group counts at the
 // interior point lo + (s + 1) (hi - lo) / (G + 1); the leading run of lanes whose count is <= j gives the new bracket
 // (the invariant count(lo) <= j < count(hi) holds whether or not the computed counts are monotone). All lanes of a
@@ -150,7 +170,8 @@ __host__ __device__ inline int rr_ld(int n) { return (n & 1) ? n : n + 1; }
 
 size_t rr_smem(int n, int m) {
   const int ld = rr_ld(n);
-  return sizeof(double2) * (3 * (size_t)n * ld + 3 * (size_t)n) + sizeof(double) * (8 * (size_t)n + m) +
+  return sizeof(double2) * (3 * (size_t)n * ld + 3 * (size_t)n + 4 * RR_MAXN) +
+         sizeof(double) * (8 * (size_t)n + m) +
          sizeof(float) * 2 * (size_t)n + sizeof(int) * (2 * (size_t)n + m) + 64;
 }
 
@@ -166,7 +187,8 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
   double2 *phi = Vh + n * LD;                           // phases of the tridiagonal scaling
   double2 *pv = phi + n;                                // p / q vectors of the Householder step
   double2 *vv = pv + n;                                 // current Householder vector
-  double *dsc = reinterpret_cast<double *>(vv + n);
+  double2 *hpart = vv + n;                              // partial products of a Householder step [4][RR_MAXN]
+  double *dsc = reinterpret_cast<double *>(hpart + 4 * RR_MAXN);
   double *dd = dsc + n, *ee = dd + n, *e2 = ee + n, *tau = e2 + n, *dinv = tau + n, *w = dinv + n;  // w: m
   double *spare = w + m;                                                                              // 2n
   float *d32 = reinterpret_cast<float *>(spare + 2 * n);
@@ -174,8 +196,8 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
   int *perm = reinterpret_cast<int *>(e232 + n);
   int *pos = perm + n;  // m
   __shared__ int s_p, s_r, s_stop, s_maxpos;
-  __shared__ double s_piv, s_tau, s_gl, s_gu, s_tn, s_pivmin;
-  __shared__ double2 s_alpha, s_K;
+  __shared__ double s_il, s_lkk, s_tau, s_gl, s_gu, s_tn, s_pivmin;
+  __shared__ double2 s_alpha, s_Kp[2];
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
   const int b = act ? act[blockIdx.x] : (int)blockIdx.x;
   const double2 *G = Gg + (long)b * sg;
@@ -203,10 +225,13 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
   // 2. pivoted Cholesky
   for (int k = 0; k < n; ++k) {
     if (warp == 0) {
-      double best = -HUGE_VAL;
+      // pivot: the largest remaining diagonal entry. Non-negative doubles order like their bit patterns read as
+      // signed 64-bit integers (negative ones fall below all of them), so the search costs no FP64 instructions;
+      // the pivot's square root and its reciprocal are formed once, by lane 0
+      long long best = LLONG_MIN;
       int bi = n;
       for (int i = k + lane; i < n; i += 32) {
-        const double v = A[i * LD + i].x;
+        const long long v = __double_as_longlong(A[i * LD + i].x);
         if (v > best) {
           best = v;
           bi = i;
@@ -214,7 +239,7 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
       }
 #pragma unroll
       for (int o = 16; o; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) {
           best = ob;
@@ -222,10 +247,16 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
         }
       }
       if (lane == 0) {
+        const double piv = bi < n ? __longlong_as_double(best) : -1.0;
         s_p = bi < n ? bi : k;
-        s_piv = best;
-        s_stop = !(best > drop);
-        if (s_stop) s_r = k;
+        s_stop = !(piv > drop);
+        if (s_stop) {
+          s_r = k;
+        } else {
+          const double il = rsqrt(piv);
+          s_il = il;
+          s_lkk = piv * il;
+        }
       }
     }
     __syncthreads();
@@ -256,15 +287,18 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
       }
       __syncthreads();
     }
-    const double lkk = sqrt(s_piv), il = 1.0 / lkk;
+    const double il = s_il;
     for (int i = k + 1 + tid; i < n; i += nt) A[i * LD + k] = cscale(A[i * LD + k], il);
     __syncthreads();
-    if (tid == 0) A[k * LD + k] = cmake<double2>(lkk, 0.0);
+    if (tid == 0) A[k * LD + k] = cmake<double2>(s_lkk, 0.0);
     const int t = n - k - 1;
     for (int e = tid; e < t * t; e += nt) {
-      const int i = k + 1 + e / t, j = k + 1 + e % t;
+      const int q = e / t, i = k + 1 + q, j = k + 1 + e - q * t;
       const double2 a = A[i * LD + k], c = A[j * LD + k];
-      A[i * LD + j] = csub(A[i * LD + j], cmake<double2>(a.x * c.x + a.y * c.y, a.y * c.x - a.x * c.y));
+      double2 v = A[i * LD + j];  // v -= a conj(c): four FP64 FMA
+      v.x = fma(-a.x, c.x, fma(-a.y, c.y, v.x));
+      v.y = fma(-a.y, c.x, fma(a.x, c.y, v.y));
+      A[i * LD + j] = v;
     }
     __syncthreads();
   }
@@ -325,29 +359,38 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
   }
   __syncthreads();
 
-  // 4. Householder tridiagonalisation of H3 (r x r)
+  // 4. Householder tridiagonalisation of H3 (r x r), on its lower triangle. A GB300 SM retires about 2 FP64 FMA
+  // per clock, so one warp-wide FP64 instruction holds an SM sub-partition's FP64 unit for tens of cycles: every
+  // step below keeps its chains of FP64 instructions short and spreads its products over all four sub-partitions.
   for (int k = 0; k + 2 < r; ++k) {
     const int t = r - k - 1;
     if (warp == 0) {
+      // x = B[k+1:, k], sigma = |x|^2; reflector v = x - alpha e1, alpha = -phase(x0) |x|, tau = 2 / |v|^2 with
+      // |v|^2 = 2 (sigma + |x0| |x|) (no cancellation)
       double sig = 0.0;
       for (int i = lane; i < t; i += 32) {
         const double2 x = B[(k + 1 + i) * LD + k];
-        sig += x.x * x.x + x.y * x.y;
+        vv[i] = x;
+        sig = fma(x.x, x.x, fma(x.y, x.y, sig));
       }
       sig = warp_sum_d(sig);
       if (lane == 0) {
-        const double2 x0 = B[(k + 1) * LD + k];
-        const double ax0 = hypot(x0.x, x0.y);
+        const double2 x0 = vv[0];
         if (sig == 0.0) {
           s_tau = 0.0;
         } else {
-          const double2 ph = ax0 > 0.0 ? cmake<double2>(x0.x / ax0, x0.y / ax0) : cmake<double2>(1.0, 0.0);
-          const double nrm = sqrt(sig);
+          const double a0 = fma(x0.x, x0.x, x0.y * x0.y);
+          const double nrm = sig * rsqrt(sig);
+          double2 ph = cmake<double2>(1.0, 0.0);
+          double ax0 = 0.0;
+          if (a0 > 0.0) {
+            const double ra = rsqrt(a0);
+            ax0 = a0 * ra;
+            ph = cmake<double2>(x0.x * ra, x0.y * ra);
+          }
           s_alpha = cmake<double2>(-ph.x * nrm, -ph.y * nrm);
-          const double2 v0 = csub(x0, s_alpha);
-          const double vn2 = sig - ax0 * ax0 + v0.x * v0.x + v0.y * v0.y;
-          s_tau = 2.0 / vn2;
-          vv[0] = v0;
+          vv[0] = cmake<double2>(fma(ph.x, nrm, x0.x), fma(ph.y, nrm, x0.y));
+          s_tau = 1.0 / fma(nrm, ax0, sig);
         }
       }
     }
@@ -359,35 +402,49 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
       __syncthreads();
       continue;
     }
-    for (int i = 1 + tid; i < t; i += nt) vv[i] = B[(k + 1 + i) * LD + k];
-    __syncthreads();
-    for (int i = tid; i < t; i += nt) Vh[k * LD + i] = vv[i];
-    // p = tau B_sub v from the lower triangle of B_sub (the only part kept up to date): one thread per row i, entry
-    // j <= i from row i, j > i as the conjugate of column i (the conjugation flips a sign bit, no FP64 work); the
-    // same trip count on every lane. Consecutive rows hit distinct banks (LD odd), column reads are contiguous.
-    for (int i = tid; i < t; i += nt) {
-      const double2 *row = B + (k + 1 + i) * LD + k + 1;
-      const double2 *col = B + (k + 1) * LD + k + 1 + i;
-      double2 s = cmake<double2>(0.0, 0.0);
-      for (int j = 0; j < t; ++j) {
-        double2 a = j <= i ? row[j] : col[j * LD];
-        a.y = __longlong_as_double(__double_as_longlong(a.y) ^ ((long long)(j > i) << 63));
-        const double2 x = vv[j];
-        s.x = fma(a.x, x.x, fma(-a.y, x.y, s.x));
-        s.y = fma(a.x, x.y, fma(a.y, x.x, s.y));
+    // partial products of B_sub v from the lower triangle of B_sub (the only part kept up to date): warp w takes
+    // rows 32 (w / 4) + lane and the quarter w % 4 of the columns; entry j <= i from row i, j > i as the conjugate of
+    // column i (the conjugation flips a sign bit, no FP64 work). Consecutive rows hit distinct banks (LD odd),
+    // column reads are contiguous.
+    {
+      const int c = warp & 3, i = (warp >> 2) * 32 + lane;
+      const int cl = (t + 3) >> 2, j0 = c * cl, j1 = min(t, j0 + cl);
+      if (i < t) {
+        const double2 *row = B + (k + 1 + i) * LD + k + 1;
+        const double2 *col = B + (k + 1) * LD + k + 1 + i;
+        double2 s = cmake<double2>(0.0, 0.0);
+        for (int j = j0; j < j1; ++j) {
+          double2 a = j <= i ? row[j] : col[j * LD];
+          a.y = __longlong_as_double(__double_as_longlong(a.y) ^ ((long long)(j > i) << 63));
+          const double2 x = vv[j];
+          s.x = fma(a.x, x.x, fma(-a.y, x.y, s.x));
+          s.y = fma(a.x, x.y, fma(a.y, x.x, s.y));
+        }
+        hpart[c * RR_MAXN + i] = s;
       }
-      pv[i] = cscale(s, tk);
     }
     __syncthreads();
-    if (warp == 0) {
-      double2 s = cmake<double2>(0.0, 0.0);
-      for (int i = lane; i < t; i += 32) s = cadd(s, cmulc(vv[i], pv[i]));
-      s = warp_sum_d2(s);
-      if (lane == 0) s_K = cscale(s, 0.5 * tk);
+    // p = tau B_sub v, K = tau/2 v^H p, q = p - K v on the row warps (two when t > 32, joined by a named barrier)
+    if (warp == 0 || (warp == 1 && t > 32)) {
+      const int i = tid;
+      double2 p = cmake<double2>(0.0, 0.0), w = p;
+      if (i < t) {
+        p = cscale(cadd(cadd(hpart[i], hpart[RR_MAXN + i]), cadd(hpart[2 * RR_MAXN + i], hpart[3 * RR_MAXN + i])),
+                   tk);
+        Vh[k * LD + i] = vv[i];
+        w = cmulc(vv[i], p);
+      }
+      w = warp_sum_d2(w);
+      if (lane == 0) s_Kp[warp] = w;
+      if (t > 32)
+        asm volatile("bar.sync 1, 64;" ::: "memory");
+      else
+        __syncwarp();
+      double2 K = s_Kp[0];
+      if (t > 32) K = cadd(K, s_Kp[1]);
+      K = cscale(K, 0.5 * tk);
+      if (i < t) pv[i] = csub(p, cmul(K, vv[i]));
     }
-    __syncthreads();
-    const double2 K = s_K;
-    for (int i = tid; i < t; i += nt) pv[i] = csub(pv[i], cmul(K, vv[i]));
     __syncthreads();
     // B_sub -= v q^H + q v^H on the lower triangle only, entries packed row by row (e -> (i, j), j <= i) so that
     // every warp is full: eight FP64 FMA per entry
@@ -493,8 +550,9 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
 
   // 6. inverse iteration, cluster position by cluster position; Z (r x mm, column-major by j) lives in B
   const int maxpos = s_maxpos;
+  // eigenvector j on warp j % 4, lane j / 4: the sequential solves run on all four SM sub-partitions
   for (int round = 0; round <= maxpos; ++round) {
-    for (int j = tid; j < mm; j += nt) {
+    for (int j = warp + 4 * lane; warp < 4 && j < mm; j += 128) {
       if (pos[j] != round) continue;
       double work[5 * RR_MAXN];
       double *z = Z + (long)j * r;
@@ -522,48 +580,65 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
 
   // 7. back-transformation y = Q Phi z (reflectors applied last to first), then L^H x = y, coef = D P x.
   double2 *out = coefg + (long)b * sc;
-  // Block-parallel form for all wanted vectors at once when the work space fits behind Z in B: Y (r x mm,
-  // row-major), per-step partial dot products (C chunks of rows x mm) and the reflector coefficients s (mm).
+  // Block-parallel form for all wanted vectors at once when the work space fits behind Z in B: Y (r x mm, row
+  // stride YLD odd, so that a column read by consecutive rows hits distinct banks) and the reflector coefficients s
+  // (mm). The coefficient s_j of a reflector is summed by a group of C consecutive lanes (rows c, c + C, ...) and a
+  // shuffle tree: one barrier per reflector step instead of two, a reduction depth of log2 C instead of C.
   const long zsz = ((long)r * mm + 1) / 2;
-  const int C = mm > 0 ? nt / mm : 0;
-  if (mm > 0 && zsz + (long)r * mm + (long)C * mm + mm <= (long)n * LD) {
-    double2 *Y = B + zsz, *part = Y + (long)r * mm, *sj = part + (long)C * mm;
+  const int YLD = mm | 1;
+  int C = 1;
+  while (2 * C <= 32 && 2 * C * mm <= nt) C *= 2;
+  if (mm > 0 && zsz + (long)r * YLD + mm <= (long)n * LD) {
+    double2 *Y = B + zsz, *sj = Y + (long)r * YLD;
     for (int e = tid; e < r * mm; e += nt) {
       const int i = e / mm, j = e - i * mm;
-      Y[e] = cscale(phi[i], Z[(long)j * r + i]);
+      Y[(long)i * YLD + j] = cscale(phi[i], Z[(long)j * r + i]);
     }
     __syncthreads();
     for (int k = r - 3; k >= 0; --k) {
       const double tk = tau[k];
       if (tk == 0.0) continue;  // uniform over the block
       const int t = r - k - 1;
-      // s_j = tau v_k^H Y[k+1:, j]: thread (c, j) sums rows k+1+c, k+1+c+C, ...
-      if (tid < C * mm) {
-        const int c = tid / mm, j = tid - c * mm;
+      // s_j = tau v_k^H Y[k+1:, j]
+      if (tid < ((C * mm + 31) & ~31)) {  // whole warps (the shuffles)
+        const int j = tid / C, c = tid - j * C;
         double2 acc = cmake<double2>(0.0, 0.0);
-        for (int i = c; i < t; i += C) acc = cadd(acc, cmulc(Vh[k * LD + i], Y[(long)(k + 1 + i) * mm + j]));
-        part[tid] = acc;
-      }
-      __syncthreads();
-      if (tid < mm) {
-        double2 acc = cmake<double2>(0.0, 0.0);
-        for (int c = 0; c < C; ++c) acc = cadd(acc, part[c * mm + tid]);
-        sj[tid] = cscale(acc, tk);
+        if (j < mm)
+          for (int i = c; i < t; i += C) {
+            const double2 v = Vh[k * LD + i], y = Y[(long)(k + 1 + i) * YLD + j];  // acc += conj(v) y
+            acc.x = fma(v.x, y.x, fma(v.y, y.y, acc.x));
+            acc.y = fma(v.x, y.y, fma(-v.y, y.x, acc.y));
+          }
+        for (int o = C >> 1; o; o >>= 1) acc = cadd(acc, shfl_xor_d2(acc, o));
+        if (j < mm && c == 0) sj[j] = cscale(acc, tk);
       }
       __syncthreads();
       for (int e = tid; e < t * mm; e += nt) {
         const int i = e / mm, j = e - i * mm;
-        Y[(long)(k + 1 + i) * mm + j] = csub(Y[(long)(k + 1 + i) * mm + j], cmul(Vh[k * LD + i], sj[j]));
+        const double2 v = Vh[k * LD + i], sv = sj[j];  // Y -= v s
+        double2 y = Y[(long)(k + 1 + i) * YLD + j];
+        y.x = fma(-v.x, sv.x, fma(v.y, sv.y, y.x));
+        y.y = fma(-v.x, sv.y, fma(-v.y, sv.x, y.y));
+        Y[(long)(k + 1 + i) * YLD + j] = y;
       }
       __syncthreads();
     }
     // L^H x = y, column-oriented from the last row: row i, final once all rows below have been applied, updates the
-    // rows above it (the scaling by 1/L_ii is folded into the coefficient and applied to row i at the end)
+    // rows above it (the scaling by 1/L_ii is applied to row i at the end). The coefficients L_il / L_ii go to Vh
+    // (free now) first, so that the update is four FP64 FMA per entry.
+    for (int e = tid; e < r * r; e += nt) {
+      const int i = e / r, l = e - i * r;
+      if (l < i) Vh[i * LD + l] = cscale(A[i * LD + l], dinv[i]);
+    }
+    __syncthreads();
     for (int i = r - 1; i > 0; --i) {
       for (int e = tid; e < i * mm; e += nt) {
         const int l = e / mm, j = e - l * mm;
-        const double2 c = cscale(A[i * LD + l], dinv[i]);  // L_il / L_ii, used conjugated
-        Y[(long)l * mm + j] = csub(Y[(long)l * mm + j], cmulc(c, Y[(long)i * mm + j]));
+        const double2 c = Vh[i * LD + l], y = Y[(long)i * YLD + j];  // Y[l] -= conj(c) Y[i]
+        double2 v = Y[(long)l * YLD + j];
+        v.x = fma(-c.x, y.x, fma(-c.y, y.y, v.x));
+        v.y = fma(-c.x, y.y, fma(c.y, y.x, v.y));
+        Y[(long)l * YLD + j] = v;
       }
       __syncthreads();
     }
@@ -571,7 +646,7 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
     __syncthreads();
     for (int e = tid; e < r * mm; e += nt) {
       const int i = e / mm, j = e - i * mm;
-      out[perm[i] * m + j] = cscale(Y[e], dinv[i] * dsc[perm[i]]);
+      out[perm[i] * m + j] = cscale(Y[(long)i * YLD + j], dinv[i] * dsc[perm[i]]);
     }
     for (int j = tid; j < m; j += nt) thetag[(long)b * m + j] = j < mm ? w[j] : 0.0;
     if (rankg && tid == 0) rankg[b] = r;

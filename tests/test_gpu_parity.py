@@ -223,10 +223,12 @@ def test_eigh_batched(pcmod, n):
         assert np.max(np.abs(V[b].conj().T @ V[b] - np.eye(n))) <= 1e-12
 
 
-def test_rayleigh_ritz(pcmod):
+@pytest.mark.parametrize("L,n,m", [(300, 30, 8), (400, 48, 16), (400, 64, 40), (400, 64, 64), (300, 40, 33)])
+def test_rayleigh_ritz(pcmod, L, n, m):
+    """Pencils up to the 64-column maximum: Householder steps with more than 32 trailing rows (two row warps), more
+    than 32 wanted pairs, and both back-transformation forms (block-parallel when its work space fits)."""
     import scipy.linalg as sla
     g = np.random.default_rng(4)
-    L, n, m = 300, 30, 8
     Q, _ = np.linalg.qr(rand_block(5, (L, L)))
     lam = np.sort(g.uniform(0.5, 1e4, L))
     A = (Q * lam) @ Q.conj().T
@@ -242,6 +244,33 @@ def test_rayleigh_ritz(pcmod):
     Xr = Sb @ coef
     assert np.max(np.abs(Xr.conj().T @ Xr - np.eye(m))) <= 1e-8
     assert np.max(np.abs(Xr.conj().T @ A @ Xr - np.diag(theta))) <= 1e-8 * lam.max()
+
+
+def test_rayleigh_ritz_degenerate_clusters(pcmod):
+    """A search space that contains a 3-fold and a 2-fold eigenspace of the operator: the pencil has exactly repeated
+    eigenvalues, whose Ritz vectors come out of inverse iteration with Gram-Schmidt inside each cluster."""
+    g = np.random.default_rng(11)
+    L, n, m = 300, 48, 16
+    Q, _ = np.linalg.qr(rand_block(12, (L, L)))
+    lam = np.sort(g.uniform(3.0, 50.0, L))
+    lam[:3] = 1.0
+    lam[3:5] = 2.0
+    A = (Q * lam) @ Q.conj().T
+    Sb = np.concatenate([Q[:, :5] @ rand_block(13, (5, 5)), rand_block(14, (L, n - 5))], axis=1)
+    G = Sb.conj().T @ Sb
+    H = Sb.conj().T @ A @ Sb
+    theta, coef, rank = pcmod.rayleigh_ritz(to_dev(G[None]), to_dev(H[None]), m)
+    theta = theta.cpu().numpy()[0]
+    coef = coef.cpu().numpy()[0]
+    assert int(rank.cpu()[0]) == n
+    assert np.allclose(theta[:5], [1, 1, 1, 2, 2], rtol=0, atol=1e-11)
+    ref = np.linalg.eigvalsh(np.linalg.solve(np.linalg.cholesky(G), np.linalg.solve(np.linalg.cholesky(G), H).conj().T))
+    assert np.max(np.abs(theta - np.sort(ref)[:m]) / np.sort(ref)[:m]) <= 1e-10
+    Xr = Sb @ coef
+    assert np.max(np.abs(Xr.conj().T @ Xr - np.eye(m))) <= 1e-9
+    assert np.max(np.abs(Xr.conj().T @ A @ Xr - np.diag(theta))) <= 1e-9 * lam.max()
+    # the first five are exact eigenvectors of the operator
+    assert np.max(np.abs(A @ Xr[:, :5] - Xr[:, :5] * theta[None, :5])) <= 1e-9 * lam.max()
 
 
 def test_rayleigh_ritz_drops_dependent_directions(pcmod):
