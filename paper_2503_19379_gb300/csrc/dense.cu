@@ -826,6 +826,16 @@ __global__ void init_block_kernel(S *__restrict__ X, long sx, long L, uint64_t s
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += (long)gridDim.x * blockDim.x) {
     const uint64_t d1 = mix64(key + G * (2ULL * (uint64_t)e + 1ULL));
     const uint64_t d2 = mix64(key + G * (2ULL * (uint64_t)e + 2ULL));
+    if constexpr (std::is_same<S, float2>::value) {
+      // complex64 start block: the same counter-based uniforms (their top 24 bits) and Box-Muller in FP32
+      const float u1 = ((float)(d1 >> 40) + 0.5f) * 0x1.0p-24f;
+      const float u2 = ((float)(d2 >> 40) + 0.5f) * 0x1.0p-24f;
+      const float rad = sqrtf(-2.0f * logf(u1));
+      float s, c;
+      sincospif(2.0f * u2, &s, &c);
+      x[e] = make_float2(rad * c, rad * s);
+      continue;
+    }
     const double u1 = ((double)(d1 >> 11) + 0.5) * 0x1.0p-53;
     const double u2 = ((double)(d2 >> 11) + 0.5) * 0x1.0p-53;
     const double rad = sqrt(-2.0 * log(u1));
@@ -833,7 +843,7 @@ __global__ void init_block_kernel(S *__restrict__ X, long sx, long L, uint64_t s
     sincospi(2.0 * u2, &s, &c);
     if constexpr (std::is_same<S, float4>::value)
       st_cdf(x + e, cdf_from(cmake<double2>(rad * c, rad * s)));
-    else
+    else if constexpr (std::is_same<S, double2>::value)
       x[e] = cmake<double2>(rad * c, rad * s);
   }
 }
@@ -844,6 +854,9 @@ int launch_init_block(int nb, long L, int m, uint64_t seed, int kidx0, void *X, 
   const unsigned gx = (unsigned)std::min<long>(256, (L + 255) / 256);
   if (dtype == PC_DFS)
     init_block_kernel<float4><<<dim3(gx, m, nb), 256, 0, st>>>(static_cast<float4 *>(X), sx, L, seed, kidx0, mask, m,
+                                                               act);
+  else if (dtype == PC_C64)
+    init_block_kernel<float2><<<dim3(gx, m, nb), 256, 0, st>>>(static_cast<float2 *>(X), sx, L, seed, kidx0, mask, m,
                                                                act);
   else
     init_block_kernel<double2><<<dim3(gx, m, nb), 256, 0, st>>>(static_cast<double2 *>(X), sx, L, seed, kidx0, mask,

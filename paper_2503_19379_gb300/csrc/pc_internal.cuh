@@ -231,7 +231,8 @@ size_t gram_df_scratch_bytes(int nb, long L, int p);
 int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam, const std::vector<int> &zero,
                 int nbands, int m, double tol, double *evals, void *evecs, int *iters, double *resid);
 // counter-based initial columns; with mask (int [nb][m]) only the flagged columns of the act k-points are written
-// X: dtype PC_C128 or PC_DFS (the same FP64 values stored as double-float pairs)
+// X: dtype PC_C128, PC_DFS (the same FP64 values stored as double-float pairs) or PC_C64 (the same uniforms, the
+// normal deviates formed in FP32)
 int launch_init_block(int nb, long L, int m, uint64_t seed, int kidx0, void *X, long sx, cudaStream_t st,
                       const int *mask = nullptr, const int *act = nullptr, int dtype = PC_C128);
 // Algorithm 4.1 restart: flags (host, [nb][m]) the columns of the redo k-points to replace before the re-solve

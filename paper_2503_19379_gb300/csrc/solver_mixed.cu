@@ -55,7 +55,7 @@ struct MixedShared {
   bool any_zero;
   std::vector<int> zero;  // per k-point: k reduced to 0 (the constant fields are projected out)
   float2 *F[2], *AF[2];
-  float4 *X64[2];  // phase-2 block, double-float pairs (PC_DFS); start() uses X64[0] as complex128 scratch
+  float4 *X64[2];  // phase-2 block, double-float pairs (PC_DFS)
   float2 *R32;
   double2 *Gm, *Hm, *coef, *RQ, *GX;
   double *theta, *norms, *rn;
@@ -135,7 +135,7 @@ class MixedSolve {
     return set_act(list);
   }
 
-  // initial block (FP64 generator, narrowed) and Rayleigh-Ritz on span(X0), then the first residual
+  // initial block (the counter-based generator, complex64) and Rayleigh-Ritz on span(X0), then the first residual
   int start() {
     StreamScope scope(ctx, g.st);
     const int m = S.m, nb = S.nb;
@@ -143,12 +143,10 @@ class MixedSolve {
     const int na = g.b1 - g.b0;
     for (int b = g.b0; b < g.b1; ++b) g.act.push_back(b);
     RUN(set_act(g.act));
-    RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, S.Ld * 16.0 * m * na, [&] {
-      return launch_init_block(na, L, m, ctx->opts.seed, 0, S.X64[0], sX, g.st, nullptr, g.d_act);
+    RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, S.Ld * 8.0 * m * na, [&] {
+      return launch_init_block(na, L, m, ctx->opts.seed, 0, S.F[0], sF, g.st, nullptr, g.d_act, PC_C64);
     }));
-    RUN(DEFL(g.act, S.X64[0], sX, PC_C128));
-    RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, S.Ld * 24.0 * m * na,
-                  [&] { return launch_narrow(na, L, m, S.X64[0], sX, S.F[0], sF, g.st, g.d_act); }));
+    RUN(DEFL(g.act, S.F[0], sF, PC_C64));
     RUN(OP32(na, m, S.F[0], sF, S.AF[0], sF));
     RUN(run_stage(ctx, PC_STAGE_GRAM, 2, 8.0 * m * (m + 1) * S.Ld * na, 2.0 * m * S.Ld * 8.0 * na, [&] {
       return launch_gram_pair(na, L, m, PC_C64, S.F[0], S.AF[0], sF, S.Gm, S.Hm, g.scratch, S.scr, g.st, g.d_act, nb,
