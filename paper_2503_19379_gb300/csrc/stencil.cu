@@ -142,7 +142,7 @@ template <typename T, int TX, int TY> constexpr size_t opz_smem_bytes() {
 }
 
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) opz_kernel(const cplx<T> *__restrict__ X, long sx, cplx<T> *__restrict__ Y,
+__global__ void __launch_bounds__(TX * TY, 6) opz_kernel(const cplx<T> *__restrict__ X, long sx, cplx<T> *__restrict__ Y,
                                                       long sy, const T *__restrict__ m0, const KParam *__restrict__ kp,
                                                       const int *__restrict__ act, int logN, int ZC, T ih) {
   using C = cplx<T>;
@@ -179,24 +179,47 @@ __global__ void __launch_bounds__(TX * TY) opz_kernel(const cplx<T> *__restrict_
     gam = p.gamma;
   }
   const int tid = threadIdx.x;
+  // The plane-independent part of every index this thread uses is formed once, before the z walk (32-bit offsets:
+  // a field block holds 3 N^3 <= 2^26 entries); per plane only the z offset is added.
+  constexpr int NV = (3 * VP + NT - 1) / NT;  // v entries per thread and plane
+  constexpr int NE = (EP + NT - 1) / NT;      // e and c entries per thread and plane
+  const int pl = (int)plane, ni = (int)n;
+  int voff[NV];  // global offset of v entry tid + k NT within its plane (with the component), -1 past the plane
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const int i = tid + k * NT;
+    const int comp = i / VP, r = i - comp * VP, ly = r / VX, lx = r - ly * VX;
+    voff[k] = i < 3 * VP ? comp * ni + (((y0 + ly - 1) & mask) << logN) + ((x0 + lx - 1) & mask) : -1;
+  }
+  int eoff[NE], eloc[NE];  // e entry tid + k NT: M0 offset within its plane (-1 past the tile) and v local index
+#pragma unroll
+  for (int k = 0; k < NE; ++k) {
+    const int i = tid + k * NT;
+    const int ey = i / EX, ex = i - ey * EX;
+    eoff[k] = i < EP ? (((y0 + ey) & mask) << logN) + ((x0 + ex) & mask) : -1;
+    eloc[k] = (ey + 1) * VX + ex + 1;  // v local index of global (x0 + ex, y0 + ey)
+  }
+  const int ly = tid / TX, lx = tid - ly * TX;
+  const int yoff = ((y0 + ly) << logN) + x0 + lx;  // output point within its plane
+  const int eo = ly * EX + lx;                      // e index of (x0+lx, y0+ly)
+  const int co = (ly + 1) * EX + lx + 1;            // c index of (x0+lx, y0+ly)
 
   auto load_v = [&](int slot, int z) {
-    const int gz = z & mask;
+    const int zo = (z & mask) * pl;
     C *vs = vbuf + slot * 3 * VP;
-    for (int i = tid; i < 3 * VP; i += NT) {
-      const int comp = i / VP, r = i - comp * VP, ly = r / VX, lx = r - ly * VX;
-      const int gx = (x0 + lx - 1) & mask, gy = (y0 + ly - 1) & mask;
-      vs[i] = Xb[comp * n + gz * plane + ((long)gy << logN) + gx];
-    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+      if (voff[k] >= 0) vs[tid + k * NT] = Xb[voff[k] + zo];
   };
   // e(z) from v(z) (slot sz) and v(z-1) (slot szm), on the tile grown by one in +x/+y
   auto make_e = [&](int eslot, int z, int sz, int szm) {
     const C *v0 = vbuf + sz * 3 * VP, *vm = vbuf + szm * 3 * VP;
     C *es = ebuf + eslot * 3 * EP;
-    const int gz = z & mask;
-    for (int i = tid; i < EP; i += NT) {
-      const int ey = i / EX, ex = i - ey * EX;
-      const int o = (ey + 1) * VX + ex + 1;  // v local index of global (x0 + ex, y0 + ey)
+    const int zo = (z & mask) * pl;
+#pragma unroll
+    for (int k = 0; k < NE; ++k) {
+      if (eoff[k] < 0) continue;
+      const int i = tid + k * NT, o = eloc[k];
       const C v1 = v0[o], v2 = v0[VP + o], v3 = v0[2 * VP + o];
       const C d3v2 = dbwd(vm[VP + o], v2, ih, kh2);
       const C d2v3 = dbwd(v0[2 * VP + o - VX], v3, ih, kh1);
@@ -204,19 +227,20 @@ __global__ void __launch_bounds__(TX * TY) opz_kernel(const cplx<T> *__restrict_
       const C d1v3 = dbwd(v0[2 * VP + o - 1], v3, ih, kh0);
       const C d2v1 = dbwd(v0[o - VX], v1, ih, kh1);
       const C d1v2 = dbwd(v0[VP + o - 1], v2, ih, kh0);
-      const long gi = gz * plane + ((long)((y0 + ey) & mask) << logN) + ((x0 + ex) & mask);
+      const int gi = zo + eoff[k];
       es[i] = cscale(csub(d3v2, d2v3), m0[gi]);
-      es[EP + i] = cscale(csub(d1v3, d3v1), m0[n + gi]);
-      es[2 * EP + i] = cscale(csub(d2v1, d1v2), m0[2 * n + gi]);
+      es[EP + i] = cscale(csub(d1v3, d3v1), m0[ni + gi]);
+      es[2 * EP + i] = cscale(csub(d2v1, d1v2), m0[2 * ni + gi]);
     }
   };
   // c(z) from v(z) (slot sz) and v(z+1) (slot szp), on the tile grown by one in -x/-y
   auto make_c = [&](int cslot, int sz, int szp) {
     const C *v0 = vbuf + sz * 3 * VP, *vp = vbuf + szp * 3 * VP;
     C *cs = cbuf + cslot * EP;
-    for (int i = tid; i < EP; i += NT) {
-      const int cy = i / EX, cx = i - cy * EX;
-      const int o = cy * VX + cx;  // v local index of global (x0 + cx - 1, y0 + cy - 1)
+#pragma unroll
+    for (int k = 0; k < NE; ++k) {
+      if (eoff[k] < 0) continue;
+      const int i = tid + k * NT, o = eloc[k] - VX - 1;  // v local index of global (x0 + cx - 1, y0 + cy - 1)
       C cc = dfwd(v0[o], v0[o + 1], ih, kh0);
       cc = cadd(cc, dfwd(v0[VP + o], v0[VP + o + VX], ih, kh1));
       cc = cadd(cc, dfwd(v0[2 * VP + o], vp[2 * VP + o], ih, kh2));
@@ -241,9 +265,6 @@ __global__ void __launch_bounds__(TX * TY) opz_kernel(const cplx<T> *__restrict_
     {
       const C *e0 = ebuf + se * 3 * EP, *e1p = ebuf + (1 - se) * 3 * EP;  // e(z), e(z+1)
       const C *cm = cbuf + sc * EP, *c0p = cbuf + (1 - sc) * EP;          // c(z-1), c(z)
-      const int ly = tid / TX, lx = tid - ly * TX;
-      const int eo = ly * EX + lx;             // e index of (x0+lx, y0+ly)
-      const int co = (ly + 1) * EX + lx + 1;   // c index of (x0+lx, y0+ly)
       const C c0 = c0p[co];
       const C e1 = e0[eo], e2 = e0[EP + eo], e3 = e0[2 * EP + eo];
       C y1 = csub(dfwd(e3, e0[2 * EP + eo + EX], ih, kh1), dfwd(e2, e1p[EP + eo], ih, kh2));
@@ -252,10 +273,10 @@ __global__ void __launch_bounds__(TX * TY) opz_kernel(const cplx<T> *__restrict_
       y2 = cadd(y2, cscale(dbwd(c0p[co - EX], c0, ih, kh1), gam));
       C y3 = csub(dfwd(e2, e0[EP + eo + 1], ih, kh0), dfwd(e1, e0[eo + EX], ih, kh1));
       y3 = cadd(y3, cscale(dbwd(cm[co], c0, ih, kh2), gam));
-      const long gi = (long)z * plane + ((long)(y0 + ly) << logN) + x0 + lx;
+      const int gi = z * pl + yoff;
       Yb[gi] = y1;
-      Yb[n + gi] = y2;
-      Yb[2 * n + gi] = y3;
+      Yb[ni + gi] = y2;
+      Yb[2 * ni + gi] = y3;
     }
     sv = 1 - sv;
     se = 1 - se;
