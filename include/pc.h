@@ -68,9 +68,9 @@ typedef struct {
     int maxiter;           /* LOBPCG iteration cap per k-point and gamma-doubling round (default 400) */
     int max_doublings;     /* Algorithm 4.1 gamma doublings cap (default 8) */
     uint64_t seed;         /* seed of the counter-based initial blocks */
-    int groups;            /* PC_PREC_MIXED: k-point groups iterated on separate streams so that one group's
-                              latency-bound steps (Rayleigh-Ritz, host decisions) overlap the other's kernels;
-                              0 (default): 2 when there are at least 8 k-points, else 1 */
+    int groups;            /* PC_PREC_MIXED: k-point groups (at most 4) iterated on separate streams so that one
+                              group's latency-bound steps (Rayleigh-Ritz, host decisions) overlap the others'
+                              kernels; 0 (default): 4 from 16 k-points, 2 from 8, else 1 */
 } pc_opts;
 
 /* Fill *opts with the defaults listed above. */

@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(YP * 3 * (1 << LOGN)) fft_z_reg_kernel(const f
 #pragma unroll
   for (int z = 0; z < N; ++z) al[z * N] = v[z];
   __syncthreads();
-  const float fac = (float)((kp[b].gamma - 1.0) / kp[b].gamma);
+  const float fac = kp[b].pfacf;  // (gamma - 1) / gamma
   const float scale = 1.0f / (float)n;
   for (int i = threadIdx.x; i < YP * N * N; i += NT) {
     const int xx = i % N, z = (i / N) % N, yy = i / (N * N);

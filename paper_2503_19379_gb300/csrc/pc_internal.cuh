@@ -46,6 +46,7 @@ struct KParam {
   float gammaf;
   float khl[3];  // remainders: (khf, khl) and (gammaf, gammal) are the double-float values of k_i / 2 and gamma
   float gammal;
+  float pfacf;   // (gamma - 1) / gamma rounded to FP32 (the complex64 preconditioner's projection factor)
 };
 
 // internal dtype of the mixed solve's FP64-accurate block: complex double-float pairs, one float4 per element
@@ -124,9 +125,11 @@ struct pc_ctx {
   pc::DevBuf S[2], AS[2], Gm, Hm, coef, theta, norms, rnorm, rank, flag;
   // mixed-precision solve: FP64 block X, complex64 residual copy, coupling R^H S, FP64 X^H X, phases, masks
   pc::DevBuf X64[2], R32, RQ, GX, phase, mask;
-  // mixed solve with two k-point groups: the second group's stream, and pinned host copies of theta, column norms
-  // and Algorithm 4.1 norms (so that a group's device-to-host copies do not block the host)
-  cudaStream_t stream2 = nullptr;
+  // mixed solve with several k-point groups: the streams of groups 1.. (group 0 runs on `stream`), and pinned host
+  // copies of theta, column norms and Algorithm 4.1 norms (so that a group's device-to-host copies do not block the
+  // host)
+  static constexpr int kMaxGroups = 4;
+  cudaStream_t xstream[kMaxGroups - 1] = {};
   double *pinned = nullptr;
   size_t pinned_count = 0;
   // tracing: per-stage statistics and event pairs awaiting harvest
@@ -139,7 +142,8 @@ struct pc_ctx {
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
   ~pc_ctx() {
-    if (stream2) cudaStreamDestroy(stream2);
+    for (cudaStream_t s : xstream)
+      if (s) cudaStreamDestroy(s);
     if (pinned) cudaFreeHost(pinned);
     for (auto &p : pending) {
       cudaEventDestroy(p.a);

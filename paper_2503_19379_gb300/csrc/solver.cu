@@ -81,6 +81,7 @@ int upload_kpoints(pc_ctx *ctx, int nb, const double *kpts, const double *gammas
     kp[b].gamma = gammas[b];
     kp[b].gammaf = (float)gammas[b];
     kp[b].gammal = (float)(gammas[b] - (double)kp[b].gammaf);
+    kp[b].pfacf = (float)((gammas[b] - 1.0) / gammas[b]);
     for (int d = 0; d < 3; ++d) axis_symbols(ctx->N, kpts[3 * b + d], &sym[((size_t)b * 3 + d) * ctx->N]);
   }
   PC_CK(cudaMemcpyAsync(ctx->kparam.p, kp.data(), sizeof(KParam) * nb, cudaMemcpyHostToDevice, ctx->stream));

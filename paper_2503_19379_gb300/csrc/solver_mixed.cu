@@ -8,22 +8,22 @@
 //   |Op| |Q| large while the coupling is O(|R| |Q|), so the rounding of the product swamps it. Because Op is Hermitian
 //   and AX = X Theta + R exactly (R is defined that way), X^H Op Q = Theta X^H Q + R^H Q, which only multiplies
 //   small, accurately stored quantities.
-// * The X-X block (X^H X, X^H AX) and the residual need FP64: the residual floor of a complex64 X is eps32 |Op| / lambda
-//   (about 1e-3 here), and the X-X block's rounding shifts the Ritz values by eps32 lambda.
+// * The X-X block (X^H X, X^H AX) and the residual need FP64: the residual floor of a complex64 X is
+//   eps32 |Op| / lambda (about 1e-3 here), and the X-X block's rounding shifts the Ritz values by eps32 lambda.
 // Phase 1 (every k-point starts here): X and AX in complex64 as well, until the complex64 residual stops falling.
 // Phase 2: X stored as double-float pairs (hi + lo FP32, ~48 bits); X' = X C_X + P' (complex64 correction),
 // AX' = Op X' by the stencil fused with the residual R = AX' - X' Theta (AX' itself is never stored), and the X-X
-// Gram block X^H X, all three in double-float arithmetic (mixed_df.cu) on the FP32 pipe. The X-X block of the projected operator is Theta X^H X + R^H X
-// (AX = X Theta + R), with R^H X from the complex64 product R^H [X | Q]: its rounding is eps32 |R| |X|, small
-// because R is.
+// Gram block X^H X, all three in double-float arithmetic (mixed_df.cu) on the FP32 pipe. The X-X block of the
+// projected operator is Theta X^H X + R^H X (AX = X Theta + R), with R^H X from the complex64 product R^H [X | Q]:
+// its rounding is eps32 |R| |X|, small because R is.
 // Convergence and Algorithm 4.1 are decided in phase 2 only, on FP64 residuals and FP64 norms.
 //
-// Scheduling: the k-points are split into contiguous groups (opts.groups, default 2 from 8 k-points on), each with
-// its own stream, active list, scratch and pinned host copies of its residual norms. Every iteration of a group ends
-// with its residual norms copied to the host and an event; the host then serves the groups in turn -- waits for a
-// group's event, takes its convergence decisions, enqueues its next iteration -- so that while it waits for one group
-// the other group's kernels occupy the GPU. This hides the latency-bound steps (the Rayleigh-Ritz kernel runs one
-// block per k-point, the host decisions leave the GPU idle) behind the other group's bandwidth-bound kernels.
+// Scheduling: the k-points are split into contiguous groups (opts.groups, up to 4; default 4 from 16 k-points, 2
+// from 8), each with its own stream, active list, scratch and pinned host copies of its residual norms. Every
+// iteration of a group ends with its residual norms copied to the host and an event; the host then serves the
+// groups in turn -- waits for a group's event, takes its convergence decisions, enqueues its next iteration -- so
+// that while it waits for one group the other groups' kernels occupy the GPU. This hides the latency-bound steps (the Rayleigh-Ritz
+// kernel runs one block per k-point, the host decisions leave the GPU idle) behind bandwidth-bound kernels.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -422,8 +422,10 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
   const long n = ctx->n, L = 3 * n;
   const long sF = 3L * m * L, sX = (long)m * L;
   const int nmax = 3 * m;
-  int ngroups = ctx->opts.groups > 0 ? ctx->opts.groups : (nb >= 8 ? 2 : 1);
-  ngroups = std::max(1, std::min(ngroups, std::min(nb, 2)));
+  // default: 4 groups from 16 k-points (measured on the 40-k-point fcc batch: 60.1 k-points/s against 57.1 with 2
+  // groups and 56.8 with 3), 2 from 8
+  int ngroups = ctx->opts.groups > 0 ? ctx->opts.groups : (nb >= 16 ? 4 : (nb >= 8 ? 2 : 1));
+  ngroups = std::max(1, std::min(ngroups, std::min(nb, pc_ctx::kMaxGroups)));
   PC_CK(ctx->S[0].reserve(sizeof(float2) * (size_t)sF * nb));
   PC_CK(ctx->S[1].reserve(sizeof(float2) * (size_t)sF * nb));
   PC_CK(ctx->AS[0].reserve(sizeof(float2) * (size_t)sF * nb));
@@ -462,7 +464,8 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
     PC_CK(cudaMallocHost(&ctx->pinned, sizeof(double) * npin));
     ctx->pinned_count = npin;
   }
-  if (ngroups > 1 && !ctx->stream2) PC_CK(cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking));
+  for (int gi = 1; gi < ngroups; ++gi)
+    if (!ctx->xstream[gi - 1]) PC_CK(cudaStreamCreateWithFlags(&ctx->xstream[gi - 1], cudaStreamNonBlocking));
 
   MixedShared S;
   S.ctx = ctx;
@@ -533,16 +536,16 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
     Group &g = groups[gi];
     g.b0 = (int)((long)nb * gi / ngroups);
     g.b1 = (int)((long)nb * (gi + 1) / ngroups);
-    g.st = gi == 0 ? st0 : ctx->stream2;
+    g.st = gi == 0 ? st0 : ctx->xstream[gi - 1];
     g.d_act = ctx->rank.as<int>() + (size_t)nb * (1 + gi);
     g.scratch = static_cast<char *>(ctx->scratch.p) + scr * gi;
     PC_CK(cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming));
   }
-  // the second stream starts after everything the caller's stream holds (setup, uploads above)
+  // the other groups' streams start after everything the caller's stream holds (setup, uploads above)
   if (ngroups > 1) {
     PC_CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
     PC_CK(cudaEventRecord(ready, st0));
-    PC_CK(cudaStreamWaitEvent(ctx->stream2, ready, 0));
+    for (int gi = 1; gi < ngroups; ++gi) PC_CK(cudaStreamWaitEvent(ctx->xstream[gi - 1], ready, 0));
   }
   for (int gi = 0; gi < ngroups && rc == PC_OK; ++gi) rc = MixedSolve(S, groups[gi]).start();
   // serve the groups in turn until all have finished
@@ -562,13 +565,15 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
     }
     if (!any) break;
   }
-  // join: the caller's stream waits for the second group's work
+  // join: the caller's stream waits for the other groups' work
   if (ngroups > 1) {
-    cudaEvent_t fin = nullptr;
-    if (cudaEventCreateWithFlags(&fin, cudaEventDisableTiming) == cudaSuccess) {
-      cudaEventRecord(fin, ctx->stream2);
-      cudaStreamWaitEvent(st0, fin, 0);
-      cudaEventDestroy(fin);
+    for (int gi = 1; gi < ngroups; ++gi) {
+      cudaEvent_t fin = nullptr;
+      if (cudaEventCreateWithFlags(&fin, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(fin, ctx->xstream[gi - 1]);
+        cudaStreamWaitEvent(st0, fin, 0);
+        cudaEventDestroy(fin);
+      }
     }
     cudaEventDestroy(ready);
   }

@@ -420,16 +420,17 @@ def test_mixed_fcc_batch_matches_fp64(pcmod):
     assert np.all(b["resid"] <= w.tol)
 
 
-def test_mixed_two_groups_match_one(pcmod):
-    """The two-stream schedule (k-points in two groups, served in turn) computes the same thing as one group: the
-    same eigenvalues to far below the tolerance, every residual within tol, on 10 FCC k-points (Gamma, X and L
-    among them, so both groups hold a k = 0 point or a folded one). Chunked reductions depend on the batch size, so
-    the two runs differ in rounding, not in the converged eigenpairs."""
+@pytest.mark.parametrize("groups", [2, 4])
+def test_mixed_groups_match_one(pcmod, groups):
+    """The multi-stream schedule (k-points in 2 or 4 groups, served in turn) computes the same thing as one group:
+    the same eigenvalues to far below the tolerance, every residual within tol, on 10 FCC k-points (Gamma, X and L
+    among them, so the groups hold a k = 0 point or a folded one). Chunked reductions depend on the batch size, so
+    the runs differ in rounding, not in the converged eigenpairs."""
     w = wl.workload_fcc_32()
     idx = [0, 3, 6, 10, 14, 20, 24, 28, 33, 39]
     kp = w.kpts[idx]
     S1, _ = make_solver(pcmod, w.N, structure=w.structure, precision=1, groups=1)
-    S2, _ = make_solver(pcmod, w.N, structure=w.structure, precision=1, groups=2)
+    S2, _ = make_solver(pcmod, w.N, structure=w.structure, precision=1, groups=groups)
     a = S1.solve(kp, w.nbands, w.tol)
     b = S2.solve(kp, w.nbands, w.tol)
     assert a["status"] == 0 and b["status"] == 0
