@@ -717,91 +717,73 @@ int launch_narrow(int nb, long L, int m, const void *X, long sx, void *Y, long s
 
 // ------------------------------------------------------------------------------------------------ k = 0 projection
 // Removes the mean of each component of each column for k-points with flags[b] != 0 (the constant kernel fields).
-// S: the element storage, float2 (complex64), double2 (complex128) or float4 (double-float pairs)
+// One block per (column, component) and k-point: FP64 sums over the component (strided, then a block tree), then
+// the subtraction in a second pass over the same entries (L2-resident). Blocks of k-points without the flag return
+// at once, so the launch can cover a whole active list. S: the element storage, float2 (complex64), double2
+// (complex128) or float4 (double-float pairs).
 template <typename S>
-__global__ void __launch_bounds__(256) mean_partial_kernel(const S *__restrict__ X, long sx, long n, long chunk,
-                                                          const int *__restrict__ flags, double2 *__restrict__ part,
-                                                          const int *__restrict__ act) {
-  const int bi = blockIdx.z, col = blockIdx.y;  // col = j * 3 + comp
+__global__ void __launch_bounds__(256) deflate_kernel(S *__restrict__ X, long sx, long n, const int *__restrict__ flags,
+                                                     const int *__restrict__ act) {
+  const int bi = blockIdx.y, col = blockIdx.x;  // col = j * 3 + comp
   const int b = act ? act[bi] : bi;
   if (!flags[b]) return;
-  const S *x = X + (long)b * sx + (long)col * n;
-  double sr = 0, si = 0;
-  const long beg = (long)blockIdx.x * chunk, end = min(n, beg + chunk);
-  for (long l = beg + threadIdx.x; l < end; l += blockDim.x) {
+  S *x = X + (long)b * sx + (long)col * n;
+  double sr = 0.0, si = 0.0;
+  for (long l = threadIdx.x; l < n; l += blockDim.x) {
     const double2 v = ld_c128(x + l);
     sr += v.x;
     si += v.y;
   }
-  __shared__ double red[2][256];
-  red[0][threadIdx.x] = sr;
-  red[1][threadIdx.x] = si;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) {
-      red[0][threadIdx.x] += red[0][threadIdx.x + w];
-      red[1][threadIdx.x] += red[1][threadIdx.x + w];
-    }
-    __syncthreads();
+  __shared__ double red[2][8];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
   }
-  if (threadIdx.x == 0) part[((long)bi * gridDim.y + col) * gridDim.x + blockIdx.x] = cmake<double2>(red[0][0], red[1][0]);
-}
-
-template <typename S>
-__global__ void __launch_bounds__(256) mean_subtract_kernel(S *__restrict__ X, long sx, long n, int nchunk,
-                                                           const int *__restrict__ flags,
-                                                           const double2 *__restrict__ part,
-                                                           const int *__restrict__ act) {
-  const int bi = blockIdx.z, col = blockIdx.y;
-  const int b = act ? act[bi] : bi;
-  if (!flags[b]) return;
-  __shared__ double2 mean;
-  if (threadIdx.x == 0) {
-    double2 s = cmake<double2>(0.0, 0.0);
-    for (int c = 0; c < nchunk; ++c) s = cadd(s, part[((long)bi * gridDim.y + col) * nchunk + c]);
-    mean = cmake<double2>(s.x / (double)n, s.y / (double)n);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][w] = sr;
+    red[1][w] = si;
   }
   __syncthreads();
-  S *x = X + (long)b * sx + (long)col * n;
+  double mr = 0.0, mi = 0.0;
+  for (int i = 0; i < nw; ++i) {
+    mr += red[0][i];
+    mi += red[1][i];
+  }
+  mr /= (double)n;
+  mi /= (double)n;
   if constexpr (std::is_same<S, float4>::value) {
-    const df mr = df_from(mean.x), mi = df_from(mean.y);
-    for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x) {
+    const df dr = df_from(mr), di = df_from(mi);
+    for (long l = threadIdx.x; l < n; l += blockDim.x) {
       cdf v = ld_cdf(x + l);
-      v.re = df_sub(v.re, mr);
-      v.im = df_sub(v.im, mi);
+      v.re = df_sub(v.re, dr);
+      v.im = df_sub(v.im, di);
       st_cdf(x + l, v);
     }
   } else {
     using T = decltype(S{}.x);
-    const T mr = (T)mean.x, mi = (T)mean.y;
-    for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x) {
-      x[l].x -= mr;
-      x[l].y -= mi;
+    const T tr = (T)mr, ti = (T)mi;
+    for (long l = threadIdx.x; l < n; l += blockDim.x) {
+      x[l].x -= tr;
+      x[l].y -= ti;
     }
   }
 }
 
-template <typename S>
-static int deflate_t(int nb, long n, int m, void *X, long sx, const int *flags, double2 *part, int nchunk, long chunk,
-                     unsigned gx, cudaStream_t st, const int *act) {
-  mean_partial_kernel<S><<<dim3(nchunk, 3 * m, nb), 256, 0, st>>>(static_cast<const S *>(X), sx, n, chunk, flags, part,
-                                                                  act);
-  PC_CK_LAUNCH();
-  mean_subtract_kernel<S><<<dim3(gx, 3 * m, nb), 256, 0, st>>>(static_cast<S *>(X), sx, n, nchunk, flags, part, act);
-  PC_CK_LAUNCH();
-  return PC_OK;
-}
-
 int launch_deflate(int nb, long n, int m, void *X, long sx, const int *flags, void *scratch, cudaStream_t st,
                    const int *act, int dtype) {
+  (void)scratch;
   if (nb == 0 || m == 0) return PC_OK;
-  const int nchunk = (int)std::min<long>(16, std::max<long>(1, n / 4096));
-  const long chunk = (n + nchunk - 1) / nchunk;
-  double2 *part = static_cast<double2 *>(scratch);
-  const unsigned gx = (unsigned)std::min<long>(64, (n + 255) / 256);
-  if (dtype == PC_C128) return deflate_t<double2>(nb, n, m, X, sx, flags, part, nchunk, chunk, gx, st, act);
-  if (dtype == PC_DFS) return deflate_t<float4>(nb, n, m, X, sx, flags, part, nchunk, chunk, gx, st, act);
-  return deflate_t<float2>(nb, n, m, X, sx, flags, part, nchunk, chunk, gx, st, act);
+  const dim3 grid(3 * m, nb);
+  if (dtype == PC_C128)
+    deflate_kernel<double2><<<grid, 256, 0, st>>>(static_cast<double2 *>(X), sx, n, flags, act);
+  else if (dtype == PC_DFS)
+    deflate_kernel<float4><<<grid, 256, 0, st>>>(static_cast<float4 *>(X), sx, n, flags, act);
+  else
+    deflate_kernel<float2><<<grid, 256, 0, st>>>(static_cast<float2 *>(X), sx, n, flags, act);
+  PC_CK_LAUNCH();
+  return PC_OK;
 }
 
 // ------------------------------------------------------------------------------------------------ initial blocks

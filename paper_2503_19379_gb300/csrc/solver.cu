@@ -366,7 +366,7 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
                      [&] { return launch_block_update(nbk, L, p, m, PC_C128, Sx, sS, Cx, sc, Y, sS, st, d_act); });
   };
   auto DEFL = [&](int nbk, void *X) {
-    return run_stage(ctx, PC_STAGE_OTHER, 2, 4.0 * Ld * m * nbk, 2.0 * Ld * cb * m * nbk,
+    return run_stage(ctx, PC_STAGE_OTHER, 1, 4.0 * Ld * m * nbk, 2.0 * Ld * cb * m * nbk,
                      [&] { return launch_deflate(nbk, n, m, X, sS, d_zero, scratch, st, d_act); });
   };
 

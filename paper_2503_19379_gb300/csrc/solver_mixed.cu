@@ -120,19 +120,17 @@ class MixedSolve {
                                                  g.d_act);
                      });
   }
-  // projection of the constant fields, on the k = 0 points of `list` only (the active list of the launches around
-  // it, restored afterwards)
+  // projection of the constant fields on the k = 0 points of `list`, which is the active list already on the device
+  // (the kernel's blocks of other k-points return at once); nothing is launched when `list` holds no k = 0 point
   int DEFL(const std::vector<int> &list, void *X, long sx, int dtype) {
     if (!S.any_zero) return PC_OK;
-    std::vector<int> z;
-    for (int b : list)
-      if (S.zero[b]) z.push_back(b);
-    if (z.empty()) return PC_OK;
-    RUN(set_act(z));
-    const int nz = (int)z.size();
-    RUN(run_stage(ctx, PC_STAGE_OTHER, 2, 4.0 * S.Ld * S.m * nz, 2.0 * S.Ld * (dtype == PC_C64 ? 8.0 : 16.0) * S.m * nz,
-                  [&] { return launch_deflate(nz, S.n, S.m, X, sx, S.d_zero, g.scratch, g.st, g.d_act, dtype); }));
-    return set_act(list);
+    int nz = 0;
+    for (int b : list) nz += S.zero[b] != 0;
+    if (nz == 0) return PC_OK;
+    const int na = (int)list.size();
+    return run_stage(ctx, PC_STAGE_OTHER, 1, 4.0 * S.Ld * S.m * nz,
+                     2.0 * S.Ld * (dtype == PC_C64 ? 8.0 : 16.0) * S.m * nz,
+                     [&] { return launch_deflate(na, S.n, S.m, X, sx, S.d_zero, g.scratch, g.st, g.d_act, dtype); });
   }
 
   // initial block (the counter-based generator, complex64) and Rayleigh-Ritz on span(X0), then the first residual
