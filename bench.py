@@ -250,6 +250,12 @@ def kernel_case(args):
         Gt = torch.from_numpy(Gm).cuda()
         Ht = torch.from_numpy(Hm).cuda()
         run = lambda: pc.rayleigh_ritz(Gt, Ht, 16)
+    elif args.kernel_case == "solve4":
+        # a mixed-precision solve of 4 k-points of the path: the solver's own kernels at production shapes (the
+        # double-float stencil with the residual epilogue on pair storage, the double-float update and Gram)
+        s4 = pc.Solver(w.N, eps, precision=pc.pc.PC_PREC_MIXED)
+        k4 = w.kpts[[3, 13, 23, 33]]
+        run = lambda: s4.solve(k4, w.nbands, w.tol)
     elif args.kernel_case.startswith("gram"):
         S = X.reshape(nb, m, L)
         AS = S.clone()
@@ -292,7 +298,7 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=12)
     ap.add_argument("--kernel-case", default=None,
                     choices=["stencil64", "stencil32", "stencil_df", "precond64", "precond32", "gram64", "gram32",
-                             "rr"],
+                             "rr", "solve4"],
                     help="run one hot kernel alone on a small batch (profiling) instead of the benchmark")
     args = ap.parse_args()
     if args.kernel_case:

@@ -729,10 +729,22 @@ __global__ void __launch_bounds__(256) deflate_kernel(S *__restrict__ X, long sx
   if (!flags[b]) return;
   S *x = X + (long)b * sx + (long)col * n;
   double sr = 0.0, si = 0.0;
-  for (long l = threadIdx.x; l < n; l += blockDim.x) {
-    const double2 v = ld_c128(x + l);
-    sr += v.x;
-    si += v.y;
+  if constexpr (std::is_same<S, float2>::value) {
+    // complex64 data: per-thread sums in FP32 (their rounding is that of the data), FP64 from the warp sums on
+    float fr = 0.f, fi = 0.f;
+    for (long l = threadIdx.x; l < n; l += blockDim.x) {
+      const float2 v = x[l];
+      fr += v.x;
+      fi += v.y;
+    }
+    sr = fr;
+    si = fi;
+  } else {
+    for (long l = threadIdx.x; l < n; l += blockDim.x) {
+      const double2 v = ld_c128(x + l);
+      sr += v.x;
+      si += v.y;
+    }
   }
   __shared__ double red[2][8];
 #pragma unroll

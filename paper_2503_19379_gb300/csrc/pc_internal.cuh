@@ -130,6 +130,9 @@ struct pc_ctx {
   // host)
   static constexpr int kMaxGroups = 4;
   cudaStream_t xstream[kMaxGroups - 1] = {};
+  // per group: a stream of the highest priority for its Rayleigh-Ritz launches (few blocks, latency-bound), so that
+  // their blocks take SMs ahead of the pending blocks of other groups' large grids
+  cudaStream_t rrstream[kMaxGroups] = {};
   double *pinned = nullptr;
   size_t pinned_count = 0;
   // tracing: per-stage statistics and event pairs awaiting harvest
@@ -143,6 +146,8 @@ struct pc_ctx {
   std::vector<cudaEvent_t> event_pool;
   ~pc_ctx() {
     for (cudaStream_t s : xstream)
+      if (s) cudaStreamDestroy(s);
+    for (cudaStream_t s : rrstream)
       if (s) cudaStreamDestroy(s);
     if (pinned) cudaFreeHost(pinned);
     for (auto &p : pending) {
@@ -193,6 +198,9 @@ int launch_block_update(int nb, long L, int p, int q, int dtype, const void *S, 
 // sg, sc: batch strides of G/H and of coef in elements; <= 0 means packed (n n, n m)
 int launch_rr(int nb, int n, int m, const void *G, const void *H, double drop, double *theta, void *coef,
               int *rank, cudaStream_t st, const int *act, long sg = 0, long sc = 0);
+// algorithmic FP64 flops of one Rayleigh-Ritz pencil of n columns, m wanted pairs (Cholesky, the two substitutions,
+// Householder tridiagonalisation, back-transformation; bisection and inverse iteration are of lower order)
+double rr_flops(int n, int m);
 int launch_residual(int nb, long L, int m, const void *X, long sx, const void *AX, long sax, const double *theta,
                     void *R, long sr, double *norms, void *scratch, size_t scratch_bytes, cudaStream_t st,
                     const int *act);

@@ -14,19 +14,17 @@
 //      position so that members are orthogonal;
 //   7. back-transformation y = Q Phi z, then coef = D P L^{-H} y.
 //
-// A GB300 SM retires about 2 FP64 FMA per clock, and a block's FP64 work here is a few hundred thousand operations,
-// so the kernel is bound by the length of its dependent chains. Every phase is therefore spread over the block:
-// substitutions column-oriented (one rank-1 row update per step for all threads), norms and dot products as warp
-// reductions only where a single value is needed (the FP64 pipe is the scarce unit: a 32-wide reduction spends 5
-// full-width FP64 additions on one sum, so matrix-vector products run one thread per row instead), the
-// back-transformation for all wanted vectors at once (partial dot products over row chunks, one short reduction
-// per vector, a parallel update), shared matrices with an odd leading dimension (row-wise access by consecutive
-// threads hits distinct banks), reciprocals of pivots taken once. Bisection (step 5) runs a group of 8 lanes per
-// eigenvalue (multisection: each lane counts at one of 8 interior points), first in FP32 down to ~30 eps32 |T|
-// (backward-stable Sturm counts make the FP32 bracket exact for a matrix within a few eps32 |T|; the bracket is
-// widened by 16 eps32 |T| and verified by two FP64 counts, with the Gershgorin interval as fallback), then in FP64
-// to the absolute width eps64 |T| (LAPACK's default for bisection, below which the FP64 Sturm count itself is not
-// accurate).
+// A GB300 SM retires about 2 FP64 FMA per clock, so one warp-wide FP64 instruction holds the FP64 unit of its SM
+// sub-partition for tens of cycles and the kernel is bound by its count of FP64 warp instructions on the longest
+// chain. Every phase is therefore spread over the block and over the four sub-partitions: substitutions
+// column-oriented (one rank-1 row update per step for all threads), matrix-vector products split by rows and column
+// quarters, the back-transformation for all wanted vectors at once (short shuffle trees per vector), shared
+// matrices with an odd leading dimension (row-wise access by consecutive threads hits distinct banks), reciprocals
+// and square roots of pivots taken once. Bisection (step 5) runs a group of 8 lanes per eigenvalue (multisection:
+// each lane counts at one of 8 interior points), first in FP32 down to ~30 eps32 |T| (backward-stable Sturm counts
+// make the FP32 bracket exact for a matrix within a few eps32 |T|; the bracket is widened by 16 eps32 |T| and
+// verified by two FP64 counts, with the Gershgorin interval as fallback), then in FP64 to the absolute width
+// eps64 |T| (LAPACK's default for bisection, below which the FP64 Sturm count itself is not accurate).
 #include <cfloat>
 #include <climits>
 #include <cmath>
@@ -693,6 +691,13 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
 }
 
 }  // namespace
+
+double rr_flops(int n, int m) {
+  const double c = (double)n * n * n;
+  // complex multiply-adds: Cholesky n^3/6, the two substitutions 2 x n^3/2, tridiagonalisation 2n^3/3 (matrix-vector
+  // product and rank-2 update per step), back-transformation 3 n^2 m / 2; 8 real flops each
+  return 8.0 * (c / 6.0 + c + 2.0 * c / 3.0 + 1.5 * (double)n * n * m);
+}
 
 int launch_rr(int nb, int n, int m, const void *G, const void *H, double drop, double *theta, void *coef, int *rank,
               cudaStream_t st, const int *act, long sg, long sc) {

@@ -358,7 +358,7 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
     });
   };
   auto RR = [&](int nbk, int nn) {
-    return run_stage(ctx, PC_STAGE_RR, 1, 0.0, 2.0 * nn * nn * cb * nbk,
+    return run_stage(ctx, PC_STAGE_RR, 1, rr_flops(nn, m) * nbk, 2.0 * nn * nn * cb * nbk,
                      [&] { return launch_rr(nbk, nn, m, Gm, Hm, drop, theta, coef, nullptr, st, d_act); });
   };
   auto UPD = [&](int nbk, int p, const void *Sx, const void *Cx, long sc, void *Y) {

@@ -85,6 +85,8 @@ struct Group {
   bool haveP = false, finished = false;
   uint64_t restarts = 0;
   cudaEvent_t ev = nullptr;
+  cudaStream_t rst = nullptr;                        // high-priority stream of its Rayleigh-Ritz launches
+  cudaEvent_t to_rr = nullptr, from_rr = nullptr;  // hand-offs between st and rst
 };
 
 class MixedSolve {
@@ -120,6 +122,24 @@ class MixedSolve {
                                                  g.d_act);
                      });
   }
+  // Rayleigh-Ritz of the group's pencils (nc columns; patch: the coupling blocks first) on the group's high-priority
+  // stream, joined back to its stream: the few blocks of this latency-bound kernel then take SMs ahead of the other
+  // groups' pending blocks instead of queueing behind them
+  int RR(int na, int nc, bool patch) {
+    const int m = S.m;
+    return run_stage(ctx, PC_STAGE_RR, patch ? 2 : 1, rr_flops(nc, m) * na, 2.0 * nc * nc * 16.0 * na, [&] {
+      PC_CK(cudaEventRecord(g.to_rr, g.st));
+      PC_CK(cudaStreamWaitEvent(g.rst, g.to_rr, 0));
+      int rc = patch ? launch_rr_patch(na, nc, m, S.Gm, S.Hm, S.RQ, S.theta, S.GX, S.d_phase, g.rst, g.d_act, S.sG,
+                                       S.sRS)
+                     : PC_OK;
+      if (rc == PC_OK)
+        rc = launch_rr(na, nc, m, S.Gm, S.Hm, S.drop, S.theta, S.coef, nullptr, g.rst, g.d_act, S.sG, S.sC);
+      PC_CK(cudaEventRecord(g.from_rr, g.rst));
+      PC_CK(cudaStreamWaitEvent(g.st, g.from_rr, 0));
+      return rc;
+    });
+  }
   // projection of the constant fields on the k = 0 points of `list`, which is the active list already on the device
   // (the kernel's blocks of other k-points return at once); nothing is launched when `list` holds no k = 0 point
   int DEFL(const std::vector<int> &list, void *X, long sx, int dtype) {
@@ -150,11 +170,7 @@ class MixedSolve {
       return launch_gram_pair(na, L, m, PC_C64, S.F[0], S.AF[0], sF, S.Gm, S.Hm, g.scratch, S.scr, g.st, g.d_act, nb,
                               S.sG);
     }));
-    RUN(run_stage(ctx, PC_STAGE_RR, 1, 0.0, 2.0 * m * m * 16.0 * na,
-                  [&] {
-                    return launch_rr(na, m, m, S.Gm, S.Hm, S.drop, S.theta, S.coef, nullptr, g.st, g.d_act, S.sG,
-                                     S.sC);
-                  }));
+    RUN(RR(na, m, false));
     RUN(run_stage(ctx, PC_STAGE_UPDATE, 1, 8.0 * m * m * S.Ld * na, 2.0 * m * S.Ld * 8.0 * na, [&] {
       return launch_block_update(na, L, m, m, PC_C64, S.F[0], sF, S.coef, S.sC, S.F[1], sF, g.st, g.d_act);
     }));
@@ -368,11 +384,7 @@ class MixedSolve {
       }));
       RUN(set_act(g.act));
     }
-    RUN(run_stage(ctx, PC_STAGE_RR, 1, 0.0, 2.0 * nc * nc * 16.0 * na, [&] {
-      int rc = launch_rr_patch(na, nc, m, S.Gm, S.Hm, S.RQ, S.theta, S.GX, S.d_phase, g.st, g.d_act, S.sG, S.sRS);
-      if (rc) return rc;
-      return launch_rr(na, nc, m, S.Gm, S.Hm, S.drop, S.theta, S.coef, nullptr, g.st, g.d_act, S.sG, S.sC);
-    }));
+    RUN(RR(na, nc, true));
     // ---- P' = [W P] coef_{W,P} (complex64), then X' per phase
     RUN(run_stage(ctx, PC_STAGE_UPDATE, 1, 8.0 * nq * m * S.Ld * na, (double)(nq + m) * S.Ld * 8.0 * na, [&] {
       return launch_block_update(na, L, nq, m, PC_C64, S.F[cur] + (long)m * L, sF, S.coef + (long)m * m, S.sC,
@@ -538,6 +550,14 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
     g.d_act = ctx->rank.as<int>() + (size_t)nb * (1 + gi);
     g.scratch = static_cast<char *>(ctx->scratch.p) + scr * gi;
     PC_CK(cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming));
+    PC_CK(cudaEventCreateWithFlags(&g.to_rr, cudaEventDisableTiming));
+    PC_CK(cudaEventCreateWithFlags(&g.from_rr, cudaEventDisableTiming));
+    if (!ctx->rrstream[gi]) {
+      int lo = 0, hi = 0;
+      PC_CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      PC_CK(cudaStreamCreateWithPriority(&ctx->rrstream[gi], cudaStreamNonBlocking, hi));
+    }
+    g.rst = ctx->rrstream[gi];
   }
   // the other groups' streams start after everything the caller's stream holds (setup, uploads above)
   if (ngroups > 1) {
@@ -576,8 +596,11 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
     cudaEventDestroy(ready);
   }
   const cudaError_t e0 = cudaStreamSynchronize(st0);
-  for (auto &g : groups)
+  for (auto &g : groups) {
     if (g.ev) cudaEventDestroy(g.ev);
+    if (g.to_rr) cudaEventDestroy(g.to_rr);
+    if (g.from_rr) cudaEventDestroy(g.from_rr);
+  }
   if (rc != PC_OK) return rc;
   PC_CK(e0);
   PC_CK(cudaStreamSynchronize(st0));
