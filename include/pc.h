@@ -60,7 +60,8 @@ extern "C" {
 typedef struct pc_ctx pc_ctx;
 
 typedef struct {
-    int order;             /* k of Table 1: 1 -> 2nd-order stencils (the only order the CUDA kernels implement) */
+    int order;             /* k of Table 1: 1 (default) -> 2nd-order stencils, 2, 3, 4 -> 4th, 6th, 8th order;
+                              orders above 1 need precision PC_PREC_FP64 (the mixed solve is second order) */
     double gamma_override; /* > 0: use this penalty instead of eq. pnt_number */
     int precond;           /* PC_PRECOND_GAMMA or PC_PRECOND_LAPLACIAN */
     int precision;         /* PC_PREC_FP64 or PC_PREC_MIXED */
@@ -151,10 +152,12 @@ int pc_reset_stats(pc_ctx *ctx);
  * Runs a device kernel; synchronous. */
 int pc_eps_spheres(int N, int nsph, const double *spheres, double eps_bg, double *eps_out);
 
-/* a1: Y = Op X = A M0 A' X + gamma B'B X for nb k-points x m fields (eq. Ker_comp; stencils of Section 4.1.2).
+/* a1: Y = Op X = A M0 A' X + gamma B'B X for nb k-points x m fields (eq. Ker_comp; stencils of Section 4.1.2,
+ * of the context's order: Table 1's 2k-th order schemes).
  *   kpts: host [nb][3] (used as given, no zone reduction); gammas: host [nb].
- *   X, Y: device blocks, dtype PC_C128, PC_C64 or PC_C128_DF (complex128 data, double-float arithmetic), batch
- *         stride m*3N^3 elements. X and Y must not overlap. */
+ *   X, Y: device blocks, dtype PC_C128, PC_C64 or PC_C128_DF (complex128 data, double-float arithmetic; order 1
+ *         only), batch stride m*3N^3 elements. X and Y must not overlap. Orders above 1 use a scratch block of
+ *         4 m N^3 entries per k-point owned by the context. */
 int pc_apply_op(pc_ctx *ctx, int nb, const double *kpts, const double *gammas, int m, int dtype, const void *X,
                 void *Y);
 
@@ -166,6 +169,10 @@ int pc_apply_half(pc_ctx *ctx, int nb, const double *kpts, int m, const void *X,
  *   out (device double [nb][m][3]) = (|M0^{1/2} A' x|^2, |B x|^2, |x|^2).
  * lambda_re = out[0]/out[2]; the symmetric Rayleigh quotient is (out[0] + gamma out[1]) / out[2]. */
 int pc_recompute_norms(pc_ctx *ctx, int nb, const double *kpts, int m, const void *X, double *out);
+
+/* Table 1: the weights of the 2k-th order staggered difference (c_s) and midpoint average (d_s), s = 1..4 (zero
+ * past k), for order = k in 1..4 (c, d: host double[4]). Host only. PC_EINVAL for another order. */
+int pc_stencil_coefficients(int order, double *c, double *d);
 
 /* a2: W = P^{-1} R with P = A A' + gamma B'B (or the vector Laplacian, per opts.precond): forward 3D FFT, the exact
  * inverse of the 3x3 symbol sigma I + (gamma-1) conj(d) d^T per mode, inverse 3D FFT (Algorithm 5.1,

@@ -6,7 +6,7 @@ tensors for device buffers) and raises on any library error. There is no CPU fal
 without a built library raises.
 """
 from .pc import (PCError, Solver, block_update, eigh_batched, eps_spheres, gram, gram_pair, init_block, lib,
-                 rayleigh_ritz, residual)
+                 rayleigh_ritz, residual, stencil_coefficients)
 
 __all__ = ["PCError", "Solver", "block_update", "eigh_batched", "eps_spheres", "gram", "gram_pair", "init_block",
-           "lib", "rayleigh_ritz", "residual"]
+           "lib", "rayleigh_ritz", "residual", "stencil_coefficients"]

@@ -116,6 +116,7 @@ struct pc_ctx {
   cudaStream_t stream = nullptr;
   pc::DevBuf m0d, m0f;      // M0 diagonal, double and float copies, [3][N^3]
   pc::DevBuf m0p;           // M0 diagonal as double-float pairs (hi, lo) float2 [3][N^3]
+  pc::DevBuf kscratch;      // higher-order stencils: e = M0 A' v (3 fields) and c = B v (1 field) per column
   pc::DevBuf twd, twf;      // FFT twiddles exp(-2 pi i t / N), t < N/2
   pc::DevBuf kparam;        // KParam [nb]
   pc::DevBuf symd;          // per-k axis symbols d_i(m) complex128 [nb][3][N]
@@ -222,6 +223,14 @@ int launch_narrow(int nb, long L, int m, const void *X, long sx, void *Y, long s
 // Y (complex128) = X (double-float pairs, PC_DFS): m columns of length L per k-point
 int launch_pairs_to_c128(int nb, long L, int m, const void *X, long sx, void *Y, long sy, cudaStream_t st,
                          const int *act);
+// stencils of order k = 2..4 (stencil_k.cu): Table 1 coefficients (c_s, d_s, s <= 4, zero past k), Y = Op X in two
+// passes (complex128 or complex64), the half-apply (A' x, B x; complex128) and the Algorithm 4.1 partial sums
+void stencil_coefficients(int k, double *c, double *d);
+int launch_apply_op_k(pc_ctx *ctx, int nb, int m, int dtype, const void *X, long sx, void *Y, long sy,
+                      const int *act);
+int launch_half_k(pc_ctx *ctx, int nb, int m, const void *X, void *E, void *Cc);
+int launch_recompute_k_partial(pc_ctx *ctx, int nb, int m, const void *X, long sx, const int *act, int nchunk,
+                               long chunk, double *part, int dtype);
 // double-float (FP32-pair) versions of the FP64-accurate kernels of the mixed solve (mixed_df.cu). launch_apply_op_df
 // takes complex128 blocks; the others take and write blocks of double-float pairs (PC_DFS).
 int launch_apply_op_df(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act);

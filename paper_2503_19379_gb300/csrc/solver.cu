@@ -38,12 +38,22 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
   return e == cudaErrorMemoryAllocation ? PC_ENOMEM : PC_ECUDA;
 }
 
-// symbol of D_i on mode m (second order): i e^{i theta/2} ((2/h) sin(theta/2) + k_i cos(theta/2))
-static void axis_symbols(int N, double k_i, double2 *out) {
+// symbol of D_i on mode m for the 2k-th order stencil (Section 5.2, the diagonalisation of the difference and average
+// matrices by the FFT): d_i(m) = i e^{i th/2} (S_i(m) + k_i Z_i(m)), th = 2 pi m / N, with
+// S_i(m) = (2/h) sum_s c_s sin((s - 1/2) th) and Z_i(m) = 2 sum_s d_s cos((s - 1/2) th); for k = 1 (c_1 = 1,
+// d_1 = 1/2) this is i e^{i th/2} ((2/h) sin(th/2) + k_i cos(th/2))
+static void axis_symbols(int N, int order, double k_i, double2 *out) {
   const double h = 1.0 / N;
+  double c[4], d[4];
+  stencil_coefficients(order, c, d);
   for (int mm = 0; mm < N; ++mm) {
     const double th = 2.0 * M_PI * mm / N;
-    const double mag = (2.0 / h) * std::sin(0.5 * th) + k_i * std::cos(0.5 * th);
+    double S = 0.0, Z = 0.0;
+    for (int q = 1; q <= order; ++q) {
+      S += c[q - 1] * std::sin((q - 0.5) * th);
+      Z += d[q - 1] * std::cos((q - 0.5) * th);
+    }
+    const double mag = (2.0 / h) * S + k_i * (2.0 * Z);
     // i e^{i th/2} = -sin(th/2) + i cos(th/2)
     out[mm].x = -std::sin(0.5 * th) * mag;
     out[mm].y = std::cos(0.5 * th) * mag;
@@ -82,7 +92,8 @@ int upload_kpoints(pc_ctx *ctx, int nb, const double *kpts, const double *gammas
     kp[b].gammaf = (float)gammas[b];
     kp[b].gammal = (float)(gammas[b] - (double)kp[b].gammaf);
     kp[b].pfacf = (float)((gammas[b] - 1.0) / gammas[b]);
-    for (int d = 0; d < 3; ++d) axis_symbols(ctx->N, kpts[3 * b + d], &sym[((size_t)b * 3 + d) * ctx->N]);
+    for (int d = 0; d < 3; ++d)
+      axis_symbols(ctx->N, ctx->opts.order, kpts[3 * b + d], &sym[((size_t)b * 3 + d) * ctx->N]);
   }
   PC_CK(cudaMemcpyAsync(ctx->kparam.p, kp.data(), sizeof(KParam) * nb, cudaMemcpyHostToDevice, ctx->stream));
   PC_CK(cudaMemcpyAsync(ctx->symd.p, sym.data(), sizeof(double2) * sym.size(), cudaMemcpyHostToDevice, ctx->stream));
@@ -180,8 +191,12 @@ extern "C" int pc_setup(pc_ctx **out, int N, const double *eps_edges, const doub
   pc_opts o;
   pc_opts_default(&o);
   if (opts) o = *opts;
-  if (o.order != 1) {
-    set_error("pc_setup: only the second-order stencils (order 1) are implemented on the GPU");
+  if (o.order < 1 || o.order > 4) {
+    set_error("pc_setup: stencil order %d: Table 1 orders 1..4 (2nd to 8th order) are implemented", o.order);
+    return PC_EUNSUPPORTED;
+  }
+  if (o.order > 1 && o.precision == PC_PREC_MIXED) {
+    set_error("pc_setup: the mixed-precision solve implements the second-order stencils (order 1) only");
     return PC_EUNSUPPORTED;
   }
   PC_REQUIRE(o.precond == PC_PRECOND_GAMMA || o.precond == PC_PRECOND_LAPLACIAN, "pc_setup: bad precond");

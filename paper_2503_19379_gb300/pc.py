@@ -52,6 +52,7 @@ SIGNATURES = {
     "pc_apply_op": (_i, [_vp, _i, _dp, _dp, _i, _i, _vp, _vp]),
     "pc_apply_half": (_i, [_vp, _i, _dp, _i, _vp, _vp, _vp]),
     "pc_recompute_norms": (_i, [_vp, _i, _dp, _i, _vp, _vp]),
+    "pc_stencil_coefficients": (_i, [_i, _dp, _dp]),
     "pc_apply_precond": (_i, [_vp, _i, _dp, _dp, _i, _i, _vp, _vp]),
     "pc_gram": (_i, [_i, _l, _i, _i, _i, _vp, _l, _vp, _l, _vp, _vp]),
     "pc_gram_pair": (_i, [_i, _l, _i, _i, _vp, _l, _vp, _vp, _vp, _vp]),
@@ -129,6 +130,14 @@ def default_opts(**kw) -> Opts:
     for k, v in kw.items():
         setattr(o, k, v)
     return o
+
+
+def stencil_coefficients(order: int):
+    """Table 1 weights (c, d) of the 2k-th order scheme, k = order (pc_stencil_coefficients; host only)."""
+    c = np.zeros(4)
+    d = np.zeros(4)
+    _check(lib().pc_stencil_coefficients(int(order), _dptr(c), _dptr(d)), "pc_stencil_coefficients")
+    return c[:order].copy(), d[:order].copy()
 
 
 def eps_spheres(N: int, spheres, eps_bg: float) -> np.ndarray:

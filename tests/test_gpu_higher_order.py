@@ -1,0 +1,151 @@
+"""Higher-order stencils (Table 1, k = 2, 3, 4: fourth, sixth and eighth order) through the C ABI against the
+oracle's operators of the same order: the operator, the half-apply and the Algorithm 4.1 norms, the preconditioner
+(whose symbol tables carry the order), and FP64 solves against the closed-form homogeneous spectrum and a dense
+LAPACK solve. The mixed-precision solve is second order only and must refuse a higher order."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import workloads as wl  # noqa: E402
+from oracle import eigs, geometry, mfd, precond, spectrum  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def pcmod():
+    from paper_2503_19379_gb300 import build as b
+    b.build()
+    import paper_2503_19379_gb300 as p
+    return p
+
+
+def make_solver(pcmod, N, structure=None, **opts):
+    s = structure or wl.sc_single_sphere()
+    eps = geometry.eps_edges(N, s.as_array(), s.eps_bg)
+    return pcmod.Solver(N, eps, **opts), 1.0 / eps
+
+
+def rand_block(seed, shape):
+    g = np.random.default_rng(seed)
+    return g.standard_normal(shape) + 1j * g.standard_normal(shape)
+
+
+def to_dev(a, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+@pytest.mark.parametrize("korder,N", [(2, 8), (3, 8), (4, 8), (2, 16), (4, 16)])
+def test_apply_op_order_k_fp64(pcmod, korder, N):
+    S, m0 = make_solver(pcmod, N, order=korder)
+    g = np.random.default_rng(10 * korder + N)
+    nb, m = 2, 2
+    kpts = g.uniform(-3.5, 3.5, (nb, 3))
+    gammas = g.uniform(1.0, 2.0 * N, nb)
+    X = rand_block(N + korder, (nb, m, 3 * N ** 3))
+    Y = S.apply_op(kpts, gammas, to_dev(X.reshape(nb, m, 3, N, N, N))).cpu().numpy().reshape(nb, m, -1)
+    for b in range(nb):
+        Op = mfd.compensated_operator(N, kpts[b], 1.0 / N, m0, gammas[b], korder)
+        ref = (Op @ X[b].T).T
+        assert np.max(np.abs(Y[b] - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("korder", [2, 4])
+def test_apply_op_order_k_fp32(pcmod, korder):
+    N = 16
+    S, m0 = make_solver(pcmod, N, order=korder)
+    kpts = np.array([[0.4, -1.3, 2.2], [0.0, 0.0, 0.0]])
+    gammas = np.array([2.0 * N, 5.0])
+    X = rand_block(7 + korder, (2, 2, 3 * N ** 3)).astype(np.complex64)
+    Y = S.apply_op(kpts, gammas, to_dev(X.reshape(2, 2, 3, N, N, N), torch.complex64)).cpu().numpy()
+    Y = Y.reshape(2, 2, -1)
+    for b in range(2):
+        ref = (mfd.compensated_operator(N, kpts[b], 1.0 / N, m0, gammas[b], korder) @ X[b].astype(np.complex128).T).T
+        assert np.max(np.abs(Y[b] - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("korder", [2, 3, 4])
+def test_apply_half_and_recompute_norms_order_k(pcmod, korder):
+    N = 8
+    S, m0 = make_solver(pcmod, N, order=korder)
+    kpts = np.array([[0.3, 0.9, -1.7], [2.0, 0.0, 0.5]])
+    X = rand_block(3 + korder, (2, 2, 3 * N ** 3))
+    E, Cc = S.apply_half(kpts, to_dev(X.reshape(2, 2, 3, N, N, N)))
+    E = E.cpu().numpy().reshape(2, 2, -1)
+    Cc = Cc.cpu().numpy().reshape(2, 2, -1)
+    nrm = S.recompute_norms(kpts, to_dev(X.reshape(2, 2, 3, N, N, N))).cpu().numpy()
+    for b in range(2):
+        Ah, B = mfd.half_operators(N, kpts[b], 1.0 / N, korder)
+        Eref = (Ah @ X[b].T).T
+        Cref = (B @ X[b].T).T
+        assert np.max(np.abs(E[b] - Eref)) <= 1e-13 * np.max(np.abs(Eref))
+        assert np.max(np.abs(Cc[b] - Cref)) <= 1e-13 * np.max(np.abs(Cref))
+        ref = np.stack([np.sum(m0.ravel()[None, :] * np.abs(Eref) ** 2, 1), np.sum(np.abs(Cref) ** 2, 1),
+                        np.sum(np.abs(X[b]) ** 2, 1)], 1)
+        assert np.allclose(nrm[b], ref, rtol=1e-12)
+
+
+@pytest.mark.parametrize("korder,variant", [(2, 0), (4, 0), (3, 1)])
+def test_apply_precond_order_k_fp64(pcmod, korder, variant):
+    N = 16
+    S, _ = make_solver(pcmod, N, precond=variant, order=korder)
+    g = np.random.default_rng(200 + korder)
+    kpts = np.vstack([g.uniform(-3, 3, (2, 3)), np.zeros((1, 3))])
+    gammas = np.array([2.0 * N, 7.0, 2.0 * N])
+    R = rand_block(N + korder, (3, 2, 3 * N ** 3))
+    W = S.apply_precond(kpts, gammas, to_dev(R.reshape(3, 2, 3, N, N, N))).cpu().numpy().reshape(3, 2, -1)
+    name = "laplacian" if variant else "gamma"
+    for b in range(3):
+        for j in range(2):
+            ref = precond.apply_preconditioner(R[b, j], N, 1.0 / N, kpts[b], gammas[b], korder, name).ravel()
+            assert np.max(np.abs(W[b, j] - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("korder", [2, 4])
+def test_precond_inverts_operator_order_k(pcmod, korder):
+    """At eps = 1 the preconditioner of order k is the exact inverse of the operator of order k (complex128 and
+    complex64 paths): pins the order of the FFT symbols against the order of the stencil, independently of the
+    oracle."""
+    N = 16
+    S, _ = make_solver(pcmod, N, structure=wl.homogeneous(1.0), order=korder)
+    kpts = np.array([[0.5, 1.5, -2.5]])
+    X = rand_block(9 + korder, (1, 2, 3, N, N, N))
+    Z = S.apply_precond(kpts, [32.0], S.apply_op(kpts, [32.0], to_dev(X))).cpu().numpy()
+    assert np.max(np.abs(Z - X)) <= 1e-11 * np.max(np.abs(X))
+    X32 = to_dev(X, torch.complex64)
+    Z32 = S.apply_precond(kpts, [32.0], S.apply_op(kpts, [32.0], X32)).cpu().numpy()
+    assert np.max(np.abs(Z32 - X)) <= 1e-4 * np.max(np.abs(X))
+
+
+@pytest.mark.parametrize("korder", [2, 4])
+def test_solve_homogeneous_closed_form_order_k(pcmod, korder):
+    """eps = 1 at N = 8 with the 2k-th order stencils: the lowest eigenvalues equal the closed-form spectrum of the
+    same order (fixed gamma = 100 keeps the compensation values above the 8th band)."""
+    N = 8
+    S, _ = make_solver(pcmod, N, structure=wl.homogeneous(1.0), gamma_override=100.0, order=korder)
+    k = np.array([0.3, -0.7, 1.1])
+    out = S.solve(k[None], 8, 1e-10)
+    ref = spectrum.homogeneous_spectrum(N, 1.0 / N, k, 1.0, 100.0, korder)[:8]
+    assert out["status"] == 0
+    assert np.max(np.abs(out["evals"][0] - ref) / ref) <= 1e-10
+
+
+def test_solve_sphere_order2_matches_dense(pcmod):
+    """SC sphere (eps = 13) at N = 8, fourth-order stencils: 6 bands against LAPACK on the oracle's operator. gamma is
+    fixed at 100 on both sides so that the compensated gradient modes (gamma |k|^2 = 84 for the mean mode) lie above
+    the 6 bands: with the penalty of eq. pnt_number (gamma = 16) the mean mode's 13.44 sits among them, LAPACK
+    returns it and the solver's Algorithm 4.1 rightly removes it."""
+    N = 8
+    S, m0 = make_solver(pcmod, N, order=2, gamma_override=100.0)
+    k = np.array([0.4, 0.8, -0.2])
+    out = S.solve(k[None], 6, 1e-10)
+    assert out["status"] == 0
+    h = 1.0 / N
+    Op = mfd.compensated_operator(N, k, h, m0, 100.0, 2)
+    ref, _ = eigs.lowest_dense(Op, 6)
+    assert np.max(np.abs(out["evals"][0] - ref) / ref) <= 1e-10
+
+
+def test_mixed_solve_refuses_higher_order(pcmod):
+    with pytest.raises(pcmod.PCError):
+        make_solver(pcmod, 8, precision=1, order=2)

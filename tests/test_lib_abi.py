@@ -66,3 +66,29 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(pc, "LIBPATH", str(tmp_path / "nope.so"))
     with pytest.raises(pc.PCError):
         pc.lib()
+
+
+@pytest.mark.parametrize("korder", [1, 2, 3, 4])
+def test_stencil_coefficients_match_table1(libpath, korder):
+    """pc_stencil_coefficients (the closed-form weights the CUDA path uses) equals the oracle's Table 1 exactly, and
+    satisfies the 2k-th order moment conditions: sum c_s (2s-1)^(2p+1) = [p = 0], sum d_s (2s-1)^(2p) = [p = 0] / 2
+    for p < k. Host only."""
+    import numpy as np
+
+    from oracle import mfd
+    from paper_2503_19379_gb300 import pc
+    c, d = pc.stencil_coefficients(korder)
+    tc, td = mfd.TABLE1[korder]
+    assert np.array_equal(c, np.asarray(tc, dtype=np.float64))
+    assert np.array_equal(d, np.asarray(td, dtype=np.float64))
+    o = 2.0 * np.arange(1, korder + 1) - 1.0
+    for p in range(korder):
+        assert abs(np.sum(c * o ** (2 * p + 1)) - (1.0 if p == 0 else 0.0)) <= 1e-12
+        assert abs(np.sum(d * o ** (2 * p)) - (0.5 if p == 0 else 0.0)) <= 1e-12
+
+
+def test_stencil_coefficients_reject_other_orders(libpath):
+    from paper_2503_19379_gb300 import pc
+    for bad in (0, 5):
+        with pytest.raises(pc.PCError):
+            pc.stencil_coefficients(bad)
