@@ -228,7 +228,7 @@ def kernel_case(args):
     nb, m, N = 16, 16, w.N
     kp = w.kpts[:nb]
     gam = np.full(nb, 2.0 * N)
-    dt = torch.complex64 if args.kernel_case.endswith("32") else torch.complex128
+    dt = torch.complex64 if args.kernel_case.endswith(("32", "32c")) else torch.complex128
     g = torch.Generator(device="cuda").manual_seed(0)
     X = torch.randn((nb, m, 3, N, N, N), dtype=dt, device="cuda", generator=g)
     L = 3 * N ** 3
@@ -256,6 +256,12 @@ def kernel_case(args):
         s4 = pc.Solver(w.N, eps, precision=pc.pc.PC_PREC_MIXED)
         k4 = w.kpts[[3, 13, 23, 33]]
         run = lambda: s4.solve(k4, w.nbands, w.tol)
+    elif args.kernel_case == "gram32c":
+        # the solver's pencil with its coupling block: [X W P] (48 columns), its image, and R (16 columns)
+        S = X.reshape(nb, m, L)
+        SS = torch.cat([S, S, S], 1).contiguous()
+        R = S.clone()
+        run = lambda: pc.gram_pair_coupled(SS, SS, R)
     elif args.kernel_case.startswith("gram"):
         S = X.reshape(nb, m, L)
         AS = S.clone()
@@ -298,7 +304,7 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=12)
     ap.add_argument("--kernel-case", default=None,
                     choices=["stencil64", "stencil32", "stencil_df", "precond64", "precond32", "gram64", "gram32",
-                             "rr", "solve4"],
+                             "gram32c", "rr", "solve4"],
                     help="run one hot kernel alone on a small batch (profiling) instead of the benchmark")
     args = ap.parse_args()
     if args.kernel_case:

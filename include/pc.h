@@ -195,6 +195,14 @@ int pc_gram(int nb, long L, int p, int q, int dtype, const void *A, long sa, con
 int pc_gram_pair(int nb, long L, int p, int dtype, const void *S, long ss, const void *AS, void *G, void *H,
                  void *stream);
 
+/* a3 with the mixed solve's coupling block: G_b = S_b^H S_b, H_b = S_b^H AS_b (as pc_gram_pair) and
+ * RQ_b = R_b^H S_b (q x p, complex128 [nb][q][p]) from one pass over S, AS and R (complex64 only; R_b of q columns,
+ * batch stride sr). The coupling X^H Op Q = Theta X^H Q + R^H Q of Section 5.1's LOBPCG takes R^H Q from RQ.
+ * p, q <= 64; on the tensor cores when 2 round8(p) + round8(q) <= 128 (rounded to 16), else as pc_gram_pair plus
+ * pc_gram. Synchronous. */
+int pc_gram_pair_coupled(int nb, long L, int p, int q, const void *S, long ss, const void *AS, const void *R, long sr,
+                         void *G, void *H, void *RQ, void *stream);
+
 /* pc_gram_pair_noalloc -- the same products as pc_gram_pair, for callers that cannot allocate device memory:
  * code that runs under a fixed device-memory budget, inside an application whose own allocator must own every
  * allocation, or in latency-critical loops where cudaMalloc/cudaFree would synchronise the device. It calls no

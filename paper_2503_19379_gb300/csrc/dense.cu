@@ -362,6 +362,25 @@ int launch_gram_pair(int nb, long L, int p, int dtype, const void *S, const void
   return PC_OK;
 }
 
+size_t gram_pair_coupled_scratch_bytes(int nb, long L, int p, int q2) {
+  return std::max({sizeof(double2) * (size_t)nb * gram_chunks(nb, L) * p * (2 * p + q2),
+                   gram_pair_scratch_bytes(nb, L, p), gram_scratch_bytes(nb, L, q2, p)});
+}
+
+int launch_gram_pair_coupled(int nb, long L, int p, int q2, int dtype, const void *S, const void *AS, long ss,
+                             const void *R, long sr, void *G, void *H, void *RQ, void *scratch, size_t scratch_bytes,
+                             cudaStream_t st, const int *act, int nb_alloc, long sg, long srq) {
+  if (nb == 0 || p == 0) return PC_OK;
+  if (dtype == PC_C64) {
+    const int rc = launch_gram_pair_coupled_tc(nb, L, p, q2, S, AS, ss, R, sr, G, H, RQ, scratch, scratch_bytes, st,
+                                               act, nb_alloc, sg, srq);
+    if (rc != PC_EUNSUPPORTED) return rc;
+  }
+  int rc = launch_gram_pair(nb, L, p, dtype, S, AS, ss, G, H, scratch, scratch_bytes, st, act, nb_alloc, sg);
+  if (rc) return rc;
+  return launch_gram(nb, L, q2, p, dtype, R, sr, S, ss, RQ, scratch, scratch_bytes, st, act, nb_alloc, srq);
+}
+
 // ------------------------------------------------------------------------------------------------ block update
 // Y_b[:, j] = sum_i S_b[:, i] C_b[i, j] (+ Z_b[:, j] when Z is given); grid (ceil(L/256), ceil(q/16), nb); one row
 // per thread, 16 outputs. Products and sums run in the precision T of S and Y; Z is a complex64 addend (the
@@ -886,6 +905,19 @@ extern "C" int pc_gram_pair(int nb, long L, int p, int dtype, const void *S, lon
   int rc = launch_gram_pair(nb, L, p, dtype, S, AS, ss, G, H, tmp.p, tmp.bytes, (cudaStream_t)stream, nullptr);
   if (rc) return rc;
   PC_CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return PC_OK;
+}
+
+extern "C" int pc_gram_pair_coupled(int nb, long L, int p, int q, const void *S, long ss, const void *AS,
+                                    const void *R, long sr, void *G, void *H, void *RQ, void *stream) {
+  PC_REQUIRE(S && AS && R && G && H && RQ, "pc_gram_pair_coupled: null argument");
+  PC_REQUIRE(nb >= 0 && L >= 0 && p >= 1 && p <= 64 && q >= 1 && q <= 64, "pc_gram_pair_coupled: bad sizes");
+  DevBuf tmp;
+  PC_CK(tmp.reserve(std::max<size_t>(16, gram_pair_coupled_scratch_bytes(nb, L, p, q))));
+  int rc = launch_gram_pair_coupled(nb, L, p, q, PC_C64, S, AS, ss, R, sr, G, H, RQ, tmp.p, tmp.bytes,
+                                    (cudaStream_t)stream, nullptr);
+  if (rc) return rc;
+  PC_CK(cudaStreamSynchronize((cudaStream_t)stream));  // tmp is released on return
   return PC_OK;
 }
 

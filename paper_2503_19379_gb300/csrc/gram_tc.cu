@@ -160,6 +160,9 @@ struct TcArgs {
   long L;
   int p, q;             // columns of A and of B1
   int PB, QB;           // padded row counts (multiples of 8); the B operand is rows [0, N) of the operand region
+  int RB, q2;           // pair mode with a coupling block: B1 = [B1a (QB - RB rows); R (RB rows, q2 used)], the
+                        // second part from its own tensor (RB = 0: none)
+  long cppR;            // columns per k-point panel of R
   int N;                // MMA N: QB + PB when pair (B = [B1; A]), else QB (multiple of 16, <= 128)
   int pair;             // pair: outputs G = A^H A and H = A^H B1 (upper triangles); else A^H B1 (p x q)
   int transpose;        // general mode: write the conjugate transpose (B1^H A, q x p) instead
@@ -169,11 +172,13 @@ struct TcArgs {
   uint32_t tmem_cols;    // allocated TMEM columns (4 nc rounded up to a power of two)
   uint32_t idesc;
   double *partG, *partH;  // pair: [nb][nchunk][p][p] double2 each; general: partH = [nb][nchunk][p][q]
+  double *partQ;          // coupling block (RB > 0): R^H A as [nb][nchunk][q2][p] double2
   const int *act;
 };
 
 __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tmA,
-                                                                const __grid_constant__ CUtensorMap tmB) {
+                                                                const __grid_constant__ CUtensorMap tmB,
+                                                                const __grid_constant__ CUtensorMap tmR) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_addr(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -239,12 +244,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a, 
     // whole boxes, TC_SPT tiles per stage (rows or tiles past the tensor are zero-filled; a last stage's second tile
     // past the chunk is loaded and not used)
     const uint32_t tx = stage_bytes;
-    const int yA = (int)(b * a.cppA), yB = (int)(b * a.cppB);
+    const int yA = (int)(b * a.cppA), yB = (int)(b * a.cppB), yR = (int)(b * a.cppR);
     const int nstage = (ntile + TC_SPT - 1) / TC_SPT;
     int issued = 0;
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      if (a.RB > 0) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmR)) : "memory");
       for (int q = 0; q < nstage; ++q) {
         const int s = q % ns;
         if (!bar_wait(bar_empty + 8u * s, ((q / ns) & 1) ^ 1, abort)) break;
@@ -255,6 +261,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a, 
           const int x = (t_begin + q * TC_SPT + h) * TC_KT;  // float offset: a multiple of 32 (128 bytes)
           tma_load_2d(st + h * tile_bytes, &tmA, x, yA, bar_full + 8u * s);
           tma_load_2d(st + h * tile_bytes + (uint32_t)a.PB * 128u, &tmB, x, yB, bar_full + 8u * s);
+          if (a.RB > 0)
+            tma_load_2d(st + h * tile_bytes + (uint32_t)(a.PB + a.QB - a.RB) * 128u, &tmR, x, yR, bar_full + 8u * s);
         }
         issued = q + 1;
       }
@@ -397,6 +405,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a, 
             const int j = c0 + k;
             const double val = (double)acc[h][k];
             if (a.pair) {
+              const int QA = a.QB - a.RB;  // rows of B1a
+              if (j >= QA && j < a.QB) {
+                // coupling block: (A^H R)_{ii, jq}, stored conjugate-transposed as (R^H A)_{jq, ii}
+                const int jq = j - QA;
+                if (jq < a.q2) {
+                  const long oQ = ((long)bi * a.nchunk + chunk) * a.q2 * a.p;
+                  a.partQ[2 * (oQ + (long)jq * a.p + ii) + im] = im ? -val : val;
+                }
+                continue;
+              }
               const bool isH = j < a.QB;
               const int jj = isH ? j : j - a.QB;
               if (j < a.N && jj < a.p && ii <= jj)
@@ -482,18 +500,24 @@ bool make_map(CUtensorMap *map, const void *base, long L, long rows, int box_row
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// pair mode with R (q2 > 0): B1 = [B; R], the coupling block R^H A written to partQ (after the G and H partials)
 int launch_tc(int nb, int nb_alloc, long L, int p, int q, bool pair, const void *A, long sa, const void *B, long sb,
               double2 *part, size_t scratch_bytes, cudaStream_t st, const int *act, int *nchunk_out,
-              bool transpose = false) {
+              bool transpose = false, const void *R = nullptr, long sr = 0, int q2 = 0) {
   TcArgs a{};
   a.cppA = sa / L;
   a.cppB = sb / L;
+  a.cppR = q2 > 0 ? sr / L : 0;
   a.L = L;
   a.p = p;
   a.q = q;
+  a.q2 = pair ? q2 : 0;
   a.PB = (p + 7) / 8 * 8;
-  a.QB = pair ? a.PB : (q + 15) / 16 * 16;
+  a.RB = a.q2 > 0 ? (a.q2 + 7) / 8 * 8 : 0;
+  if (a.RB > 0 && (2 * a.PB + a.RB) % 16 != 0) a.RB += 8;  // the MMA's N must be a multiple of 16
+  a.QB = pair ? a.PB + a.RB : (q + 15) / 16 * 16;
   a.N = pair ? a.QB + a.PB : a.QB;
+  if (a.N > 128) return PC_EUNSUPPORTED;
   a.pair = pair ? 1 : 0;
   a.transpose = transpose ? 1 : 0;
   a.ktiles = (int)(2 * L / TC_KT);
@@ -501,7 +525,7 @@ int launch_tc(int nb, int nb_alloc, long L, int p, int q, bool pair, const void 
   while (ns > 2 && tc_smem(a.PB, a.QB, ns) > (size_t)TC_SMEM_MAX) --ns;
   if (tc_smem(a.PB, a.QB, ns) > (size_t)TC_SMEM_MAX) return PC_EUNSUPPORTED;
   a.ns = ns;
-  const size_t per_chunk = (pair ? 2 : 1) * sizeof(double2) * (size_t)nb * p * (pair ? p : q);
+  const size_t per_chunk = sizeof(double2) * (size_t)nb * p * (pair ? 2 * p + a.q2 : q);
   const long maxc = (long)std::min<size_t>(scratch_bytes / per_chunk, 4096);
   if (maxc < 1) return PC_EUNSUPPORTED;
   int c = tc_chunks(nb, a.ktiles, maxc);
@@ -516,6 +540,7 @@ int launch_tc(int nb, int nb_alloc, long L, int p, int q, bool pair, const void 
   while (a.tmem_cols < (uint32_t)(4 * a.nc)) a.tmem_cols *= 2;
   a.partG = reinterpret_cast<double *>(part);
   a.partH = pair ? reinterpret_cast<double *>(part + (size_t)nb * c * p * p) : reinterpret_cast<double *>(part);
+  a.partQ = a.q2 > 0 ? reinterpret_cast<double *>(part + 2 * (size_t)nb * c * p * p) : nullptr;
   a.act = act;
   static bool configured = false;
   if (!configured) {
@@ -525,11 +550,17 @@ int launch_tc(int nb, int nb_alloc, long L, int p, int q, bool pair, const void 
   // a CTA that takes all 512 TMEM columns must have its SM to itself: ask for more than half the shared memory
   size_t smem = tc_smem(a.PB, a.QB, ns);
   if (a.tmem_cols == 512) smem = std::max<size_t>(smem, TC_SMEM_MAX / 2 + 4096);
-  CUtensorMap tmA, tmB;
+  CUtensorMap tmA, tmB, tmR;
+  const int brows = a.QB - a.RB;  // rows of the B tile
   if (!make_map(&tmA, A, L, (long)(nb_alloc - 1) * a.cppA + p, a.PB) ||
-      !make_map(&tmB, B, L, (long)(nb_alloc - 1) * a.cppB + q, a.QB))
+      !make_map(&tmB, B, L, (long)(nb_alloc - 1) * a.cppB + q, brows))
     return PC_EUNSUPPORTED;
-  gram_tc_kernel<<<dim3(c, nb), TC_THREADS, smem, st>>>(a, tmA, tmB);
+  if (a.RB > 0) {
+    if (!make_map(&tmR, R, L, (long)(nb_alloc - 1) * a.cppR + a.q2, a.RB)) return PC_EUNSUPPORTED;
+  } else {
+    tmR = tmB;  // not read
+  }
+  gram_tc_kernel<<<dim3(c, nb), TC_THREADS, smem, st>>>(a, tmA, tmB, tmR);
   PC_CK_LAUNCH();
   *nchunk_out = c;
   return PC_OK;
@@ -566,6 +597,25 @@ int launch_gram_pair_tc(int nb, long L, int p, const void *S, const void *AS, lo
                      &c);
   if (rc) return rc;
   launch_gram_pair_reduce(nb, c, p, part, act, G, H, st, sg);
+  PC_CK_LAUNCH();
+  return PC_OK;
+}
+
+// G = S^H S, H = S^H AS and RQ = R^H S (q2 x p, row stride p) in one pass over [S | AS | R] (complex64, 2 p + q2
+// rounded up <= 128 MMA columns); PC_EUNSUPPORTED as above.
+int launch_gram_pair_coupled_tc(int nb, long L, int p, int q2, const void *S, const void *AS, long ss, const void *R,
+                                long sr, void *G, void *H, void *RQ, void *scratch, size_t scratch_bytes,
+                                cudaStream_t st, const int *act, int nb_alloc, long sg, long srq) {
+  if (q2 < 1 || !tc_shape_ok(L, p, p, S, ss, AS, ss) || !tc_shape_ok(L, q2, q2, R, sr, R, sr))
+    return PC_EUNSUPPORTED;
+  int c = 0;
+  double2 *part = static_cast<double2 *>(scratch);
+  int rc = launch_tc(nb, nb_alloc > 0 ? nb_alloc : nb, L, p, p, true, S, ss, AS, ss, part, scratch_bytes, st, act,
+                     &c, false, R, sr, q2);
+  if (rc) return rc;
+  launch_gram_pair_reduce(nb, c, p, part, act, G, H, st, sg);
+  PC_CK_LAUNCH();
+  launch_gram_reduce(nb, c, q2, p, part + 2 * (size_t)nb * c * p * p, act, RQ, st, srq);
   PC_CK_LAUNCH();
   return PC_OK;
 }

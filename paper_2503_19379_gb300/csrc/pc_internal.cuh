@@ -189,6 +189,15 @@ void launch_gram_reduce(int nb, int nchunk, int p, int q, const double2 *part, c
 // complex64 Gram products on the tensor cores (gram_tc.cu); PC_EUNSUPPORTED when the shape does not fit
 int launch_gram_pair_tc(int nb, long L, int p, const void *S, const void *AS, long ss, void *G, void *H,
                         void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc, long sg);
+int launch_gram_pair_coupled_tc(int nb, long L, int p, int q2, const void *S, const void *AS, long ss, const void *R,
+                                long sr, void *G, void *H, void *RQ, void *scratch, size_t scratch_bytes,
+                                cudaStream_t st, const int *act, int nb_alloc, long sg, long srq);
+// G = S^H S, H = S^H AS (p columns) and RQ = R^H S (q2 x p) for nb k-points; one tensor-core pass for complex64
+// where the shape allows, else launch_gram_pair and launch_gram
+int launch_gram_pair_coupled(int nb, long L, int p, int q2, int dtype, const void *S, const void *AS, long ss,
+                             const void *R, long sr, void *G, void *H, void *RQ, void *scratch, size_t scratch_bytes,
+                             cudaStream_t st, const int *act, int nb_alloc = -1, long sg = 0, long srq = 0);
+size_t gram_pair_coupled_scratch_bytes(int nb, long L, int p, int q2);
 int launch_gram_tc(int nb, long L, int p, int q, const void *A, long sa, const void *B, long sb, void *G,
                    void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc, long sg);
 // reads and clears the time-out flag of the tensor-core Gram kernel (call after a synchronisation)

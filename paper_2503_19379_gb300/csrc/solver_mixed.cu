@@ -363,16 +363,13 @@ class MixedSolve {
     }));
     RUN(DEFL(g.act, S.F[cur] + (long)m * L, sF, PC_C64));
     RUN(OP32(na, m, S.F[cur] + (long)m * L, sF, S.AF[cur] + (long)m * L, sF));
-    // ---- pencil: complex64 products over [X | W | P], the R^H Q coupling, FP64 X-X block in phase 2
-    RUN(run_stage(ctx, PC_STAGE_GRAM, 2, 8.0 * nc * (nc + 1) * S.Ld * na, 2.0 * nc * S.Ld * 8.0 * na, [&] {
-      return launch_gram_pair(na, L, nc, PC_C64, S.F[cur], S.AF[cur], sF, S.Gm, S.Hm, g.scratch, S.scr, g.st, g.d_act,
-                              nb, S.sG);
-    }));
-    // R^H [X | Q]: the coupling R^H Q of H, and R^H X for the X-X block in phase 2
-    RUN(run_stage(ctx, PC_STAGE_GRAM, 2, 8.0 * m * nc * S.Ld * na, (double)(m + nc) * S.Ld * 8.0 * na, [&] {
-      return launch_gram(na, L, m, nc, PC_C64, S.R32, sX, S.F[cur], sF, S.RQ, g.scratch, S.scr, g.st, g.d_act, nb,
-                         S.sRS);
-    }));
+    // ---- pencil: complex64 products over [X | W | P] and, in the same pass, R^H [X | Q] (the coupling R^H Q of H,
+    // and R^H X for the X-X block in phase 2); FP64 X-X block in phase 2
+    RUN(run_stage(ctx, PC_STAGE_GRAM, 3, 8.0 * (nc * (nc + 1) + m * nc) * S.Ld * na,
+                  (2.0 * nc + m) * S.Ld * 8.0 * na, [&] {
+                    return launch_gram_pair_coupled(na, L, nc, m, PC_C64, S.F[cur], S.AF[cur], sF, S.R32, sX, S.Gm,
+                                                    S.Hm, S.RQ, g.scratch, S.scr, g.st, g.d_act, nb, S.sG, S.sRS);
+                  }));
     act1.clear();
     act2.clear();
     for (int b : g.act) (S.phase[b] == 1 ? act1 : act2).push_back(b);
@@ -460,7 +457,8 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
   // the chunked reductions' partial sums depend on the active count (not monotonically): size for every count
   size_t scr = 16;
   for (int na = 1; na <= gmax; ++na)
-    scr = std::max({scr, gram_pair_scratch_bytes(na, L, nmax), gram_df_scratch_bytes(na, L, m),
+    scr = std::max({scr, gram_pair_scratch_bytes(na, L, nmax), gram_pair_coupled_scratch_bytes(na, L, nmax, m),
+                    gram_df_scratch_bytes(na, L, m),
                     gram_scratch_bytes(na, L, m, nmax), residual_scratch_bytes(na, L, m),
                     recompute_scratch_bytes(n, na, m), op_df_resid_scratch_bytes(ctx, na, m),
                     sizeof(double2) * (size_t)na * 3 * m * 16});

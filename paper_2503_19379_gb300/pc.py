@@ -57,6 +57,7 @@ SIGNATURES = {
     "pc_gram": (_i, [_i, _l, _i, _i, _i, _vp, _l, _vp, _l, _vp, _vp]),
     "pc_gram_pair": (_i, [_i, _l, _i, _i, _vp, _l, _vp, _vp, _vp, _vp]),
     "pc_gram_pair_noalloc": (_i, [_i, _l, _i, _i, _vp, _l, _vp, _vp, _vp, _vp]),
+    "pc_gram_pair_coupled": (_i, [_i, _l, _i, _i, _vp, _l, _vp, _vp, _l, _vp, _vp, _vp, _vp]),
     "pc_block_update": (_i, [_i, _l, _i, _i, _i, _vp, _l, _vp, _vp, _l, _vp]),
     "pc_eigh_batched": (_i, [_i, _i, _vp, _vp, _vp, _vp]),
     "pc_rayleigh_ritz": (_i, [_i, _i, _i, _vp, _vp, _d, _vp, _vp, _vp, _vp]),
@@ -260,6 +261,21 @@ def gram(A, B, stream=None):
     _check(lib().pc_gram(nb, L, p, q, _dtype_code(A), _dev(A), p * L, _dev(B), q * L, _dev(G), _stream(stream)),
            "pc_gram")
     return G
+
+
+def gram_pair_coupled(S, AS, R, stream=None):
+    """(G, H, RQ) = (S^H S, S^H AS, R^H S) for complex64 panels S, AS (nb, p, L) and R (nb, q, L) in one pass
+    (pc_gram_pair_coupled)."""
+    torch = _torch()
+    nb, p, L = S.shape
+    q = R.shape[1]
+    G = torch.empty((nb, p, p), dtype=torch.complex128, device=S.device)
+    H = torch.empty_like(G)
+    RQ = torch.empty((nb, q, p), dtype=torch.complex128, device=S.device)
+    _check(lib().pc_gram_pair_coupled(nb, L, p, q, _dev(S, [torch.complex64]), p * L, _dev(AS, [torch.complex64]),
+                                      _dev(R, [torch.complex64]), q * L, _dev(G), _dev(H), _dev(RQ), _stream(stream)),
+           "pc_gram_pair_coupled")
+    return G, H, RQ
 
 
 def gram_pair(S, AS, stream=None):

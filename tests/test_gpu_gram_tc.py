@@ -77,3 +77,20 @@ def test_gram_pair_split_exposes_lo(pcmod):
         assert np.allclose(np.diag(H[b]).real, 3 * L * x2, rtol=2e-6, atol=0)
     check(G, S, S, rel=2e-6)
     check(H, S, AS, rel=2e-6)
+
+
+@pytest.mark.parametrize("nb,p,q,L", [(3, 48, 16, 3 * 32 ** 3), (2, 32, 16, 4096), (2, 40, 9, 3 * 16 ** 3),
+                                      (4, 8, 3, 512), (1, 64, 16, 2048)])
+def test_gram_pair_coupled_c64(pcmod, nb, p, q, L):
+    """G = S^H S, H = S^H AS and RQ = R^H S from one pass over [S | AS | R] (the mixed solve's pencil and coupling
+    block). The last case (2 p + q beyond 128 MMA columns) takes the separate pair and general products."""
+    S = rand_c64(p + 3 * q + L, (nb, p, L))
+    AS = (S * np.random.default_rng(L + 1).uniform(0.5, 4.0, L)[None, None, :]).astype(np.complex64)
+    R = rand_c64(q + 17, (nb, q, L))
+    G, H, RQ = pcmod.gram_pair_coupled(dev(S), dev(AS), dev(R))
+    G, H, RQ = G.cpu().numpy(), H.cpu().numpy(), RQ.cpu().numpy()
+    check(G, S, S)
+    check(H, S, AS)
+    check(RQ, R, S)
+    for b in range(nb):
+        assert np.array_equal(G[b], G[b].conj().T) and np.array_equal(H[b], H[b].conj().T)
