@@ -54,8 +54,9 @@ DF_OPS_PER_FLOP = 9.0
 # DRAM traffic per algorithmic byte of a stage's kernel, from an ncu capture of it on a smaller case (committed
 # summary named beside it); the bench scales it by the bytes of its own launches. Only for kernels unchanged since.
 MEASURED_TRAFFIC = {
-    "gram": (1.2177 / 1.2080, "profiles/gram_tc_kernel_pair48_16k_N32.md: dram__bytes_read + dram__bytes_write = "
-                              "1.2177 GB for 1.2080 GB algorithmic (16 k-points x 48 columns), scaled to the launch"),
+    "gram": (1.4211 / 1.4093, "profiles/gram_tc_kernel_coupled48x16_16k_N32.md: dram__bytes_read + "
+                              "dram__bytes_write = 1.4211 GB for 1.4093 GB algorithmic (16 k-points x (48 + 48 + 16) "
+                              "columns), scaled to the launch"),
 }
 
 
@@ -260,8 +261,9 @@ def kernel_case(args):
         # the solver's pencil with its coupling block: [X W P] (48 columns), its image, and R (16 columns)
         S = X.reshape(nb, m, L)
         SS = torch.cat([S, S, S], 1).contiguous()
+        ASS = torch.cat([S, S, S], 1).contiguous()  # its own buffer, as the operator image is in the solver
         R = S.clone()
-        run = lambda: pc.gram_pair_coupled(SS, SS, R)
+        run = lambda: pc.gram_pair_coupled(SS, ASS, R)
     elif args.kernel_case.startswith("gram"):
         S = X.reshape(nb, m, L)
         AS = S.clone()
