@@ -66,9 +66,14 @@ def stage_roofline(stage, d, precision, peaks, src):
     t = d["ms"] / calls / 1e3
     if precision == "fp64" or stage in ("rr", "recompute"):
         achieved = d["flops"] / calls / t / 1e12
-        return {"bound": "alu", "kernel": stage, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+        line = {"bound": "alu", "kernel": stage, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (FP64 CUDA cores)"}
+        if stage == "rr":
+            line["note"] = ("one CTA per pencil: a launch of a 10-k-point group occupies 10 of the 152 SMs, so the "
+                            "fraction of the occupied SMs' FP64 peak is 15.2x frac; the stage time is the interval "
+                            "on the group's stream while three other groups share the GPU")
+        return line
     if stage == "dfloat":
         achieved = d["flops"] / calls / t / 1e12
         peak = FP32_PEAK_TFLOPS / DF_OPS_PER_FLOP
