@@ -715,24 +715,6 @@ int launch_pairs_to_c128(int nb, long L, int m, const void *X, long sx, void *Y,
   return PC_OK;
 }
 
-// Y (complex64) = X (FP64) for m columns of length L per k-point.
-__global__ void narrow_kernel(const double2 *__restrict__ X, long sx, float2 *__restrict__ Y, long sy, long L,
-                              const int *__restrict__ act) {
-  const int b = act ? act[blockIdx.z] : (int)blockIdx.z, j = blockIdx.y;
-  const double2 *x = X + (long)b * sx + (long)j * L;
-  float2 *y = Y + (long)b * sy + (long)j * L;
-  for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < L; l += (long)gridDim.x * blockDim.x)
-    y[l] = make_float2((float)x[l].x, (float)x[l].y);
-}
-
-int launch_narrow(int nb, long L, int m, const void *X, long sx, void *Y, long sy, cudaStream_t st, const int *act) {
-  if (nb == 0 || m == 0) return PC_OK;
-  const unsigned gx = (unsigned)std::min<long>(256, (L + 255) / 256);
-  narrow_kernel<<<dim3(gx, m, nb), 256, 0, st>>>(static_cast<const double2 *>(X), sx, static_cast<float2 *>(Y), sy, L,
-                                                 act);
-  PC_CK_LAUNCH();
-  return PC_OK;
-}
 
 // ------------------------------------------------------------------------------------------------ k = 0 projection
 // Removes the mean of each component of each column for k-points with flags[b] != 0 (the constant kernel fields).

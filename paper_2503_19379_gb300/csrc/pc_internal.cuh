@@ -228,7 +228,6 @@ int launch_residual_mixed(int nb, long L, int m, int dtype_x, const void *X, lon
 int launch_rr_patch(int nb, int n, int m, void *G, void *H, const void *RS, const double *theta, const void *GX,
                     const int *phase, cudaStream_t st, const int *act, long sg = 0, long srs = 0);
 int launch_widen(int nb, long L, int m, const void *X, long sx, void *Y, long sy, cudaStream_t st, const int *act);
-int launch_narrow(int nb, long L, int m, const void *X, long sx, void *Y, long sy, cudaStream_t st, const int *act);
 // Y (complex128) = X (double-float pairs, PC_DFS): m columns of length L per k-point
 int launch_pairs_to_c128(int nb, long L, int m, const void *X, long sx, void *Y, long sy, cudaStream_t st,
                          const int *act);
