@@ -390,9 +390,10 @@ class MixedSolve {
     if (!act1.empty()) {
       RUN(set_act(act1));
       const int n1 = (int)act1.size();
-      RUN(run_stage(ctx, PC_STAGE_UPDATE, 1, 8.0 * nc * m * S.Ld * n1, (double)(nc + m) * S.Ld * 8.0 * n1, [&] {
-        return launch_block_update(n1, L, nc, m, PC_C64, S.F[cur], sF, S.coef, S.sC, S.F[nxt], sF, g.st,
-                                   g.d_act);
+      // X' = X C_X + P' (the P' just formed is [W P] C_{W,P}): reads 2m columns instead of the 3m of [X W P]
+      RUN(run_stage(ctx, PC_STAGE_UPDATE, 1, 8.0 * m * m * S.Ld * n1, 3.0 * m * S.Ld * 8.0 * n1, [&] {
+        return launch_block_update(n1, L, m, m, PC_C64, S.F[cur], sF, S.coef, S.sC, S.F[nxt], sF, g.st, g.d_act,
+                                   S.F[nxt] + 2L * m * L, sF);
       }));
       RUN(DEFL(act1, S.F[nxt], sF, PC_C64));
       RUN(OP32(n1, m, S.F[nxt], sF, S.AF[nxt], sF));
