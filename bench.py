@@ -423,6 +423,7 @@ def main():
                                     "10 bands, 40 k-points Gamma-X-W-K-Gamma-L, tol 1e-6, all k-points in one "
                                     "batched solve"),
                        "precision": args.precision, "nk_per_gpu": nk, "nbands": w.nbands, "tol": w.tol,
+                       "kpoint_groups": args.groups if args.groups > 0 else "library default (4 from 16 k-points)",
                        "mean_lobpcg_iterations": mean_iters, "max_lobpcg_iterations": max_iters,
                        "status": max(statuses),
                        "cache": "inputs larger than L2 (search blocks ~9 GB per GPU), no flush"},
