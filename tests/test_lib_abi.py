@@ -92,3 +92,15 @@ def test_stencil_coefficients_reject_other_orders(libpath):
     for bad in (0, 5):
         with pytest.raises(pc.PCError):
             pc.stencil_coefficients(bad)
+
+
+def test_header_is_plain_c():
+    """include/pc.h is a C ABI: it compiles as C99 (no C++ or CUDA types in the signatures)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    res = subprocess.run([cc, "-fsyntax-only", "-x", "c", "-std=c99", "-Wall", "-Werror", HEADER],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
