@@ -210,7 +210,8 @@ def run_reference(args, rank, ws, dist):
             times.append(secs / its * ipk)
     t = statistics.mean(times)
     value = 1.0 / t
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+    # n_gpus: the launch this line pairs with (the oracle itself runs on rank 0's host cores, see cpu_baseline)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "N": w.N, "nbands": w.nbands, "tol": w.tol, "nk_per_step": 1},
