@@ -104,3 +104,37 @@ def test_header_is_plain_c():
     res = subprocess.run([cc, "-fsyntax-only", "-x", "c", "-std=c99", "-Wall", "-Werror", HEADER],
                          capture_output=True, text=True)
     assert res.returncode == 0, res.stderr
+
+
+def _setup_rc(N, eps=None, lattice=None, **opts):
+    """pc_setup through ctypes; returns (rc, message). Every case below fails argument validation before any CUDA
+    call, so no GPU is needed."""
+    import ctypes as C
+
+    import numpy as np
+
+    from paper_2503_19379_gb300 import pc
+    L = pc.lib()
+    o = pc.default_opts(**opts)
+    e = np.ones((3, N, N, N)) if eps is None else eps
+    h = C.c_void_p()
+    lat = None if lattice is None else np.ascontiguousarray(np.asarray(lattice, dtype=np.float64).ravel())
+    rc = L.pc_setup(C.byref(h), N, pc._dptr(np.ascontiguousarray(e, dtype=np.float64)),
+                    pc._dptr(lat) if lat is not None else None, C.byref(o), None)
+    return rc, L.pc_last_error().decode()
+
+
+def test_setup_rejects_bad_arguments_on_the_host(libpath):
+    import numpy as np
+    rc, msg = _setup_rc(12)
+    assert rc == -1 and "power of two" in msg
+    rc, msg = _setup_rc(8, lattice=np.diag([1.0, 1.0, 2.0]))
+    assert rc == -2 and "cubic" in msg
+    rc, msg = _setup_rc(8, order=5)
+    assert rc == -2 and "order" in msg
+    rc, msg = _setup_rc(8, order=2, precision=1)
+    assert rc == -2 and "mixed" in msg
+    bad = np.ones((3, 8, 8, 8))
+    bad[1, 2, 3, 4] = 0.0
+    rc, msg = _setup_rc(8, eps=bad)
+    assert rc == -1 and "eps_edges" in msg
