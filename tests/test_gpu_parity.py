@@ -436,3 +436,20 @@ def test_mixed_groups_match_one(pcmod, groups):
     assert a["status"] == 0 and b["status"] == 0
     assert np.max(np.abs(a["evals"] - b["evals"]) / a["evals"]) <= 1e-8
     assert np.all(b["resid"] <= w.tol)
+
+
+def test_mixed_full_benchmark_batch(pcmod):
+    """The benchmark's own configuration: all 40 FCC k-points in one mixed solve with the default four k-point groups
+    on four streams. Every residual within tol, and on a sample of four k-points (Gamma, two interior points, L) the
+    eigenvalues equal those of the FP64 solve to 1e-6 relative."""
+    w = wl.workload_fcc_32()
+    S32, _ = make_solver(pcmod, w.N, structure=w.structure, precision=1)
+    b = S32.solve(w.kpts, w.nbands, w.tol)
+    assert b["status"] == 0
+    assert np.all(b["resid"] <= w.tol)
+    assert np.max(b["iters"]) <= 150
+    idx = [0, 17, 26, 39]
+    S64, _ = make_solver(pcmod, w.N, structure=w.structure)
+    a = S64.solve(w.kpts[idx], w.nbands, w.tol)
+    assert a["status"] == 0
+    assert np.max(np.abs(a["evals"] - b["evals"][idx]) / a["evals"]) <= 1e-6
