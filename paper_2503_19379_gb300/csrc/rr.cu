@@ -168,7 +168,7 @@ __host__ __device__ inline int rr_ld(int n) { return (n & 1) ? n : n + 1; }
 
 size_t rr_smem(int n, int m) {
   const int ld = rr_ld(n);
-  return sizeof(double2) * (3 * (size_t)n * ld + 3 * (size_t)n + 4 * RR_MAXN) +
+  return sizeof(double2) * (3 * (size_t)n * ld + 4 * (size_t)n + 4 * RR_MAXN) +
          sizeof(double) * (8 * (size_t)n + m) +
          sizeof(float) * 2 * (size_t)n + sizeof(int) * (2 * (size_t)n + m) + 64;
 }
@@ -184,8 +184,9 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
   double2 *Vh = B + n * LD;                             // Householder vectors, row k = v_k
   double2 *phi = Vh + n * LD;                           // phases of the tridiagonal scaling
   double2 *pv = phi + n;                                // p / q vectors of the Householder step
-  double2 *vv = pv + n;                                 // current Householder vector
-  double2 *hpart = vv + n;                              // partial products of a Householder step [4][RR_MAXN]
+  double2 *vv = pv + n;                                 // Householder vectors: two buffers (look-ahead)
+  double2 *vv2 = vv + n;
+  double2 *hpart = vv2 + n;                             // partial products of a Householder step [4][RR_MAXN]
   double *dsc = reinterpret_cast<double *>(hpart + 4 * RR_MAXN);
   double *dd = dsc + n, *ee = dd + n, *e2 = ee + n, *tau = e2 + n, *dinv = tau + n, *w = dinv + n;  // w: m
   double *spare = w + m;                                                                              // 2n
@@ -194,8 +195,8 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
   int *perm = reinterpret_cast<int *>(e232 + n);
   int *pos = perm + n;  // m
   __shared__ int s_p, s_r, s_stop, s_maxpos;
-  __shared__ double s_il, s_lkk, s_tau, s_gl, s_gu, s_tn, s_pivmin;
-  __shared__ double2 s_alpha, s_Kp[2];
+  __shared__ double s_il, s_lkk, s_tau2[2], s_gl, s_gu, s_tn, s_pivmin;
+  __shared__ double2 s_alpha2[2], s_Kp[2];
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
   const int b = act ? act[blockIdx.x] : (int)blockIdx.x;
   const double2 *G = Gg + (long)b * sg;
@@ -360,44 +361,65 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
   // 4. Householder tridiagonalisation of H3 (r x r), on its lower triangle. A GB300 SM retires about 2 FP64 FMA
   // per clock, so one warp-wide FP64 instruction holds an SM sub-partition's FP64 unit for tens of cycles: every
   // step below keeps its chains of FP64 instructions short and spreads its products over all four sub-partitions.
-  for (int k = 0; k + 2 < r; ++k) {
-    const int t = r - k - 1;
-    if (warp == 0) {
-      // x = B[k+1:, k], sigma = |x|^2; reflector v = x - alpha e1, alpha = -phase(x0) |x|, tau = 2 / |v|^2 with
-      // |v|^2 = 2 (sigma + |x0| |x|) (no cancellation)
-      double sig = 0.0;
-      for (int i = lane; i < t; i += 32) {
-        const double2 x = B[(k + 1 + i) * LD + k];
-        vv[i] = x;
-        sig = fma(x.x, x.x, fma(x.y, x.y, sig));
-      }
-      sig = warp_sum_d(sig);
-      if (lane == 0) {
-        const double2 x0 = vv[0];
-        if (sig == 0.0) {
-          s_tau = 0.0;
-        } else {
-          const double a0 = fma(x0.x, x0.x, x0.y * x0.y);
-          const double nrm = sig * rsqrt(sig);
-          double2 ph = cmake<double2>(1.0, 0.0);
-          double ax0 = 0.0;
-          if (a0 > 0.0) {
-            const double ra = rsqrt(a0);
-            ax0 = a0 * ra;
-            ph = cmake<double2>(x0.x * ra, x0.y * ra);
-          }
-          s_alpha = cmake<double2>(-ph.x * nrm, -ph.y * nrm);
-          vv[0] = cmake<double2>(fma(ph.x, nrm, x0.x), fma(ph.y, nrm, x0.y));
-          s_tau = 1.0 / fma(nrm, ax0, sig);
+  // Look-ahead: in the rank-2 update of step k, warp 0 updates the trailing block's first column first and forms
+  // the reflector of step k+1 from it while the other warps update the rest, so the reflector's serial chain of
+  // scalar FP64 work overlaps the update (two reflector buffers alternate).
+  //
+  // reflector of column kk (warp 0): x = B[kk+1:, kk], sigma = |x|^2; v = x - alpha e1, alpha = -phase(x0) |x|,
+  // tau = 2 / |v|^2 with |v|^2 = 2 (sigma + |x0| |x|) (no cancellation)
+  auto make_reflector = [&](int kk, double2 *vb, int slot) {
+    const int tt = r - kk - 1;
+    double sig = 0.0;
+    for (int i = lane; i < tt; i += 32) {
+      const double2 x = B[(kk + 1 + i) * LD + kk];
+      vb[i] = x;
+      sig = fma(x.x, x.x, fma(x.y, x.y, sig));
+    }
+    sig = warp_sum_d(sig);
+    if (lane == 0) {
+      const double2 x0 = vb[0];
+      if (sig == 0.0) {
+        s_tau2[slot] = 0.0;
+      } else {
+        const double a0 = fma(x0.x, x0.x, x0.y * x0.y);
+        const double nrm = sig * rsqrt(sig);
+        double2 ph = cmake<double2>(1.0, 0.0);
+        double ax0 = 0.0;
+        if (a0 > 0.0) {
+          const double ra = rsqrt(a0);
+          ax0 = a0 * ra;
+          ph = cmake<double2>(x0.x * ra, x0.y * ra);
         }
+        s_alpha2[slot] = cmake<double2>(-ph.x * nrm, -ph.y * nrm);
+        vb[0] = cmake<double2>(fma(ph.x, nrm, x0.x), fma(ph.y, nrm, x0.y));
+        s_tau2[slot] = 1.0 / fma(nrm, ax0, sig);
       }
     }
-    __syncthreads();
-    const double tk = s_tau;
+  };
+  // B_sub -= v q^H + q v^H at entry (i, j) of the trailing block of step k: eight FP64 FMA
+  auto rank2_entry = [&](int k, int i, int j, const double2 *vc) {
+    const double2 vi = vc[i], qi = pv[i], vj = vc[j], qj = pv[j];
+    double2 *bp = B + (k + 1 + i) * LD + k + 1 + j;
+    double2 bv = *bp;
+    bv.x = fma(-vi.x, qj.x, fma(-vi.y, qj.y, fma(-qi.x, vj.x, fma(-qi.y, vj.y, bv.x))));
+    bv.y = fma(-vi.y, qj.x, fma(vi.x, qj.y, fma(-qi.y, vj.x, fma(qi.x, vj.y, bv.y))));
+    *bp = bv;
+  };
+  int cur = 0;        // reflector buffer of the current step
+  bool have = false;  // its reflector was formed by the previous step's look-ahead
+  for (int k = 0; k + 2 < r; ++k) {
+    const int t = r - k - 1;
+    double2 *vc = cur ? vv2 : vv;
+    if (!have) {
+      if (warp == 0) make_reflector(k, vc, cur);
+      __syncthreads();
+    }
+    const double tk = s_tau2[cur];
     if (tid == 0) tau[k] = tk;
     if (tk == 0.0) {
       for (int i = tid; i < t; i += nt) Vh[k * LD + i] = cmake<double2>(0.0, 0.0);
       __syncthreads();
+      have = false;
       continue;
     }
     // partial products of B_sub v from the lower triangle of B_sub (the only part kept up to date): warp w takes
@@ -414,7 +436,7 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
         for (int j = j0; j < j1; ++j) {
           double2 a = j <= i ? row[j] : col[j * LD];
           a.y = __longlong_as_double(__double_as_longlong(a.y) ^ ((long long)(j > i) << 63));
-          const double2 x = vv[j];
+          const double2 x = vc[j];
           s.x = fma(a.x, x.x, fma(-a.y, x.y, s.x));
           s.y = fma(a.x, x.y, fma(a.y, x.x, s.y));
         }
@@ -429,8 +451,8 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
       if (i < t) {
         p = cscale(cadd(cadd(hpart[i], hpart[RR_MAXN + i]), cadd(hpart[2 * RR_MAXN + i], hpart[3 * RR_MAXN + i])),
                    tk);
-        Vh[k * LD + i] = vv[i];
-        w = cmulc(vv[i], p);
+        Vh[k * LD + i] = vc[i];
+        w = cmulc(vc[i], p);
       }
       w = warp_sum_d2(w);
       if (lane == 0) s_Kp[warp] = w;
@@ -441,25 +463,32 @@ __global__ void __launch_bounds__(RR_THREADS) rr_kernel(const double2 *__restric
       double2 K = s_Kp[0];
       if (t > 32) K = cadd(K, s_Kp[1]);
       K = cscale(K, 0.5 * tk);
-      if (i < t) pv[i] = csub(p, cmul(K, vv[i]));
+      if (i < t) pv[i] = csub(p, cmul(K, vc[i]));
     }
     __syncthreads();
-    // B_sub -= v q^H + q v^H on the lower triangle only, entries packed row by row (e -> (i, j), j <= i) so that
-    // every warp is full: eight FP64 FMA per entry
-    for (int e = tid; e < t * (t + 1) / 2; e += nt) {
-      int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-      if (i * (i + 1) / 2 > e) --i;
-      if ((i + 1) * (i + 2) / 2 <= e) ++i;
-      const int j = e - i * (i + 1) / 2;
-      const double2 vi = vv[i], qi = pv[i], vj = vv[j], qj = pv[j];
-      double2 *bp = B + (k + 1 + i) * LD + k + 1 + j;
-      double2 bv = *bp;
-      bv.x = fma(-vi.x, qj.x, fma(-vi.y, qj.y, fma(-qi.x, vj.x, fma(-qi.y, vj.y, bv.x))));
-      bv.y = fma(-vi.y, qj.x, fma(vi.x, qj.y, fma(-qi.y, vj.x, fma(qi.x, vj.y, bv.y))));
-      *bp = bv;
+    // the rank-2 update on the lower triangle, entries packed row by row (e -> (i, j), j <= i) so that every warp
+    // is full; with a next step, warp 0 takes the first column and the next reflector, warps 1.. the entries j >= 1
+    const bool ahead = k + 3 < r;
+    if (ahead && warp == 0) {
+      for (int i = lane; i < t; i += 32) rank2_entry(k, i, 0, vc);
+      __syncwarp();
+      make_reflector(k + 1, cur ? vv : vv2, 1 - cur);
     }
-    for (int i = tid; i < t; i += nt) B[(k + 1 + i) * LD + k] = i == 0 ? s_alpha : cmake<double2>(0.0, 0.0);
+    {
+      const int off = ahead ? 1 : 0, first = ahead ? 32 : 0, nthr = nt - first, tt = t - off;
+      if (tid >= first)
+        for (int e = tid - first; e < tt * (tt + 1) / 2; e += nthr) {
+          int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+          if (i * (i + 1) / 2 > e) --i;
+          if ((i + 1) * (i + 2) / 2 <= e) ++i;
+          const int j = e - i * (i + 1) / 2;
+          rank2_entry(k, i + off, j + off, vc);
+        }
+      for (int i = tid; i < t; i += nt) B[(k + 1 + i) * LD + k] = i == 0 ? s_alpha2[cur] : cmake<double2>(0.0, 0.0);
+    }
     __syncthreads();
+    have = ahead;
+    if (ahead) cur = 1 - cur;
   }
 
   // real tridiagonal T = Phi^H T_c Phi: moduli and unit phases in parallel, the phase product on one thread
