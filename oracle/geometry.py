@@ -11,6 +11,12 @@ Readings:
   Where spheres overlap, the last sphere in the list that contains the point gives its permittivity.
 * An edge midpoint whose distance to a sphere surface is below 1e-12 is "on the interface": its entry is
   4 / (sum of eps at the centres of the 4 cells sharing that edge), as in Section 4.4's harmonic rule.
+
+General lattice (Section 2's coordinate change x = A y): the grid above lives in y on the unit cube; a DoF at y sits
+at the Cartesian point x = A y. Sphere centres and radii are then Cartesian, and periodicity is under the columns of
+A: the distance to a centre is the minimum over the images c + A n. The nearest image is found by reducing the
+fractional offset A^{-1}(x - c) to [-1/2, 1/2]^3 and searching the 27 neighbouring translates, which is exact for
+cells whose reduced offset lies within one translate of the nearest image (the SC, FCC and BCC primitive cells).
 """
 from __future__ import annotations
 
@@ -26,13 +32,34 @@ def _periodic_distance(p, c):
     return np.sqrt(np.sum(d * d, axis=-1))
 
 
-def eps_at_points(points: np.ndarray, spheres: np.ndarray, eps_bg: float):
-    """Permittivity at each point, and a flag telling whether the point lies on some sphere surface."""
+def _lattice_distance(x, c, A, Ainv):
+    """Euclidean distance from Cartesian points x (..., 3) to the nearest image c + A n of the centre c."""
+    f = (x - np.asarray(c)[None, :]) @ Ainv.T
+    f = f - np.round(f)
+    r = np.array([-1.0, 0.0, 1.0])
+    shifts = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3)
+    best = np.full(f.shape[0], np.inf)
+    for s in shifts:
+        v = (f + s[None, :]) @ A.T
+        best = np.minimum(best, np.sqrt(np.sum(v * v, axis=-1)))
+    return best
+
+
+def eps_at_points(points: np.ndarray, spheres: np.ndarray, eps_bg: float, lattice=None):
+    """Permittivity at each point, and a flag telling whether the point lies on some sphere surface. Without a
+    lattice the points are fractions of the unit cube; with one they are y coordinates, mapped to x = A y."""
     pts = np.asarray(points, dtype=np.float64).reshape(-1, 3)
+    if lattice is not None:
+        A = np.asarray(lattice, dtype=np.float64)
+        Ainv = np.linalg.inv(A)
+        pts = pts @ A.T
     eps = np.full(pts.shape[0], float(eps_bg))
     on_iface = np.zeros(pts.shape[0], dtype=bool)
     for cx, cy, cz, r, e in np.asarray(spheres, dtype=np.float64).reshape(-1, 5):
-        dist = _periodic_distance(pts, (cx, cy, cz))
+        if lattice is None:
+            dist = _periodic_distance(pts, (cx, cy, cz))
+        else:
+            dist = _lattice_distance(pts, (cx, cy, cz), A, Ainv)
         eps[dist <= r] = e
         on_iface |= np.abs(dist - r) < INTERFACE_TOL
     return eps, on_iface
@@ -48,15 +75,16 @@ def edge_positions(N: int, axis: int) -> np.ndarray:
     return pos
 
 
-def eps_edges(N: int, spheres, eps_bg: float) -> np.ndarray:
-    """Permittivity at the 3 N^3 edge DoFs, shape (3, N, N, N), with the interface rule applied."""
+def eps_edges(N: int, spheres, eps_bg: float, lattice=None) -> np.ndarray:
+    """Permittivity at the 3 N^3 edge DoFs, shape (3, N, N, N), with the interface rule applied. With ``lattice``
+    the edge midpoints and cell centres are y coordinates mapped to x = A y, and the spheres are Cartesian."""
     h = 1.0 / N
     out = np.empty((3, N, N, N))
     i = np.arange(N)
     zc, yc, xc = np.meshgrid(i, i, i, indexing="ij")
     for axis in range(3):
         pos = edge_positions(N, axis)
-        eps, on = eps_at_points(pos, spheres, eps_bg)
+        eps, on = eps_at_points(pos, spheres, eps_bg, lattice)
         eps = eps.reshape(N, N, N)
         on = on.reshape(N, N, N)
         for z, y, x in zip(*np.nonzero(on)):
@@ -69,7 +97,7 @@ def eps_edges(N: int, spheres, eps_bg: float) -> np.ndarray:
                     idx[others[0]] += o1
                     idx[others[1]] += o2
                     centre = (np.asarray(idx, dtype=np.float64) + 0.5) * h
-                    e, _ = eps_at_points(centre[None, :], spheres, eps_bg)
+                    e, _ = eps_at_points(centre[None, :], spheres, eps_bg, lattice)
                     total += e[0]
             # stored as a permittivity, so that the M0 entry 1/eps equals the harmonic-rule value 4 / total
             eps[z, y, x] = total / 4.0
@@ -77,6 +105,6 @@ def eps_edges(N: int, spheres, eps_bg: float) -> np.ndarray:
     return out
 
 
-def m0_from_structure(N: int, spheres, eps_bg: float) -> np.ndarray:
+def m0_from_structure(N: int, spheres, eps_bg: float, lattice=None) -> np.ndarray:
     """The diagonal of M0, shape (3, N, N, N)."""
-    return 1.0 / eps_edges(N, spheres, eps_bg)
+    return 1.0 / (eps_edges(N, spheres, eps_bg) if lattice is None else eps_edges(N, spheres, eps_bg, lattice))
