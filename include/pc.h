@@ -12,7 +12,9 @@
  * check of Algorithm 4.1.
  *
  * Conventions common to every entry point
- * - Grid: N a power of two, 8 <= N <= 256; lattice constant a = 1 (h = 1/N); cubic cell only.
+ * - Grid: N a power of two, 8 <= N <= 256, h = 1/N, on the unit cube. The cubic cell (lattice = identity) has lattice
+ *   constant a = 1. A general cell (Section 2's coordinate change x = A y, Section 4.2.2) keeps the grid on the unit
+ *   cube of y; D_i becomes D_hat_i = sum_j b_ji K_j + i L_i with b = A^{-1}, and the field components stay Cartesian.
  * - A face (or edge) field is complex [3][N][N][N] = (component, z, y, x), x fastest, so that D_1 acts on x.
  *   A cell field is complex [N][N][N]. A "block" of m fields stores field j at offset j * 3 N^3 (column-major
  *   tall-skinny matrix with L = 3 N^3 rows); a batch of blocks for nb k-points stores block b at offset
@@ -82,7 +84,12 @@ int pc_opts_default(pc_opts *opts);
  *   N:         grid points per axis (power of two, 8..256).
  *   eps_edges: host [3][N][N][N] permittivity at the edge DoFs (x-edges at ((i+1/2)h, jh, kh), etc.), all > 0.
  *              M0 = diag(1/eps_edges).
- *   lattice:   host double[9], columns a1, a2, a3; must be the identity (cubic cell, a = 1) -> else PC_EUNSUPPORTED.
+ *   lattice:   host double[9] or NULL (identity): the lattice vectors a1, a2, a3 one after the other
+ *              (lattice[3 n + c] = component c of a_{n+1}), finite and linearly independent (else PC_EINVAL). The
+ *              identity runs the cubic cell's kernels; any other cell runs the general-lattice stencils at every
+ *              order and the FP64 / complex64 paths only (PC_PREC_MIXED with a non-identity lattice ->
+ *              PC_EUNSUPPORTED; the double-float stencil likewise). eps_edges then holds the permittivity at the
+ *              Cartesian points A y of the edge midpoints y (pc_eps_spheres_lattice).
  *   opts:      options (NULL -> defaults).
  *   stream:    cudaStream_t to use for all work of this context (NULL -> the legacy default stream).
  * Uploads M0 and the FFT tables once (one host-to-device copy). */
@@ -90,9 +97,10 @@ int pc_setup(pc_ctx **out, int N, const double *eps_edges, const double *lattice
              void *stream);
 
 /* pc_solve -- lowest nbands eigenpairs for each of nk Bloch vectors (Sections 3.2, 4.5, 5; Algorithm 4.1).
- *   kpts:   host [nk][3] Bloch vectors in units 1/a (reduced into [-pi, pi]^3 internally; a vector equivalent to 0
- *           is treated as k = 0: its 3 constant kernel fields are projected out and the lowest nonzero eigenvalues
- *           are returned).
+ *   kpts:   host [nk][3] Cartesian Bloch vectors in units 1/a (reduced internally: into [-pi, pi]^3 on the cube; by
+ *           the reciprocal lattice G = 2 pi A^{-T} n, n = round(A^T k / 2 pi), on a general cell); a vector
+ *           equivalent to 0 is treated as k = 0: its 3 constant kernel fields are projected out and the lowest
+ *           nonzero eigenvalues are returned).
  *   nbands: eigenpairs per k-point, 1 <= nbands <= 21 (nbands + guard <= 21).
  *   tol:    column j converged when |Op x - lambda x| <= tol |lambda| |x|.
  *   evals:  host [nk][nbands] ascending omega^2 (units (1/a)^2).
@@ -151,6 +159,17 @@ int pc_reset_stats(pc_ctx *ctx);
  *            Section 4.4: eps = (sum of eps at the 4 adjacent cell centres) / 4, so that M0 = 4 / sum.
  * Runs a device kernel; synchronous. */
 int pc_eps_spheres(int N, int nsph, const double *spheres, double eps_bg, double *eps_out);
+
+/* a0 on a general cell (Section 2's coordinate change x = A y; Section 4.4's rules).
+ *   lattice: host double[9], a1, a2, a3 one after the other as in pc_setup; linearly independent (else PC_EINVAL).
+ *   spheres: host [nsph][5] = (cx, cy, cz, r, eps_in), Cartesian (the units of the lattice vectors); a point x
+ *            belongs to a sphere when its distance to the nearest image c + A n of the centre is <= r (images
+ *            searched among the 27 translates around the reduced offset); later spheres take precedence.
+ *   eps_out: host [3][N][N][N] at the points A y of the edge midpoints y of the unit cube; the interface rule of
+ *            pc_eps_spheres applies with the cell centres mapped the same way.
+ * Runs a device kernel; synchronous. */
+int pc_eps_spheres_lattice(int N, const double *lattice, int nsph, const double *spheres, double eps_bg,
+                           double *eps_out);
 
 /* a1: Y = Op X = A M0 A' X + gamma B'B X for nb k-points x m fields (eq. Ker_comp; stencils of Section 4.1.2,
  * of the context's order: Table 1's 2k-th order schemes).

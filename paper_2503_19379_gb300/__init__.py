@@ -5,8 +5,9 @@ package is the thin Python binding over it: ``pc`` marshals arguments (numpy arr
 tensors for device buffers) and raises on any library error. There is no CPU fallback: importing the binding
 without a built library raises.
 """
-from .pc import (PCError, Solver, block_update, eigh_batched, eps_spheres, gram, gram_pair, gram_pair_coupled,
-                 init_block, lib, rayleigh_ritz, residual, stencil_coefficients)
+from .pc import (PCError, Solver, block_update, eigh_batched, eps_spheres, eps_spheres_lattice, gram, gram_pair,
+                 gram_pair_coupled, init_block, lattice_vectors, lib, rayleigh_ritz, residual, stencil_coefficients)
 
-__all__ = ["PCError", "Solver", "block_update", "eigh_batched", "eps_spheres", "gram", "gram_pair",
-           "gram_pair_coupled", "init_block", "lib", "rayleigh_ritz", "residual", "stencil_coefficients"]
+__all__ = ["PCError", "Solver", "block_update", "eigh_batched", "eps_spheres", "eps_spheres_lattice", "gram",
+           "gram_pair", "gram_pair_coupled", "init_block", "lattice_vectors", "lib", "rayleigh_ritz", "residual",
+           "stencil_coefficients"]

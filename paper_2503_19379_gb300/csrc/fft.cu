@@ -3,7 +3,8 @@
 //
 // Every circulant K_i, L_i is diagonal in the DFT basis (eq. diag_of_circ), so per mode m the preconditioner
 // P = A A' + gamma B'B is the 3x3 matrix sigma I + (gamma - 1) conj(d) d^T with d_i = symbol of D_i on mode m_i and
-// sigma = |d|^2. Its exact inverse (Sherman-Morrison) is (1/sigma) [I - (gamma-1)/(gamma sigma) conj(d) d^T]; with
+// sigma = |d|^2. On a general lattice d_i is the symbol of D_hat_i = sum_j b_ji K_j + i L_i, which depends on all
+// three mode indices (the same 3x3 algebra holds for any complex d). Its exact inverse (Sherman-Morrison) is (1/sigma) [I - (gamma-1)/(gamma sigma) conj(d) d^T]; with
 // the vector-Laplacian variant (gamma -> 1 in P) it is the scalar 1/sigma of Algorithm 5.1.
 //
 // Passes (each a read and a write of the block):
@@ -149,7 +150,8 @@ __global__ void __launch_bounds__(512) fft_xy_kernel(const cplx<T> *__restrict__
 }
 
 // Pass along z with the symbol: all 3 components of U contiguous x values at one y. grid (N*(N/U), m, nb).
-template <typename T>
+// LAT (general lattice, Section 4.2.2): d_i = sum_j (part of axis j)(m_j) from the tables [b][i][j][N].
+template <typename T, bool LAT>
 __global__ void __launch_bounds__(256) fft_z_symbol_kernel(const cplx<T> *__restrict__ in, long si,
                                                            cplx<T> *__restrict__ out, long so,
                                                            const cplx<T> *__restrict__ tw,
@@ -175,16 +177,30 @@ __global__ void __launch_bounds__(256) fft_z_symbol_kernel(const cplx<T> *__rest
   __syncthreads();
   fft_lines<C, true, true>(a, 3 * U, U, N * U, 1, U, logN, s_tw);  // lines (comp, u); z stride U
   // symbol inverse per mode
-  const double2 *symb = sym + (long)b * 3 * N;
+  const double2 *symb = sym + (long)b * (LAT ? 9 : 3) * N;
   const T fac = (T)((kp[b].gamma - 1.0) / kp[b].gamma);  // (gamma - 1) / gamma, once per block
   const T scale = (T)(1.0 / (double)n);
   const int my = bitrev(y, logN);
-  const double2 d2d = symb[N + my];
+  const double2 d2d = LAT ? make_double2(0.0, 0.0) : symb[N + my];
   for (int i = threadIdx.x; i < N * U; i += blockDim.x) {
     const int u = i % U, z = i / U;
     const int mx = bitrev(xt * U + u, logN), mz = bitrev(z, logN);
-    const double2 d1d = symb[mx], d3d = symb[2 * N + mz];
-    const C d1 = cmake<C>((T)d1d.x, (T)d1d.y), d2 = cmake<C>((T)d2d.x, (T)d2d.y), d3 = cmake<C>((T)d3d.x, (T)d3d.y);
+    C d1, d2, d3;
+    if constexpr (LAT) {
+      auto dsum = [&](int c) {
+        const double2 *t = symb + (long)c * 3 * N;
+        const double2 px = t[mx], py = t[N + my], pz = t[2 * N + mz];
+        return cmake<C>((T)(px.x + py.x + pz.x), (T)(px.y + py.y + pz.y));
+      };
+      d1 = dsum(0);
+      d2 = dsum(1);
+      d3 = dsum(2);
+    } else {
+      const double2 d1d = symb[mx], d3d = symb[2 * N + mz];
+      d1 = cmake<C>((T)d1d.x, (T)d1d.y);
+      d2 = cmake<C>((T)d2d.x, (T)d2d.y);
+      d3 = cmake<C>((T)d3d.x, (T)d3d.y);
+    }
     const T sigma = d1.x * d1.x + d1.y * d1.y + d2.x * d2.x + d2.y * d2.y + d3.x * d3.x + d3.y * d3.y;
     C r1 = a[i], r2 = a[N * U + i], r3 = a[2 * N * U + i];
     if (!(sigma > (T)0)) {
@@ -428,7 +444,8 @@ static int launch_precond_t(pc_ctx *ctx, int nb, int m, const void *R, long sr, 
     PC_CK(cudaFuncSetAttribute(fft_x_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     PC_CK(cudaFuncSetAttribute(fft_y_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     PC_CK(cudaFuncSetAttribute(fft_y_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    PC_CK(cudaFuncSetAttribute(fft_z_symbol_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    PC_CK(cudaFuncSetAttribute(fft_z_symbol_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    PC_CK(cudaFuncSetAttribute(fft_z_symbol_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     configured = true;
   }
   const C *Rc = static_cast<const C *>(R);
@@ -452,9 +469,13 @@ static int launch_precond_t(pc_ctx *ctx, int nb, int m, const void *R, long sr, 
     fft_y_kernel<T, true><<<dim3(gy, m, nb), 256, sy, ctx->stream>>>(Wc, sw, Wc, sw, tw, act, logN, Uy);
     PC_CK_LAUNCH();
   }
-  fft_z_symbol_kernel<T><<<dim3(gz, m, nb), 256, sz, ctx->stream>>>(Wc, sw, Wc, sw, tw, ctx->symd.as<double2>(),
-                                                                    ctx->kparam.as<KParam>(), act, logN, Uz,
-                                                                    ctx->opts.precond == PC_PRECOND_LAPLACIAN);
+  const int lap = ctx->opts.precond == PC_PRECOND_LAPLACIAN;
+  if (ctx->lat)
+    fft_z_symbol_kernel<T, true><<<dim3(gz, m, nb), 256, sz, ctx->stream>>>(
+        Wc, sw, Wc, sw, tw, ctx->symd.as<double2>(), ctx->kparam.as<KParam>(), act, logN, Uz, lap);
+  else
+    fft_z_symbol_kernel<T, false><<<dim3(gz, m, nb), 256, sz, ctx->stream>>>(
+        Wc, sw, Wc, sw, tw, ctx->symd.as<double2>(), ctx->kparam.as<KParam>(), act, logN, Uz, lap);
   PC_CK_LAUNCH();
   if (plane) {
     fft_xy_kernel<T, false><<<dim3(3 * N, m, nb), txy, sxy, ctx->stream>>>(Wc, sw, Wc, sw, tw, act, logN);
@@ -472,6 +493,8 @@ int launch_precond(pc_ctx *ctx, int nb, int m, int dtype, const void *R, long sr
                    const int *act) {
   if (nb == 0 || m == 0) return PC_OK;
   if (dtype == PC_C128) return launch_precond_t<double>(ctx, nb, m, R, sr, W, sw, act);
+  // the register path's symbols are per axis; a general lattice takes the shared-memory path
+  if (ctx->lat) return launch_precond_t<float>(ctx, nb, m, R, sr, W, sw, act);
   const float2 *Rf = static_cast<const float2 *>(R);
   float2 *Wf = static_cast<float2 *>(W);
   switch (ctx->logN) {

@@ -5,6 +5,7 @@
 // eps = (sum of eps at the 4 cell centres sharing the edge) / 4, i.e. M0 = 4 / sum (harmonic rule of Section 4.4).
 // Arithmetic uses explicit round-to-nearest intrinsics (no fused multiply-add) so that the classification of a
 // point does not depend on instruction selection.
+#include <cmath>
 #include <vector>
 
 #include "pc_internal.cuh"
@@ -69,6 +70,87 @@ __global__ void eps_edges_kernel(const double *__restrict__ sph, int nsph, doubl
   out[gid] = e;
 }
 
+// ---------------------------------------------------------------------------------------------- general lattice
+// Section 2's coordinate change x = A y: the grid above lives in y on the unit cube, and a DoF at y sits at the
+// Cartesian point x = A y. Sphere centres and radii are Cartesian; the distance to a centre c is the minimum over its
+// images c + A n, found by reducing the fractional offset A^{-1}(x - c) to [-1/2, 1/2]^3 and searching the 27
+// neighbouring translates.
+struct LatMat {
+  double a[9], ai[9];  // A and A^{-1}, row-major
+};
+
+__device__ __forceinline__ double dot3_rn(const double *r, double v0, double v1, double v2) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(r[0], v0), __dmul_rn(r[1], v1)), __dmul_rn(r[2], v2));
+}
+
+__device__ double sphere_dist_lat(const double *x, const double *s, const LatMat &L) {
+  const double d0 = __dsub_rn(x[0], s[0]), d1 = __dsub_rn(x[1], s[1]), d2 = __dsub_rn(x[2], s[2]);
+  double f[3];
+  for (int i = 0; i < 3; ++i) {
+    f[i] = dot3_rn(L.ai + 3 * i, d0, d1, d2);
+    f[i] = __dsub_rn(f[i], rint(f[i]));
+  }
+  double best = INFINITY;
+  for (int t = 0; t < 27; ++t) {
+    const double g0 = __dadd_rn(f[0], (double)(t % 3 - 1)), g1 = __dadd_rn(f[1], (double)((t / 3) % 3 - 1)),
+                 g2 = __dadd_rn(f[2], (double)(t / 9 - 1));
+    const double v0 = dot3_rn(L.a, g0, g1, g2), v1 = dot3_rn(L.a + 3, g0, g1, g2), v2 = dot3_rn(L.a + 6, g0, g1, g2);
+    best = fmin(best, sqrt(__dadd_rn(__dadd_rn(__dmul_rn(v0, v0), __dmul_rn(v1, v1)), __dmul_rn(v2, v2))));
+  }
+  return best;
+}
+
+__device__ double eps_point_lat(const double *y, const double *sph, int nsph, double eps_bg, const LatMat &L,
+                                bool *iface) {
+  const double x[3] = {dot3_rn(L.a, y[0], y[1], y[2]), dot3_rn(L.a + 3, y[0], y[1], y[2]),
+                       dot3_rn(L.a + 6, y[0], y[1], y[2])};
+  double e = eps_bg;
+  bool on = false;
+  for (int s = 0; s < nsph; ++s) {
+    const double *sp = sph + 5 * s;
+    const double d = sphere_dist_lat(x, sp, L);
+    if (d <= sp[3]) e = sp[4];
+    if (fabs(__dsub_rn(d, sp[3])) < IFACE_TOL) on = true;
+  }
+  if (iface) *iface = on;
+  return e;
+}
+
+__global__ void eps_edges_lat_kernel(const double *__restrict__ sph, int nsph, double eps_bg, int N, const LatMat L,
+                                     double *out) {
+  const long n = (long)N * N * N;
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= 3 * n) return;
+  const int axis = (int)(gid / n);
+  const long r = gid - (long)axis * n;
+  const int ix = (int)(r % N), iy = (int)((r / N) % N), iz = (int)(r / ((long)N * N));
+  const double h = 1.0 / (double)N;
+  double p[3] = {__dmul_rn((double)ix, h), __dmul_rn((double)iy, h), __dmul_rn((double)iz, h)};
+  p[axis] = __dadd_rn(p[axis], __dmul_rn(0.5, h));
+  bool on = false;
+  double e = eps_point_lat(p, sph, nsph, eps_bg, L, &on);
+  if (on) {
+    int o1 = (axis + 1) % 3, o2 = (axis + 2) % 3;
+    if (o1 > o2) {
+      const int t = o1;
+      o1 = o2;
+      o2 = t;
+    }
+    double total = 0.0;
+    for (int a = -1; a <= 0; ++a)
+      for (int c = -1; c <= 0; ++c) {
+        int idx[3] = {ix, iy, iz};
+        idx[o1] += a;
+        idx[o2] += c;
+        double q[3];
+        for (int d = 0; d < 3; ++d) q[d] = __dmul_rn(__dadd_rn((double)idx[d], 0.5), h);
+        total = __dadd_rn(total, eps_point_lat(q, sph, nsph, eps_bg, L, nullptr));
+      }
+    e = total / 4.0;
+  }
+  out[gid] = e;
+}
+
 }  // namespace pc
 
 using namespace pc;
@@ -84,6 +166,31 @@ extern "C" int pc_eps_spheres(int N, int nsph, const double *spheres, double eps
   PC_CK(dout.reserve(sizeof(double) * total));
   if (nsph) PC_CK(cudaMemcpy(ds.p, spheres, sizeof(double) * 5 * nsph, cudaMemcpyHostToDevice));
   eps_edges_kernel<<<(unsigned)((total + 255) / 256), 256>>>(ds.as<double>(), nsph, eps_bg, N, dout.as<double>());
+  PC_CK_LAUNCH();
+  PC_CK(cudaMemcpy(eps_out, dout.p, sizeof(double) * total, cudaMemcpyDeviceToHost));
+  return PC_OK;
+}
+
+extern "C" int pc_eps_spheres_lattice(int N, const double *lattice, int nsph, const double *spheres, double eps_bg,
+                                      double *eps_out) {
+  PC_REQUIRE(lattice && eps_out && (nsph == 0 || spheres), "pc_eps_spheres_lattice: null argument");
+  PC_REQUIRE(N >= 2 && N <= 1024 && nsph >= 0 && nsph <= 4096, "pc_eps_spheres_lattice: bad sizes");
+  PC_REQUIRE(eps_bg > 0.0, "pc_eps_spheres_lattice: eps_bg must be > 0");
+  for (int i = 0; i < 9; ++i) PC_REQUIRE(std::isfinite(lattice[i]), "pc_eps_spheres_lattice: lattice not finite");
+  for (int s = 0; s < nsph; ++s)
+    PC_REQUIRE(spheres[5 * s + 4] > 0.0 && spheres[5 * s + 3] >= 0.0, "pc_eps_spheres_lattice: bad sphere %d", s);
+  LatMat L;
+  if (invert_lattice(lattice, L.a, L.ai) != 0) {
+    set_error("pc_eps_spheres_lattice: the lattice vectors must be linearly independent");
+    return PC_EINVAL;
+  }
+  const long total = 3L * N * N * N;
+  DevBuf ds, dout;
+  PC_CK(ds.reserve(sizeof(double) * 5 * std::max(nsph, 1)));
+  PC_CK(dout.reserve(sizeof(double) * total));
+  if (nsph) PC_CK(cudaMemcpy(ds.p, spheres, sizeof(double) * 5 * nsph, cudaMemcpyHostToDevice));
+  eps_edges_lat_kernel<<<(unsigned)((total + 255) / 256), 256>>>(ds.as<double>(), nsph, eps_bg, N, L,
+                                                                 dout.as<double>());
   PC_CK_LAUNCH();
   PC_CK(cudaMemcpy(eps_out, dout.p, sizeof(double) * total, cudaMemcpyDeviceToHost));
   return PC_OK;

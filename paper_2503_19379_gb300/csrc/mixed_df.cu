@@ -381,8 +381,8 @@ static int op_df_dispatch(pc_ctx *ctx, int nb, int m, const void *X, long sx, vo
 
 int launch_apply_op_df(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act) {
   if (nb == 0 || m == 0) return PC_OK;
-  if (ctx->opts.order != 1) {
-    set_error("double-float stencil: second order (order 1) only");
+  if (ctx->opts.order != 1 || ctx->lat) {
+    set_error("double-float stencil: second order (order 1) on the cubic cell only");
     return PC_EUNSUPPORTED;
   }
   int nchunk = 0;

@@ -114,12 +114,17 @@ struct pc_ctx {
   long n = 0;  // N^3
   pc_opts opts{};
   cudaStream_t stream = nullptr;
+  // general lattice (Section 2's coordinate change x = A y, Section 4.2.2): lat is set when A is not the identity;
+  // binv = A^{-1} row-major (binv[3 * i + j] = b_ij), amat = A row-major (amat[3 * i + j] = a_j component i)
+  bool lat = false;
+  double binv[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  double amat[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   pc::DevBuf m0d, m0f;      // M0 diagonal, double and float copies, [3][N^3]
   pc::DevBuf m0p;           // M0 diagonal as double-float pairs (hi, lo) float2 [3][N^3]
   pc::DevBuf kscratch;      // higher-order stencils: e = M0 A' v (3 fields) and c = B v (1 field) per column
   pc::DevBuf twd, twf;      // FFT twiddles exp(-2 pi i t / N), t < N/2
   pc::DevBuf kparam;        // KParam [nb]
-  pc::DevBuf symd;          // per-k axis symbols d_i(m) complex128 [nb][3][N]
+  pc::DevBuf symd;          // per-k axis symbols d_i(m) complex128 [nb][3][N]; general lattice: [nb][3][3][N]
   pc::DevBuf scratch;       // general scratch (partial sums)
   int kcap = 0;             // capacity (k-points) of kparam / symd
   // solver buffers
@@ -164,6 +169,9 @@ namespace pc {
 template <typename F> int run_stage(pc_ctx *ctx, int stage, int kernels, double flops, double bytes, F &&launch);
 // Accumulates the elapsed times of finished event pairs; pairs still in flight stay pending.
 int harvest_timing(pc_ctx *ctx);
+// A (row-major) and b = A^{-1} (row-major) from the lattice vectors a_1, a_2, a_3 stored one after the other
+// (lattice[3 n + c] = component c of a_{n+1}); nonzero when the vectors are numerically dependent
+int invert_lattice(const double *lattice, double *amat, double *binv);
 // uploads kparams (and symbol tables) for nb k-points into the context; returns 0 or an error code
 int upload_kpoints(pc_ctx *ctx, int nb, const double *kpts, const double *gammas);
 // kernels launched by the solver (all on ctx->stream)
@@ -239,6 +247,8 @@ int launch_apply_op_k(pc_ctx *ctx, int nb, int m, int dtype, const void *X, long
 int launch_half_k(pc_ctx *ctx, int nb, int m, const void *X, void *E, void *Cc);
 int launch_recompute_k_partial(pc_ctx *ctx, int nb, int m, const void *X, long sx, const int *act, int nchunk,
                                long chunk, double *part, int dtype);
+// The two-pass kernels above also serve a general lattice (ctx->lat) at every order 1..4: D_hat_a = sum_j b_ja K_j
+// + i L_a replaces D_a (Section 4.2.2).
 // double-float (FP32-pair) versions of the FP64-accurate kernels of the mixed solve (mixed_df.cu). launch_apply_op_df
 // takes complex128 blocks; the others take and write blocks of double-float pairs (PC_DFS).
 int launch_apply_op_df(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act);

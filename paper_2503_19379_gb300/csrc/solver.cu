@@ -60,6 +60,49 @@ static void axis_symbols(int N, int order, double k_i, double2 *out) {
   }
 }
 
+// General lattice (Section 4.2.2): D_hat_i = sum_j b_ji K_j + i L_i has the symbol
+// d_i = sum_j i e^{i th_j/2} (b_ji S(m_j) + [j = i] k_i Z(m_j)), a sum of one table per axis j. This writes the table
+// of axis j for component i: weights wS = b_ji and wZ = k_i (j = i) or 0.
+static void lattice_part_symbols(int N, int order, double wS, double wZ, double2 *out) {
+  const double h = 1.0 / N;
+  double c[4], d[4];
+  stencil_coefficients(order, c, d);
+  for (int mm = 0; mm < N; ++mm) {
+    const double th = 2.0 * M_PI * mm / N;
+    double S = 0.0, Z = 0.0;
+    for (int q = 1; q <= order; ++q) {
+      S += c[q - 1] * std::sin((q - 0.5) * th);
+      Z += d[q - 1] * std::cos((q - 0.5) * th);
+    }
+    const double mag = wS * ((2.0 / h) * S) + wZ * (2.0 * Z);
+    out[mm].x = -std::sin(0.5 * th) * mag;
+    out[mm].y = std::cos(0.5 * th) * mag;
+  }
+}
+
+// amat[3 i + j] = component i of a_{j+1}; b = A^{-1} by the adjugate
+int invert_lattice(const double *lattice, double *amat, double *binv) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) amat[3 * i + j] = lattice[3 * j + i];
+  const double *a = amat;
+  const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+  const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+  double scale = 0.0;
+  for (int i = 0; i < 9; ++i) scale = std::max(scale, std::fabs(a[i]));
+  if (!(std::fabs(det) > 1e-12 * scale * scale * scale)) return 1;
+  // adjugate / det
+  binv[0] = c00 / det;
+  binv[1] = (a[2] * a[7] - a[1] * a[8]) / det;
+  binv[2] = (a[1] * a[5] - a[2] * a[4]) / det;
+  binv[3] = c01 / det;
+  binv[4] = (a[0] * a[8] - a[2] * a[6]) / det;
+  binv[5] = (a[2] * a[3] - a[0] * a[5]) / det;
+  binv[6] = c02 / det;
+  binv[7] = (a[1] * a[6] - a[0] * a[7]) / det;
+  binv[8] = (a[0] * a[4] - a[1] * a[3]) / det;
+  return 0;
+}
+
 void spurious_mask(const std::vector<int> &redo, int m, int nbands, double tol, const std::vector<double> &theta,
                    const std::vector<double> &rn, std::vector<int> &mask) {
   std::fill(mask.begin(), mask.end(), 0);
@@ -75,13 +118,14 @@ void spurious_mask(const std::vector<int> &redo, int m, int nbands, double tol, 
 
 int upload_kpoints(pc_ctx *ctx, int nb, const double *kpts, const double *gammas) {
   if (nb <= 0) return PC_OK;
+  const int tabs = ctx->lat ? 9 : 3;  // symbol tables per k-point: d_i by axis, or the parts (i, j) of d_i
   if (nb > ctx->kcap) {
     PC_CK(ctx->kparam.reserve(sizeof(KParam) * nb));
-    PC_CK(ctx->symd.reserve(sizeof(double2) * 3 * (size_t)ctx->N * nb));
+    PC_CK(ctx->symd.reserve(sizeof(double2) * tabs * (size_t)ctx->N * nb));
     ctx->kcap = nb;
   }
   std::vector<KParam> kp(nb);
-  std::vector<double2> sym((size_t)3 * ctx->N * nb);
+  std::vector<double2> sym((size_t)tabs * ctx->N * nb);
   for (int b = 0; b < nb; ++b) {
     for (int d = 0; d < 3; ++d) {
       kp[b].k[d] = kpts[3 * b + d];
@@ -92,8 +136,15 @@ int upload_kpoints(pc_ctx *ctx, int nb, const double *kpts, const double *gammas
     kp[b].gammaf = (float)gammas[b];
     kp[b].gammal = (float)(gammas[b] - (double)kp[b].gammaf);
     kp[b].pfacf = (float)((gammas[b] - 1.0) / gammas[b]);
-    for (int d = 0; d < 3; ++d)
-      axis_symbols(ctx->N, ctx->opts.order, kpts[3 * b + d], &sym[((size_t)b * 3 + d) * ctx->N]);
+    if (!ctx->lat) {
+      for (int d = 0; d < 3; ++d)
+        axis_symbols(ctx->N, ctx->opts.order, kpts[3 * b + d], &sym[((size_t)b * 3 + d) * ctx->N]);
+    } else {
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          lattice_part_symbols(ctx->N, ctx->opts.order, ctx->binv[3 * j + i], j == i ? kpts[3 * b + i] : 0.0,
+                               &sym[(((size_t)b * 3 + i) * 3 + j) * ctx->N]);
+    }
   }
   PC_CK(cudaMemcpyAsync(ctx->kparam.p, kp.data(), sizeof(KParam) * nb, cudaMemcpyHostToDevice, ctx->stream));
   PC_CK(cudaMemcpyAsync(ctx->symd.p, sym.data(), sizeof(double2) * sym.size(), cudaMemcpyHostToDevice, ctx->stream));
@@ -179,18 +230,26 @@ extern "C" int pc_setup(pc_ctx **out, int N, const double *eps_edges, const doub
   PC_REQUIRE(out && eps_edges, "pc_setup: null argument");
   *out = nullptr;
   PC_REQUIRE(is_pow2(N) && N >= 8 && N <= 256, "pc_setup: N must be a power of two in [8, 256], got %d", N);
+  // lattice[3 n + c] = component c of a_{n+1}: A = (a_1, a_2, a_3) column by column
+  double amat[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, binv[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  bool general = false;
   if (lattice) {
     for (int i = 0; i < 9; ++i) {
-      const double want = (i % 4 == 0) ? 1.0 : 0.0;
-      if (lattice[i] != want) {
-        set_error("pc_setup: only the unit cubic cell (lattice = identity) is implemented");
-        return PC_EUNSUPPORTED;
-      }
+      PC_REQUIRE(std::isfinite(lattice[i]), "pc_setup: lattice entries must be finite");
+      if (lattice[i] != ((i % 4 == 0) ? 1.0 : 0.0)) general = true;
+    }
+    if (general && invert_lattice(lattice, amat, binv) != 0) {
+      set_error("pc_setup: the lattice vectors must be linearly independent");
+      return PC_EINVAL;
     }
   }
   pc_opts o;
   pc_opts_default(&o);
   if (opts) o = *opts;
+  if (general && o.precision == PC_PREC_MIXED) {
+    set_error("pc_setup: the mixed-precision solve implements the cubic cell only (lattice = identity)");
+    return PC_EUNSUPPORTED;
+  }
   if (o.order < 1 || o.order > 4) {
     set_error("pc_setup: stencil order %d: Table 1 orders 1..4 (2nd to 8th order) are implemented", o.order);
     return PC_EUNSUPPORTED;
@@ -212,6 +271,9 @@ extern "C" int pc_setup(pc_ctx **out, int N, const double *eps_edges, const doub
   ctx->n = n;
   ctx->opts = o;
   ctx->stream = (cudaStream_t)stream;
+  ctx->lat = general;
+  std::memcpy(ctx->amat, amat, sizeof(amat));
+  std::memcpy(ctx->binv, binv, sizeof(binv));
   std::vector<double> m0(3 * n);
   std::vector<float> m0f(3 * n);
   std::vector<float2> m0p(3 * n);  // double-float pairs of m0
@@ -264,6 +326,22 @@ double reduce_component(double k) {
   return k - g * std::nearbyint(k / g);
 }
 
+// Bloch vector reduced by the reciprocal lattice G = 2 pi A^{-T} n of a general cell: n = round(A^T k / 2 pi),
+// k' = k - 2 pi A^{-T} n; a k whose fractional coordinates A^T k / 2 pi all lie within 1e-12 of integers is
+// equivalent to 0 and becomes exactly 0
+void reduce_lattice(const pc_ctx *ctx, const double *k, double *out) {
+  const double g = 2.0 * M_PI;
+  double f[3], nr[3];
+  bool zero = true;
+  for (int j = 0; j < 3; ++j) {
+    f[j] = (ctx->amat[j] * k[0] + ctx->amat[3 + j] * k[1] + ctx->amat[6 + j] * k[2]) / g;  // (A^T k)_j / 2 pi
+    nr[j] = std::nearbyint(f[j]);
+    if (std::fabs(f[j] - nr[j]) > 1e-12) zero = false;
+  }
+  for (int i = 0; i < 3; ++i)
+    out[i] = zero ? 0.0 : k[i] - g * (ctx->binv[i] * nr[0] + ctx->binv[3 + i] * nr[1] + ctx->binv[6 + i] * nr[2]);
+}
+
 }  // namespace
 
 extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, double tol, double *evals, void *evecs,
@@ -285,8 +363,9 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
   std::vector<int> zero(nb), doublings(nb, 0), itcount(nb, 0), done(nb, 0), round_start(nb, 0);
   for (int b = 0; b < nb; ++b) {
     double k2 = 0;
+    if (ctx->lat) reduce_lattice(ctx, kpts + 3 * b, &kr[3 * b]);
     for (int d = 0; d < 3; ++d) {
-      kr[3 * b + d] = reduce_component(kpts[3 * b + d]);
+      if (!ctx->lat) kr[3 * b + d] = reduce_component(kpts[3 * b + d]);
       k2 += kr[3 * b + d] * kr[3 * b + d];
     }
     zero[b] = (k2 == 0.0);

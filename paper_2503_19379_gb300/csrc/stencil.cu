@@ -425,7 +425,7 @@ static int launch_opz_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, void
 int launch_apply_op(pc_ctx *ctx, int nb, int m, int dtype, const void *X, long sx, void *Y, long sy,
                     const int *act) {
   if (nb == 0 || m == 0) return PC_OK;
-  if (ctx->opts.order > 1) return launch_apply_op_k(ctx, nb, m, dtype, X, sx, Y, sy, act);
+  if (ctx->opts.order > 1 || ctx->lat) return launch_apply_op_k(ctx, nb, m, dtype, X, sx, Y, sy, act);
   const int N = ctx->N;
   if (dtype == PC_C64 && N >= 32) return launch_opz_t<float, 32, 8>(ctx, nb, m, X, sx, Y, sy, act);
   if (dtype == PC_C128) {
@@ -454,7 +454,7 @@ int launch_recompute(pc_ctx *ctx, int nb, int m, const void *X, long sx, double 
     return PC_EINVAL;
   }
   double *part = static_cast<double *>(scratch);
-  if (ctx->opts.order > 1) {
+  if (ctx->opts.order > 1 || ctx->lat) {
     int rc = launch_recompute_k_partial(ctx, nb, m, X, sx, act, nchunk, chunk, part, dtype);
     if (rc) return rc;
   } else if (dtype == PC_DFS)
@@ -494,7 +494,7 @@ extern "C" int pc_apply_half(pc_ctx *ctx, int nb, const double *kpts, int m, con
   std::vector<double> g(nb, 1.0);
   int rc = upload_kpoints(ctx, nb, kpts, g.data());
   if (rc) return rc;
-  if (ctx->opts.order > 1) return launch_half_k(ctx, nb, m, X, E, C);
+  if (ctx->opts.order > 1 || ctx->lat) return launch_half_k(ctx, nb, m, X, E, C);
   dim3 grid((unsigned)((ctx->n + 255) / 256), m, nb);
   half_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const double2 *>(X), static_cast<double2 *>(E),
                                               static_cast<double2 *>(C), ctx->kparam.as<KParam>(), ctx->logN, m,

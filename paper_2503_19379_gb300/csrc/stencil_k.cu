@@ -16,6 +16,12 @@
 // M0. Neighbours are read from global memory through L1 and L2: these orders are off the benchmark's path (which
 // runs the second-order z-marching kernels) and are written for clarity; the mixed-precision solve, whose phase 2
 // needs the double-float stencil, stays at second order.
+//
+// General lattice (Section 2's coordinate change x = A y, Section 4.2.2): with b = A^{-1}, D_i is replaced by
+// D_hat_i = sum_j b_ji K_j + i L_i, i.e.
+//   (D_hat_i f)_r  = sum_j (b_ji/h) sum_s c_s (f_{r+s e_j} - f_{r-(s-1) e_j}) + i k_i sum_s d_s (f_{r+s e_i} + ...),
+// and D_hat_i' likewise with the adjoint offsets. The same two passes run with these operators (template flag LAT)
+// at every order, the second-order one included.
 #include <cmath>
 
 #include "dfloat.cuh"
@@ -52,6 +58,17 @@ namespace {
 template <typename T> struct Coef {
   T c[KMAX], d[KMAX];
 };
+
+// general lattice: bh[3 j + a] = b_ja / h, the weight of the difference along axis j in D_hat_a
+template <typename T> struct Lat {
+  T bh[9];
+};
+
+template <typename T> Lat<T> lat_for(const pc_ctx *ctx) {
+  Lat<T> l;
+  for (int i = 0; i < 9; ++i) l.bh[i] = (T)(ctx->binv[i] * (double)ctx->N);
+  return l;
+}
 
 template <typename T> Coef<T> coef_for(int k) {
   double c[KMAX], d[KMAX];
@@ -104,6 +121,58 @@ __device__ __forceinline__ C dkt(const C *__restrict__ g, int a, int x, int y, i
   return cmake<C>(ih * df.x + ka * sm.y, ih * df.y - ka * sm.x);
 }
 
+// (D_hat_a f) at (x, y, z) on a general lattice
+template <typename T, typename C, int K>
+__device__ __forceinline__ C dl(const C *__restrict__ f, int a, int x, int y, int z, int logN, T ka,
+                                const Coef<T> &cf, const Lat<T> &lt) {
+  C acc = cmake<C>(T(0), T(0)), sm = acc;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    C df = cmake<C>(T(0), T(0));
+#pragma unroll
+    for (int s = 1; s <= K; ++s) {
+      const C p = at(f, j, s, x, y, z, logN), q = at(f, j, 1 - s, x, y, z, logN);
+      df = cadd(df, cscale(csub(p, q), cf.c[s - 1]));
+      if (j == a) sm = cadd(sm, cscale(cadd(p, q), cf.d[s - 1]));
+    }
+    acc = cadd(acc, cscale(df, lt.bh[3 * j + a]));
+  }
+  return cmake<C>(acc.x - ka * sm.y, acc.y + ka * sm.x);
+}
+
+// (D_hat_a' g) at (x, y, z) on a general lattice (b real: D_hat_a' = sum_j b_ja K_j' - i L_a')
+template <typename T, typename C, int K>
+__device__ __forceinline__ C dlt(const C *__restrict__ g, int a, int x, int y, int z, int logN, T ka,
+                                 const Coef<T> &cf, const Lat<T> &lt) {
+  C acc = cmake<C>(T(0), T(0)), sm = acc;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    C df = cmake<C>(T(0), T(0));
+#pragma unroll
+    for (int s = 1; s <= K; ++s) {
+      const C p = at(g, j, -s, x, y, z, logN), q = at(g, j, s - 1, x, y, z, logN);
+      df = cadd(df, cscale(csub(p, q), cf.c[s - 1]));
+      if (j == a) sm = cadd(sm, cscale(cadd(p, q), cf.d[s - 1]));
+    }
+    acc = cadd(acc, cscale(df, lt.bh[3 * j + a]));
+  }
+  return cmake<C>(acc.x + ka * sm.y, acc.y - ka * sm.x);
+}
+
+// D_a or D_hat_a (LAT), and the adjoints, behind one call
+template <typename T, typename C, int K, bool LAT>
+__device__ __forceinline__ C dop(const C *__restrict__ f, int a, int x, int y, int z, int logN, T ih, T ka,
+                                 const Coef<T> &cf, const Lat<T> &lt) {
+  if constexpr (LAT) return dl<T, C, K>(f, a, x, y, z, logN, ka, cf, lt);
+  else return dk<T, C, K>(f, a, x, y, z, logN, ih, ka, cf);
+}
+template <typename T, typename C, int K, bool LAT>
+__device__ __forceinline__ C dopt(const C *__restrict__ g, int a, int x, int y, int z, int logN, T ih, T ka,
+                                  const Coef<T> &cf, const Lat<T> &lt) {
+  if constexpr (LAT) return dlt<T, C, K>(g, a, x, y, z, logN, ka, cf, lt);
+  else return dkt<T, C, K>(g, a, x, y, z, logN, ih, ka, cf);
+}
+
 template <typename T> __device__ __forceinline__ T kval(const KParam &p, int a);
 template <> __device__ __forceinline__ double kval<double>(const KParam &p, int a) { return p.k[a]; }
 template <> __device__ __forceinline__ float kval<float>(const KParam &p, int a) { return 2.0f * p.khf[a]; }
@@ -113,11 +182,11 @@ template <> __device__ __forceinline__ float gval<float>(const KParam &p) { retu
 
 // pass 1: e = [M0] A' v (three components) and c = B v of column j of k-point act[bz]; outputs at
 // E + (bz m + j) 3n and Cc + (bz m + j) n. grid (ceil(n / 256), m, nb)
-template <typename T, int K>
+template <typename T, int K, bool LAT>
 __global__ void __launch_bounds__(256) opk_half_kernel(const cplx<T> *__restrict__ X, long sx, cplx<T> *__restrict__ E,
                                                       cplx<T> *__restrict__ Cc, const T *__restrict__ m0,
                                                       const KParam *__restrict__ kp, const int *__restrict__ act,
-                                                      int logN, T ih, const Coef<T> cf) {
+                                                      int logN, T ih, const Coef<T> cf, const Lat<T> lt) {
   using C = cplx<T>;
   const long n = 1L << (3 * logN);
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -129,16 +198,17 @@ __global__ void __launch_bounds__(256) opk_half_kernel(const cplx<T> *__restrict
   const KParam &p = kp[b];
   const T k0 = kval<T>(p, 0), k1 = kval<T>(p, 1), k2 = kval<T>(p, 2);
   const C *v1 = X + (long)b * sx + (long)j * 3 * n, *v2 = v1 + n, *v3 = v2 + n;
-  C e1 = csub(dkt<T, C, K>(v2, 2, x, y, z, logN, ih, k2, cf), dkt<T, C, K>(v3, 1, x, y, z, logN, ih, k1, cf));
-  C e2 = csub(dkt<T, C, K>(v3, 0, x, y, z, logN, ih, k0, cf), dkt<T, C, K>(v1, 2, x, y, z, logN, ih, k2, cf));
-  C e3 = csub(dkt<T, C, K>(v1, 1, x, y, z, logN, ih, k1, cf), dkt<T, C, K>(v2, 0, x, y, z, logN, ih, k0, cf));
+  auto Dt = [&](const C *f, int a, T ka) { return dopt<T, C, K, LAT>(f, a, x, y, z, logN, ih, ka, cf, lt); };
+  auto D = [&](const C *f, int a, T ka) { return dop<T, C, K, LAT>(f, a, x, y, z, logN, ih, ka, cf, lt); };
+  C e1 = csub(Dt(v2, 2, k2), Dt(v3, 1, k1));
+  C e2 = csub(Dt(v3, 0, k0), Dt(v1, 2, k2));
+  C e3 = csub(Dt(v1, 1, k1), Dt(v2, 0, k0));
   if (m0) {
     e1 = cscale(e1, m0[i]);
     e2 = cscale(e2, m0[n + i]);
     e3 = cscale(e3, m0[2 * n + i]);
   }
-  const C c = cadd(cadd(dk<T, C, K>(v1, 0, x, y, z, logN, ih, k0, cf), dk<T, C, K>(v2, 1, x, y, z, logN, ih, k1, cf)),
-                   dk<T, C, K>(v3, 2, x, y, z, logN, ih, k2, cf));
+  const C c = cadd(cadd(D(v1, 0, k0), D(v2, 1, k1)), D(v3, 2, k2));
   if (E) {
     C *eb = E + ((long)bz * m + j) * 3 * n;
     eb[i] = e1;
@@ -149,10 +219,11 @@ __global__ void __launch_bounds__(256) opk_half_kernel(const cplx<T> *__restrict
 }
 
 // pass 2: y = A e + gamma B' c for column j of k-point act[bz]
-template <typename T, int K>
+template <typename T, int K, bool LAT>
 __global__ void __launch_bounds__(256) opk_full_kernel(const cplx<T> *__restrict__ E, const cplx<T> *__restrict__ Cc,
                                                       cplx<T> *__restrict__ Y, long sy, const KParam *__restrict__ kp,
-                                                      const int *__restrict__ act, int logN, T ih, const Coef<T> cf) {
+                                                      const int *__restrict__ act, int logN, T ih, const Coef<T> cf,
+                                                      const Lat<T> lt) {
   using C = cplx<T>;
   const long n = 1L << (3 * logN);
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -165,12 +236,14 @@ __global__ void __launch_bounds__(256) opk_full_kernel(const cplx<T> *__restrict
   const T k0 = kval<T>(p, 0), k1 = kval<T>(p, 1), k2 = kval<T>(p, 2), gam = gval<T>(p);
   const C *e1 = E + ((long)bz * m + j) * 3 * n, *e2 = e1 + n, *e3 = e2 + n;
   const C *c = Cc + ((long)bz * m + j) * n;
-  C y1 = csub(dk<T, C, K>(e3, 1, x, y, z, logN, ih, k1, cf), dk<T, C, K>(e2, 2, x, y, z, logN, ih, k2, cf));
-  C y2 = csub(dk<T, C, K>(e1, 2, x, y, z, logN, ih, k2, cf), dk<T, C, K>(e3, 0, x, y, z, logN, ih, k0, cf));
-  C y3 = csub(dk<T, C, K>(e2, 0, x, y, z, logN, ih, k0, cf), dk<T, C, K>(e1, 1, x, y, z, logN, ih, k1, cf));
-  y1 = cadd(y1, cscale(dkt<T, C, K>(c, 0, x, y, z, logN, ih, k0, cf), gam));
-  y2 = cadd(y2, cscale(dkt<T, C, K>(c, 1, x, y, z, logN, ih, k1, cf), gam));
-  y3 = cadd(y3, cscale(dkt<T, C, K>(c, 2, x, y, z, logN, ih, k2, cf), gam));
+  auto Dt = [&](const C *f, int a, T ka) { return dopt<T, C, K, LAT>(f, a, x, y, z, logN, ih, ka, cf, lt); };
+  auto D = [&](const C *f, int a, T ka) { return dop<T, C, K, LAT>(f, a, x, y, z, logN, ih, ka, cf, lt); };
+  C y1 = csub(D(e3, 1, k1), D(e2, 2, k2));
+  C y2 = csub(D(e1, 2, k2), D(e3, 0, k0));
+  C y3 = csub(D(e2, 0, k0), D(e1, 1, k1));
+  y1 = cadd(y1, cscale(Dt(c, 0, k0), gam));
+  y2 = cadd(y2, cscale(Dt(c, 1, k1), gam));
+  y3 = cadd(y3, cscale(Dt(c, 2, k2), gam));
   C *yb = Y + (long)b * sy + (long)j * 3 * n;
   yb[i] = y1;
   yb[n + i] = y2;
@@ -179,13 +252,13 @@ __global__ void __launch_bounds__(256) opk_full_kernel(const cplx<T> *__restrict
 
 // Algorithm 4.1 norms at order K: per-block partial sums of (sum M0 |A'x|^2, sum |Bx|^2, sum |x|^2); S: complex128
 // or double-float pairs, read as FP64. grid (nchunk, m, nb), 256 threads
-template <typename S, int K>
+template <typename S, int K, bool LAT>
 __global__ void __launch_bounds__(256) recompute_k_partial_kernel(const S *__restrict__ X, long sx,
                                                                  const double *__restrict__ m0,
                                                                  const KParam *__restrict__ kp,
                                                                  const int *__restrict__ act, int logN, double ih,
                                                                  long chunk, const Coef<double> cf,
-                                                                 double *__restrict__ part) {
+                                                                 const Lat<double> lt, double *__restrict__ part) {
   const long n = 1L << (3 * logN);
   const int N = 1 << logN;
   const int bi = blockIdx.z, j = blockIdx.y;
@@ -196,9 +269,11 @@ __global__ void __launch_bounds__(256) recompute_k_partial_kernel(const S *__res
   const long beg = (long)blockIdx.x * chunk, end = min(n, beg + chunk);
   for (long i = beg + threadIdx.x; i < end; i += blockDim.x) {
     const int x = (int)(i & (N - 1)), y = (int)((i >> logN) & (N - 1)), z = (int)(i >> (2 * logN));
-    // gather the stencil's neighbours as FP64 through a small lambda over the storage type
-    auto dkS = [&](int comp, int a, bool adj) {
-      double2 df = make_double2(0.0, 0.0), sm = df;
+    // gather the stencil's neighbours as FP64 through a small lambda over the storage type: the difference (df)
+    // and average (sm) sums along axis a
+    auto terms = [&](int comp, int a, bool adj, double2 &df, double2 &sm) {
+      df = make_double2(0.0, 0.0);
+      sm = df;
 #pragma unroll
       for (int s = 1; s <= K; ++s) {
         const int op = adj ? -s : s, oq = adj ? s - 1 : 1 - s;
@@ -220,9 +295,25 @@ __global__ void __launch_bounds__(256) recompute_k_partial_kernel(const S *__res
         df = cadd(df, cscale(csub(pv, qv), cf.c[s - 1]));
         sm = cadd(sm, cscale(cadd(pv, qv), cf.d[s - 1]));
       }
+    };
+    auto dkS = [&](int comp, int a, bool adj) {
+      double2 df, sm;
+      terms(comp, a, adj, df, sm);
       const double ka = p.k[a];
-      return adj ? make_double2(ih * df.x + ka * sm.y, ih * df.y - ka * sm.x)
-                 : make_double2(ih * df.x - ka * sm.y, ih * df.y + ka * sm.x);
+      if constexpr (LAT) {  // sum_j (b_ja / h) (difference along j) + i k_a (average along a)
+        double2 acc = cscale(df, lt.bh[3 * a + a]);
+        for (int jx = 0; jx < 3; ++jx) {
+          if (jx == a) continue;
+          double2 dj, sj;
+          terms(comp, jx, adj, dj, sj);
+          acc = cadd(acc, cscale(dj, lt.bh[3 * jx + a]));
+        }
+        return adj ? make_double2(acc.x + ka * sm.y, acc.y - ka * sm.x)
+                   : make_double2(acc.x - ka * sm.y, acc.y + ka * sm.x);
+      } else {
+        return adj ? make_double2(ih * df.x + ka * sm.y, ih * df.y - ka * sm.x)
+                   : make_double2(ih * df.x - ka * sm.y, ih * df.y + ka * sm.x);
+      }
     };
     const double2 e1 = csub(dkS(1, 2, true), dkS(2, 1, true));
     const double2 e2 = csub(dkS(2, 0, true), dkS(0, 2, true));
@@ -254,57 +345,74 @@ __global__ void __launch_bounds__(256) recompute_k_partial_kernel(const S *__res
   }
 }
 
-template <typename T, int K>
+template <typename T, int K, bool LAT>
 int apply_op_k_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act) {
   using C = cplx<T>;
   const long n = ctx->n;
   PC_CK(ctx->kscratch.reserve(sizeof(C) * 4 * (size_t)n * m * nb));
   C *E = ctx->kscratch.as<C>(), *Cc = E + 3 * n * (long)m * nb;
   const Coef<T> cf = coef_for<T>(K);
+  const Lat<T> lt = lat_for<T>(ctx);
   const T *m0 = std::is_same<T, double>::value ? ctx->m0d.as<T>() : ctx->m0f.as<T>();
   const dim3 grid((unsigned)((n + 255) / 256), m, nb);
-  opk_half_kernel<T, K><<<grid, 256, 0, ctx->stream>>>(static_cast<const C *>(X), sx, E, Cc, m0,
-                                                        ctx->kparam.as<KParam>(), act, ctx->logN, (T)ctx->N, cf);
+  opk_half_kernel<T, K, LAT><<<grid, 256, 0, ctx->stream>>>(static_cast<const C *>(X), sx, E, Cc, m0,
+                                                             ctx->kparam.as<KParam>(), act, ctx->logN, (T)ctx->N, cf,
+                                                             lt);
   PC_CK_LAUNCH();
-  opk_full_kernel<T, K><<<grid, 256, 0, ctx->stream>>>(E, Cc, static_cast<C *>(Y), sy, ctx->kparam.as<KParam>(), act,
-                                                        ctx->logN, (T)ctx->N, cf);
+  opk_full_kernel<T, K, LAT><<<grid, 256, 0, ctx->stream>>>(E, Cc, static_cast<C *>(Y), sy, ctx->kparam.as<KParam>(),
+                                                             act, ctx->logN, (T)ctx->N, cf, lt);
   PC_CK_LAUNCH();
   return PC_OK;
 }
 
+// cube: orders 2..4 (order 1 runs the tiled kernels of stencil.cu); general lattice: orders 1..4
 template <typename T>
 int apply_op_k_dispatch(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act) {
-  switch (ctx->opts.order) {
-    case 2: return apply_op_k_t<T, 2>(ctx, nb, m, X, sx, Y, sy, act);
-    case 3: return apply_op_k_t<T, 3>(ctx, nb, m, X, sx, Y, sy, act);
-    case 4: return apply_op_k_t<T, 4>(ctx, nb, m, X, sx, Y, sy, act);
-    default: set_error("stencil order %d is not implemented", ctx->opts.order); return PC_EUNSUPPORTED;
+  if (ctx->lat) {
+    switch (ctx->opts.order) {
+      case 1: return apply_op_k_t<T, 1, true>(ctx, nb, m, X, sx, Y, sy, act);
+      case 2: return apply_op_k_t<T, 2, true>(ctx, nb, m, X, sx, Y, sy, act);
+      case 3: return apply_op_k_t<T, 3, true>(ctx, nb, m, X, sx, Y, sy, act);
+      case 4: return apply_op_k_t<T, 4, true>(ctx, nb, m, X, sx, Y, sy, act);
+      default: break;
+    }
+  } else {
+    switch (ctx->opts.order) {
+      case 2: return apply_op_k_t<T, 2, false>(ctx, nb, m, X, sx, Y, sy, act);
+      case 3: return apply_op_k_t<T, 3, false>(ctx, nb, m, X, sx, Y, sy, act);
+      case 4: return apply_op_k_t<T, 4, false>(ctx, nb, m, X, sx, Y, sy, act);
+      default: break;
+    }
   }
+  set_error("stencil order %d is not implemented", ctx->opts.order);
+  return PC_EUNSUPPORTED;
 }
 
-template <int K>
+template <int K, bool LAT>
 int half_k_t(pc_ctx *ctx, int nb, int m, const void *X, void *E, void *Cc) {
   const dim3 grid((unsigned)((ctx->n + 255) / 256), m, nb);
-  opk_half_kernel<double, K><<<grid, 256, 0, ctx->stream>>>(
+  opk_half_kernel<double, K, LAT><<<grid, 256, 0, ctx->stream>>>(
       static_cast<const double2 *>(X), (long)m * 3 * ctx->n, static_cast<double2 *>(E), static_cast<double2 *>(Cc),
-      nullptr, ctx->kparam.as<KParam>(), nullptr, ctx->logN, (double)ctx->N, coef_for<double>(K));
+      nullptr, ctx->kparam.as<KParam>(), nullptr, ctx->logN, (double)ctx->N, coef_for<double>(K),
+      lat_for<double>(ctx));
   PC_CK_LAUNCH();
   return PC_OK;
 }
 
-template <int K>
+template <int K, bool LAT>
 int recompute_k_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, const int *act, int nchunk, long chunk,
                   double *part, int dtype) {
   const dim3 grid(nchunk, m, nb);
   const Coef<double> cf = coef_for<double>(K);
+  const Lat<double> lt = lat_for<double>(ctx);
   if (dtype == PC_DFS)
-    recompute_k_partial_kernel<float4, K><<<grid, 256, 0, ctx->stream>>>(
+    recompute_k_partial_kernel<float4, K, LAT><<<grid, 256, 0, ctx->stream>>>(
         static_cast<const float4 *>(X), sx, ctx->m0d.as<double>(), ctx->kparam.as<KParam>(), act, ctx->logN,
-        (double)ctx->N, chunk, cf, part);
+        (double)ctx->N, chunk, cf, lt, part);
   else
-    recompute_k_partial_kernel<double2, K><<<grid, 256, 0, ctx->stream>>>(
+    recompute_k_partial_kernel<double2, K, LAT><<<grid, 256, 0, ctx->stream>>>(
         static_cast<const double2 *>(X), sx, ctx->m0d.as<double>(), ctx->kparam.as<KParam>(), act, ctx->logN,
-        (double)ctx->N, chunk, cf, part);
+        (double)ctx->N, chunk, cf, lt, part);
   PC_CK_LAUNCH();
   return PC_OK;
 }
@@ -321,22 +429,46 @@ int launch_apply_op_k(pc_ctx *ctx, int nb, int m, int dtype, const void *X, long
 }
 
 int launch_half_k(pc_ctx *ctx, int nb, int m, const void *X, void *E, void *Cc) {
-  switch (ctx->opts.order) {
-    case 2: return half_k_t<2>(ctx, nb, m, X, E, Cc);
-    case 3: return half_k_t<3>(ctx, nb, m, X, E, Cc);
-    case 4: return half_k_t<4>(ctx, nb, m, X, E, Cc);
-    default: set_error("stencil order %d is not implemented", ctx->opts.order); return PC_EUNSUPPORTED;
+  if (ctx->lat) {
+    switch (ctx->opts.order) {
+      case 1: return half_k_t<1, true>(ctx, nb, m, X, E, Cc);
+      case 2: return half_k_t<2, true>(ctx, nb, m, X, E, Cc);
+      case 3: return half_k_t<3, true>(ctx, nb, m, X, E, Cc);
+      case 4: return half_k_t<4, true>(ctx, nb, m, X, E, Cc);
+      default: break;
+    }
+  } else {
+    switch (ctx->opts.order) {
+      case 2: return half_k_t<2, false>(ctx, nb, m, X, E, Cc);
+      case 3: return half_k_t<3, false>(ctx, nb, m, X, E, Cc);
+      case 4: return half_k_t<4, false>(ctx, nb, m, X, E, Cc);
+      default: break;
+    }
   }
+  set_error("stencil order %d is not implemented", ctx->opts.order);
+  return PC_EUNSUPPORTED;
 }
 
 int launch_recompute_k_partial(pc_ctx *ctx, int nb, int m, const void *X, long sx, const int *act, int nchunk,
                                long chunk, double *part, int dtype) {
-  switch (ctx->opts.order) {
-    case 2: return recompute_k_t<2>(ctx, nb, m, X, sx, act, nchunk, chunk, part, dtype);
-    case 3: return recompute_k_t<3>(ctx, nb, m, X, sx, act, nchunk, chunk, part, dtype);
-    case 4: return recompute_k_t<4>(ctx, nb, m, X, sx, act, nchunk, chunk, part, dtype);
-    default: set_error("stencil order %d is not implemented", ctx->opts.order); return PC_EUNSUPPORTED;
+  if (ctx->lat) {
+    switch (ctx->opts.order) {
+      case 1: return recompute_k_t<1, true>(ctx, nb, m, X, sx, act, nchunk, chunk, part, dtype);
+      case 2: return recompute_k_t<2, true>(ctx, nb, m, X, sx, act, nchunk, chunk, part, dtype);
+      case 3: return recompute_k_t<3, true>(ctx, nb, m, X, sx, act, nchunk, chunk, part, dtype);
+      case 4: return recompute_k_t<4, true>(ctx, nb, m, X, sx, act, nchunk, chunk, part, dtype);
+      default: break;
+    }
+  } else {
+    switch (ctx->opts.order) {
+      case 2: return recompute_k_t<2, false>(ctx, nb, m, X, sx, act, nchunk, chunk, part, dtype);
+      case 3: return recompute_k_t<3, false>(ctx, nb, m, X, sx, act, nchunk, chunk, part, dtype);
+      case 4: return recompute_k_t<4, false>(ctx, nb, m, X, sx, act, nchunk, chunk, part, dtype);
+      default: break;
+    }
   }
+  set_error("stencil order %d is not implemented", ctx->opts.order);
+  return PC_EUNSUPPORTED;
 }
 
 }  // namespace pc

@@ -49,6 +49,7 @@ SIGNATURES = {
     "pc_destroy": (None, [_vp]),
     "pc_last_error": (C.c_char_p, []),
     "pc_eps_spheres": (_i, [_i, _i, _dp, _d, _dp]),
+    "pc_eps_spheres_lattice": (_i, [_i, _dp, _i, _dp, _d, _dp]),
     "pc_apply_op": (_i, [_vp, _i, _dp, _dp, _i, _i, _vp, _vp]),
     "pc_apply_half": (_i, [_vp, _i, _dp, _i, _vp, _vp, _vp]),
     "pc_recompute_norms": (_i, [_vp, _i, _dp, _i, _vp, _vp]),
@@ -150,17 +151,35 @@ def eps_spheres(N: int, spheres, eps_bg: float) -> np.ndarray:
     return out
 
 
-class Solver:
-    """One structure on one grid: pc_setup / pc_solve / pc_destroy and the step-level kernels."""
+def lattice_vectors(lattice) -> np.ndarray:
+    """The C layout of a lattice matrix A (columns a_1, a_2, a_3): a_1, a_2, a_3 one after the other."""
+    A = np.asarray(lattice, dtype=np.float64).reshape(3, 3)
+    return np.ascontiguousarray(A.T).ravel()
 
-    def __init__(self, N: int, eps_edges: np.ndarray, stream=None, **opts):
+
+def eps_spheres_lattice(N: int, lattice, spheres, eps_bg: float) -> np.ndarray:
+    """Permittivity at the edge DoFs of a general cell, host array (3, N, N, N) (pc_eps_spheres_lattice). ``lattice``
+    is A with the lattice vectors as columns; sphere centres and radii are Cartesian."""
+    sph = np.ascontiguousarray(np.asarray(spheres, dtype=np.float64).reshape(-1, 5))
+    lat = lattice_vectors(lattice)
+    out = np.empty((3, N, N, N), dtype=np.float64)
+    _check(lib().pc_eps_spheres_lattice(N, _dptr(lat), sph.shape[0], _dptr(sph) if sph.size else None,
+                                        float(eps_bg), _dptr(out)), "pc_eps_spheres_lattice")
+    return out
+
+
+class Solver:
+    """One structure on one grid: pc_setup / pc_solve / pc_destroy and the step-level kernels. ``lattice`` is the
+    matrix A whose columns are the lattice vectors (None: the unit cube)."""
+
+    def __init__(self, N: int, eps_edges: np.ndarray, stream=None, lattice=None, **opts):
         self.N = int(N)
         self.n = self.N ** 3
         eps = np.ascontiguousarray(np.asarray(eps_edges, dtype=np.float64).reshape(3, N, N, N))
         self.opts = default_opts(**opts)
         self._stream = _stream(stream)
         h = C.c_void_p()
-        lat = np.eye(3).ravel()
+        lat = lattice_vectors(np.eye(3) if lattice is None else lattice)
         _check(lib().pc_setup(C.byref(h), self.N, _dptr(eps), _dptr(lat), C.byref(self.opts), self._stream),
                "pc_setup")
         self._h = h

@@ -55,9 +55,9 @@ def test_opts_default_and_errors_without_gpu(libpath):
     eps[5] = -1.0
     rc = pc.lib().pc_setup(ctypes.byref(h), 8, pc._dptr(eps), None, None, None)
     assert rc == -1 and b"eps_edges" in pc.lib().pc_last_error()
-    lat = np.diag([1.0, 2.0, 1.0]).ravel()
+    lat = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [1.0, 1.0, 0.0]]).ravel()  # a3 = a1 + a2: a singular cell
     rc = pc.lib().pc_setup(ctypes.byref(h), 8, pc._dptr(np.ones(3 * 8 ** 3)), pc._dptr(lat), None, None)
-    assert rc == -2
+    assert rc == -1 and b"independent" in pc.lib().pc_last_error()
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
@@ -128,8 +128,12 @@ def test_setup_rejects_bad_arguments_on_the_host(libpath):
     import numpy as np
     rc, msg = _setup_rc(12)
     assert rc == -1 and "power of two" in msg
-    rc, msg = _setup_rc(8, lattice=np.diag([1.0, 1.0, 2.0]))
-    assert rc == -2 and "cubic" in msg
+    rc, msg = _setup_rc(8, lattice=np.diag([1.0, 1.0, 2.0]), precision=1)
+    assert rc == -2 and "cubic" in msg and "mixed" in msg
+    rc, msg = _setup_rc(8, lattice=[0.0, 0.5, 0.5, 0.5, 0.0, 0.5, 0.5, 0.5, 0.0 * np.nan])
+    assert rc == -1 and "finite" in msg
+    rc, msg = _setup_rc(8, lattice=[1.0, 2.0, 3.0, 2.0, 4.0, 6.0, 0.0, 0.0, 1.0])
+    assert rc == -1 and "independent" in msg
     rc, msg = _setup_rc(8, order=5)
     assert rc == -2 and "order" in msg
     rc, msg = _setup_rc(8, order=2, precision=1)
