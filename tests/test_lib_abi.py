@@ -142,3 +142,30 @@ def test_setup_rejects_bad_arguments_on_the_host(libpath):
     bad[1, 2, 3, 4] = 0.0
     rc, msg = _setup_rc(8, eps=bad)
     assert rc == -1 and "eps_edges" in msg
+
+
+def test_eps_spheres_lattice_rejects_bad_arguments_on_the_host(libpath):
+    """pc_eps_spheres_lattice validates the cell and the spheres before any CUDA call."""
+    import numpy as np
+
+    from paper_2503_19379_gb300 import pc
+    out = np.empty((3, 8, 8, 8))
+    sph = np.array([[0.0, 0.0, 0.0, 0.2, 13.0]])
+    L = pc.lib()
+    flat = np.array([1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 1.0, 1.0, 0.0])  # a3 = a1 + a2
+    assert L.pc_eps_spheres_lattice(8, pc._dptr(flat), 1, pc._dptr(sph), 1.0, pc._dptr(out)) == -1
+    assert b"independent" in L.pc_last_error()
+    bad = np.array([[0.0, 0.0, 0.0, 0.2, -1.0]])
+    eye = np.eye(3).ravel()
+    assert L.pc_eps_spheres_lattice(8, pc._dptr(eye), 1, pc._dptr(bad), 1.0, pc._dptr(out)) == -1
+    assert L.pc_eps_spheres_lattice(8, None, 1, pc._dptr(sph), 1.0, pc._dptr(out)) == -1
+
+
+def test_lattice_vectors_layout():
+    """The binding passes a_1, a_2, a_3 one after the other: the columns of A, as pc_setup documents."""
+    import numpy as np
+
+    from paper_2503_19379_gb300 import pc
+    A = np.array([[1.0, 2.0, 3.0], [4.0, 5.0, 6.0], [7.0, 8.0, 10.0]])
+    v = pc.lattice_vectors(A)
+    assert np.array_equal(v[0:3], A[:, 0]) and np.array_equal(v[3:6], A[:, 1]) and np.array_equal(v[6:9], A[:, 2])
