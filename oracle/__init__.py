@@ -19,6 +19,8 @@ Modules and what each one follows:
                    recompute check (Algorithm 4.1) and the k = 0 treatment (Remark after eq. penalised_marix).
 * general lattices -- ``mfd``, ``spectrum``, ``precond`` and ``geometry`` take an optional ``lattice`` A (Section 2's
                    coordinate change, Section 4.2.2: K_hat_i = sum_j b_ji K_j with b = A^{-1}).
+* ``warmstart`` -- the learned warm start's network (no counterpart in the paper, whose LOBPCG starts from a random
+                   block): forward and hand-derived backward of each layer, the subspace loss, Adam.
 * ``rng``       -- the counter-based generator that seeds initial blocks (splitmix64 finaliser + Box-Muller).
 
 Every function states the passage it follows. Pins for each function live in ``tests/test_oracle_*.py``.
