@@ -264,6 +264,53 @@ int pc_residual(int nb, long L, int m, const void *X, const void *AX, const doub
  * (splitmix64 output function + Box-Muller; see the oracle's rng module for the definition). Device PC_C128. */
 int pc_init_block(int nb, long L, int m, uint64_t seed, int kidx0, void *X, void *stream);
 
+/* ---------------- learned warm start (no counterpart in the paper; its LOBPCG starts from a random block) -------
+ * A 3D convolutional network over M0 = 1/eps, conditioned on k, predicts an initial block X0 of nb face fields and
+ * guesses y of log lambda for nb bands: conv 3 -> PC_WS_C1 and PC_WS_C1 -> PC_WS_C2 channels (3x3x3, stride 2,
+ * circular padding, bias, ReLU), FiLM from phi(k) = (sin k, cos k), a 1x1x1 head to 6 nb channels at (N/4)^3,
+ * periodic linear upsampling x4 per axis; value head y = Wv [mean z; phi] + bv. Trained by the subspace loss
+ * nb - tr(G^-1 B B^H), G = X^H X, B = X^H V, against eigenvectors V of converged solves, plus w_val (y - log lambda)^2.
+ * All network arithmetic is FP32; the Grams accumulate in FP64.
+ * Parameters: one flat device float array of pc_ws_param_count(nb) entries in the order W1 (C1,3,3,3,3), b1,
+ * W2 (C2,C1,3,3,3), b2, Fa (C2,6), fa, Fc (C2,6), fc, Wh (6 nb, C2), bh, Wv (nb, C2 + 6), bv, each row-major.
+ * Sizes: N a power of two in [16, 256]; 1 <= nb <= 16; 1 <= S <= 65535 samples per call. */
+#define PC_WS_C1 8
+#define PC_WS_C2 16
+
+/* Number of floats in the parameter array for nb bands (-1 if nb is out of range). Host only. */
+long pc_ws_param_count(int nb);
+
+/* Bytes of the device workspace that pc_ws_forward and pc_ws_backward share for S samples (0 if out of range). */
+size_t pc_ws_work_bytes(int N, int nb, int S);
+
+/* Forward pass for S samples.
+ *   params: device float [pc_ws_param_count(nb)].
+ *   m0:     device float [nstruct][3][N][N][N], M0 = 1/eps at the edge DoFs of each structure.
+ *   sidx:   device int [S], the structure of each sample.
+ *   kpts:   host double [S][3], the Bloch vector of each sample.
+ *   X:      device complex64 [S][nb][3][N][N][N] (out): the predicted block of each sample.
+ *   y:      device float [S][nb] (out): the guesses of log lambda.
+ *   work:   device buffer of pc_ws_work_bytes(N, nb, S) bytes; keeps the activations for pc_ws_backward.
+ * Synchronous on stream. */
+int pc_ws_forward(int N, int nb, int S, const float *params, const float *m0, const int *sidx, const double *kpts,
+                  void *X, float *y, void *work, void *stream);
+
+/* Loss and gradient for the S samples of the preceding pc_ws_forward call with the same work buffer and inputs.
+ *   V:     device complex64 [S][nb][3][N][N][N], orthonormal eigenvectors of each sample's converged solve.
+ *   lam:   device double [S][nb], the eigenvalues (> 0).
+ *   grad:  device float [pc_ws_param_count(nb)] (out): the gradient of the mean loss over the S samples.
+ *   loss:  device double [S] (out): each sample's loss (NaN where X^H X was not positive definite; that sample
+ *          then adds no gradient).
+ * Enqueued on stream; returns before completion. */
+int pc_ws_backward(int N, int nb, int S, const float *params, const float *m0, const int *sidx, const void *X,
+                   const float *y, const void *V, const double *lam, float w_val, float *grad, double *loss,
+                   void *work, void *stream);
+
+/* One Adam step (Kingma and Ba) on P parameters in place: m, v device float [P] moments (zero before step t = 1),
+ * t the 1-based step count for the bias corrections. Enqueued on stream. */
+int pc_ws_adam(long P, float *params, const float *grad, float *m, float *v, int t, float lr, float b1, float b2,
+               float eps, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

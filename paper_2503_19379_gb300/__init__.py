@@ -6,8 +6,9 @@ tensors for device buffers) and raises on any library error. There is no CPU fal
 without a built library raises.
 """
 from .pc import (PCError, Solver, block_update, eigh_batched, eps_spheres, eps_spheres_lattice, gram, gram_pair,
-                 gram_pair_coupled, init_block, lattice_vectors, lib, rayleigh_ritz, residual, stencil_coefficients)
+                 gram_pair_coupled, init_block, lattice_vectors, lib, rayleigh_ritz, residual, stencil_coefficients,
+                 WarmStart)
 
 __all__ = ["PCError", "Solver", "block_update", "eigh_batched", "eps_spheres", "eps_spheres_lattice", "gram",
            "gram_pair", "gram_pair_coupled", "init_block", "lattice_vectors", "lib", "rayleigh_ritz", "residual",
-           "stencil_coefficients"]
+           "stencil_coefficients", "WarmStart"]

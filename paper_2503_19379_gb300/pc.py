@@ -67,6 +67,11 @@ SIGNATURES = {
     "pc_set_timing": (_i, [_vp, _i]),
     "pc_get_stats": (_i, [_vp, C.POINTER(StageStat)]),
     "pc_reset_stats": (_i, [_vp]),
+    "pc_ws_param_count": (_l, [_i]),
+    "pc_ws_work_bytes": (C.c_size_t, [_i, _i, _i]),
+    "pc_ws_forward": (_i, [_i, _i, _i, _vp, _vp, _vp, _dp, _vp, _vp, _vp, _vp]),
+    "pc_ws_backward": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp]),
+    "pc_ws_adam": (_i, [_l, _vp, _vp, _vp, _vp, _i, C.c_float, C.c_float, C.c_float, C.c_float, _vp]),
 }
 
 
@@ -356,3 +361,53 @@ def init_block(nb: int, L: int, m: int, seed: int, kidx0: int = 0, stream=None):
     X = torch.empty((nb, m, L), dtype=torch.complex128, device="cuda")
     _check(lib().pc_init_block(nb, L, m, seed, kidx0, _dev(X), _stream(stream)), "pc_init_block")
     return X
+
+
+class WarmStart:
+    """The learned warm start's network on the device (pc_ws_*): forward, backward and Adam over a flat float32
+    parameter tensor. Tensors are torch CUDA tensors; m0 is float32 [nstruct][3][N][N][N], sidx int32 [S]."""
+
+    def __init__(self, N: int, nb: int, S: int, params=None, stream=None):
+        torch = _torch()
+        self.N, self.nb, self.S = int(N), int(nb), int(S)
+        self.P = int(lib().pc_ws_param_count(self.nb))
+        if self.P <= 0:
+            raise PCError(f"pc_ws_param_count: nb = {nb} out of range")
+        wb = int(lib().pc_ws_work_bytes(self.N, self.nb, self.S))
+        if wb == 0:
+            raise PCError(f"pc_ws_work_bytes: N = {N}, nb = {nb}, S = {S} out of range")
+        self.work = torch.empty(wb, dtype=torch.uint8, device="cuda")
+        self.params = (torch.zeros(self.P, dtype=torch.float32, device="cuda") if params is None
+                       else params.to(device="cuda", dtype=torch.float32).contiguous())
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.t = 0
+        self._stream = _stream(stream)
+
+    def forward(self, m0, sidx, kpts):
+        """(X [S][nb][3][N][N][N] complex64, y [S][nb] float32) for the S samples."""
+        torch = _torch()
+        k = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(self.S, 3))
+        X = torch.empty((self.S, self.nb, 3, self.N, self.N, self.N), dtype=torch.complex64, device="cuda")
+        y = torch.empty((self.S, self.nb), dtype=torch.float32, device="cuda")
+        _check(lib().pc_ws_forward(self.N, self.nb, self.S, _dev(self.params, [torch.float32]),
+                                   _dev(m0, [torch.float32]), _dev(sidx, [torch.int32]), _dptr(k), _dev(X), _dev(y),
+                                   _dev(self.work), self._stream), "pc_ws_forward")
+        return X, y
+
+    def backward(self, m0, sidx, X, y, V, lam, w_val: float = 0.1):
+        """(grad [P] float32, loss [S] float64) for the samples of the preceding forward."""
+        torch = _torch()
+        grad = torch.empty_like(self.params)
+        loss = torch.empty(self.S, dtype=torch.float64, device="cuda")
+        _check(lib().pc_ws_backward(self.N, self.nb, self.S, _dev(self.params, [torch.float32]),
+                                    _dev(m0, [torch.float32]), _dev(sidx, [torch.int32]), _dev(X, [torch.complex64]),
+                                    _dev(y, [torch.float32]), _dev(V, [torch.complex64]), _dev(lam, [torch.float64]),
+                                    float(w_val), _dev(grad), _dev(loss), _dev(self.work), self._stream),
+               "pc_ws_backward")
+        return grad, loss
+
+    def adam(self, grad, lr: float = 1e-3, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+        self.t += 1
+        _check(lib().pc_ws_adam(self.P, _dev(self.params), _dev(grad), _dev(self.m), _dev(self.v), self.t, float(lr),
+                                float(b1), float(b2), float(eps), self._stream), "pc_ws_adam")

@@ -169,3 +169,28 @@ def test_lattice_vectors_layout():
     A = np.array([[1.0, 2.0, 3.0], [4.0, 5.0, 6.0], [7.0, 8.0, 10.0]])
     v = pc.lattice_vectors(A)
     assert np.array_equal(v[0:3], A[:, 0]) and np.array_equal(v[3:6], A[:, 1]) and np.array_equal(v[6:9], A[:, 2])
+
+
+def test_warm_start_host_entry_points(libpath):
+    """The warm start's parameter count equals the oracle's model, the workspace size is positive, and bad sizes are
+    rejected before any CUDA call."""
+    import ctypes as C
+
+    import numpy as np
+
+    from oracle import warmstart as ws
+    from paper_2503_19379_gb300 import pc
+    L = pc.lib()
+    for nb in (1, 8, 16):
+        p = ws.init_params(8, 16, nb)
+        assert L.pc_ws_param_count(nb) == sum(v.size for v in p.values())
+    assert L.pc_ws_param_count(0) == -1 and L.pc_ws_param_count(17) == -1
+    assert L.pc_ws_work_bytes(32, 8, 4) > 0 and L.pc_ws_work_bytes(12, 8, 4) == 0
+    k = np.zeros(3)
+    rc = L.pc_ws_forward(12, 8, 1, None, None, None, pc._dptr(k), None, None, None, None)
+    assert rc == -1 and b"power of two" in L.pc_last_error()
+    rc = L.pc_ws_forward(32, 8, 1, None, None, None, pc._dptr(k), None, None, None, None)
+    assert rc == -1 and b"null" in L.pc_last_error()
+    rc = L.pc_ws_adam(4, None, None, None, None, 1, C.c_float(1e-3), C.c_float(0.9), C.c_float(0.999),
+                      C.c_float(1e-8), None)
+    assert rc == -1
