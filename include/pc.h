@@ -114,6 +114,14 @@ int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, double tol, do
              int *iters, double *resid);
 
 /* Release a context and its device memory (never caller memory). NULL is allowed. */
+/* pc_solve_init -- pc_solve from a caller-provided initial block: the first n0 columns of each k-point's starting
+ * block are X0 (the learned warm start's prediction, or the eigenvectors of a neighbouring k-point), the remaining
+ * columns are the counter-based random fields of pc_solve. At k = 0 the constant fields are projected out of X0 as
+ * well. The paper's LOBPCG starts from a random block; this entry point has no counterpart there.
+ *   X0: device complex64 [nk][n0][3][N][N][N]; 1 <= n0 <= nbands. Other arguments and results as pc_solve. */
+int pc_solve_init(pc_ctx *ctx, int nk, const double *kpts, int nbands, double tol, const void *X0, int n0,
+                  double *evals, void *evecs, int *iters, double *resid);
+
 void pc_destroy(pc_ctx *ctx);
 
 /* Thread-local description of the last error ("" if none). */

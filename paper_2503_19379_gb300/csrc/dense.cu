@@ -450,6 +450,32 @@ int launch_block_update(int nb, long L, int p, int q, int dtype, const void *S, 
   return PC_OK;
 }
 
+// ------------------------------------------------------------------------------------------------ initial block input
+// complex64 -> complex128 copy of the first q columns (q L entries) of k-points b0 + blockIdx.y
+__global__ void __launch_bounds__(256) copy_x0_kernel(const float2 *__restrict__ X0, long qL, int b0,
+                                                      double2 *__restrict__ X, long sx) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= qL) return;
+  const long b = b0 + blockIdx.y;
+  const float2 v = X0[b * qL + i];
+  X[b * sx + i] = make_double2((double)v.x, (double)v.y);
+}
+
+int launch_copy_x0(const pc_ctx *ctx, int b0, int nbk, int dtype, void *X, long sx, cudaStream_t st) {
+  if (!ctx->x0 || nbk == 0 || ctx->x0n == 0) return PC_OK;
+  const long qL = (long)ctx->x0n * 3 * ctx->n;
+  const float2 *src = static_cast<const float2 *>(ctx->x0);
+  if (dtype == PC_C64) {
+    // one strided copy: nbk rows of qL complex64 entries, source pitch qL, destination pitch sx
+    PC_CK(cudaMemcpy2DAsync(static_cast<float2 *>(X) + (long)b0 * sx, sizeof(float2) * sx, src + (long)b0 * qL,
+                            sizeof(float2) * qL, sizeof(float2) * qL, nbk, cudaMemcpyDeviceToDevice, st));
+    return PC_OK;
+  }
+  copy_x0_kernel<<<dim3((unsigned)((qL + 255) / 256), nbk), 256, 0, st>>>(src, qL, b0, static_cast<double2 *>(X), sx);
+  PC_CK_LAUNCH();
+  return PC_OK;
+}
+
 // ------------------------------------------------------------------------------------------------ residual
 __global__ void __launch_bounds__(256) residual_partial_kernel(const double2 *__restrict__ X, long sx,
                                                               const double2 *__restrict__ AX, long sax,

@@ -117,6 +117,9 @@ struct pc_ctx {
   // general lattice (Section 2's coordinate change x = A y, Section 4.2.2): lat is set when A is not the identity;
   // binv = A^{-1} row-major (binv[3 * i + j] = b_ij), amat = A row-major (amat[3 * i + j] = a_j component i)
   bool lat = false;
+  // caller-provided initial block of pc_solve_init: device complex64 [nk][x0n][3][N][N][N], or null
+  const void *x0 = nullptr;
+  int x0n = 0;
   double binv[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   double amat[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   pc::DevBuf m0d, m0f;      // M0 diagonal, double and float copies, [3][N^3]
@@ -272,6 +275,9 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
 // counter-based initial columns; with mask (int [nb][m]) only the flagged columns of the act k-points are written
 // X: dtype PC_C128, PC_DFS (the same FP64 values stored as double-float pairs) or PC_C64 (the same uniforms, the
 // normal deviates formed in FP32)
+// the caller's initial block (ctx->x0, complex64) into the first ctx->x0n columns of the panels of k-points
+// b0 .. b0 + nbk - 1 at X + b * sx (dtype PC_C128 or PC_C64 panels; sx in elements)
+int launch_copy_x0(const pc_ctx *ctx, int b0, int nbk, int dtype, void *X, long sx, cudaStream_t st);
 int launch_init_block(int nb, long L, int m, uint64_t seed, int kidx0, void *X, long sx, cudaStream_t st,
                       const int *mask = nullptr, const int *act = nullptr, int dtype = PC_C128);
 // Algorithm 4.1 restart: flags (host, [nb][m]) the columns of the redo k-points to replace before the re-solve

@@ -469,6 +469,7 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
   const int na0 = (int)act.size();
   RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, Ld * cb * m * nb,
                 [&] { return launch_init_block(nb, L, m, ctx->opts.seed, 0, S[0], sS, st); }));
+  if (ctx->x0) RUN(launch_copy_x0(ctx, 0, nb, PC_C128, S[0], sS, st));
   if (any_zero) RUN(DEFL(na0, S[0]));
   RUN(OP(na0, S[0], AS[0]));
   RUN(GRAM(na0, m, S[0], AS[0]));
@@ -621,4 +622,16 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
   if (iters)
     for (int b = 0; b < nb; ++b) iters[b] = itcount[b];
   return status;
+}
+
+extern "C" int pc_solve_init(pc_ctx *ctx, int nk, const double *kpts, int nbands, double tol, const void *X0, int n0,
+                             double *evals, void *evecs, int *iters, double *resid) {
+  PC_REQUIRE(ctx && X0, "pc_solve_init: null argument");
+  PC_REQUIRE(n0 >= 1 && n0 <= nbands, "pc_solve_init: need 1 <= n0 <= nbands, got n0 = %d", n0);
+  ctx->x0 = X0;
+  ctx->x0n = n0;
+  const int rc = pc_solve(ctx, nk, kpts, nbands, tol, evals, evecs, iters, resid);
+  ctx->x0 = nullptr;
+  ctx->x0n = 0;
+  return rc;
 }

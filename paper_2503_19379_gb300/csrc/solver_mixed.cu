@@ -164,6 +164,7 @@ class MixedSolve {
     RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, S.Ld * 8.0 * m * na, [&] {
       return launch_init_block(na, L, m, ctx->opts.seed, 0, S.F[0], sF, g.st, nullptr, g.d_act, PC_C64);
     }));
+    if (ctx->x0) RUN(launch_copy_x0(ctx, g.b0, na, PC_C64, S.F[0], sF, g.st));
     RUN(DEFL(g.act, S.F[0], sF, PC_C64));
     RUN(OP32(na, m, S.F[0], sF, S.AF[0], sF));
     RUN(run_stage(ctx, PC_STAGE_GRAM, 2, 8.0 * m * (m + 1) * S.Ld * na, 2.0 * m * S.Ld * 8.0 * na, [&] {

@@ -46,6 +46,7 @@ SIGNATURES = {
     "pc_opts_default": (_i, [C.POINTER(Opts)]),
     "pc_setup": (_i, [C.POINTER(_vp), _i, _dp, _dp, C.POINTER(Opts), _vp]),
     "pc_solve": (_i, [_vp, _i, _dp, _i, _d, _dp, _vp, _ip, _dp]),
+    "pc_solve_init": (_i, [_vp, _i, _dp, _i, _d, _vp, _i, _dp, _vp, _ip, _dp]),
     "pc_destroy": (None, [_vp]),
     "pc_last_error": (C.c_char_p, []),
     "pc_eps_spheres": (_i, [_i, _i, _dp, _d, _dp]),
@@ -200,8 +201,9 @@ class Solver:
         except Exception:
             pass
 
-    def solve(self, kpts, nbands: int, tol: float, want_vectors: bool = False):
-        """pc_solve; returns dict(evals, iters, resid, status[, evecs (torch complex128 on the device)])."""
+    def solve(self, kpts, nbands: int, tol: float, want_vectors: bool = False, x0=None):
+        """pc_solve (pc_solve_init when x0, a torch complex64 CUDA tensor [nk][n0][3][N][N][N], gives the first n0
+        columns of the initial block); returns dict(evals, iters, resid, status[, evecs (torch complex128)])."""
         k = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
         nk = k.shape[0]
         evals = np.zeros((nk, nbands))
@@ -211,8 +213,16 @@ class Solver:
         if want_vectors:
             torch = _torch()
             evecs = torch.empty((nk, nbands, 3, self.N, self.N, self.N), dtype=torch.complex128, device="cuda")
-        rc = lib().pc_solve(self._h, nk, _dptr(k), nbands, float(tol), _dptr(evals),
-                            _dev(evecs) if evecs is not None else None, iters.ctypes.data_as(_ip), _dptr(resid))
+        ev = _dev(evecs) if evecs is not None else None
+        if x0 is None:
+            rc = lib().pc_solve(self._h, nk, _dptr(k), nbands, float(tol), _dptr(evals), ev,
+                                iters.ctypes.data_as(_ip), _dptr(resid))
+        else:
+            torch = _torch()
+            if tuple(x0.shape[:1]) != (nk,) or tuple(x0.shape[2:]) != (3, self.N, self.N, self.N):
+                raise PCError("x0 must have shape [nk][n0][3][N][N][N]")
+            rc = lib().pc_solve_init(self._h, nk, _dptr(k), nbands, float(tol), _dev(x0, [torch.complex64]),
+                                     int(x0.shape[1]), _dptr(evals), ev, iters.ctypes.data_as(_ip), _dptr(resid))
         _check(rc, "pc_solve", warn_ok=True)
         out = {"evals": evals, "iters": iters, "resid": resid, "status": rc}
         if evecs is not None:

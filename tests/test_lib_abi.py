@@ -194,3 +194,13 @@ def test_warm_start_host_entry_points(libpath):
     rc = L.pc_ws_adam(4, None, None, None, None, 1, C.c_float(1e-3), C.c_float(0.9), C.c_float(0.999),
                       C.c_float(1e-8), None)
     assert rc == -1
+
+
+def test_solve_init_rejects_null_arguments_on_the_host(libpath):
+    import numpy as np
+
+    from paper_2503_19379_gb300 import pc
+    k = np.zeros(3)
+    ev = np.zeros(4)
+    rc = pc.lib().pc_solve_init(None, 1, pc._dptr(k), 4, 1e-6, None, 2, pc._dptr(ev), None, None, None)
+    assert rc == -1 and b"null" in pc.lib().pc_last_error()
