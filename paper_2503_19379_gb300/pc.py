@@ -16,6 +16,7 @@ LIBPATH = os.path.join(HERE, "libpc.so")
 PC_C128, PC_C64, PC_C128_DF = 0, 1, 2
 PC_PRECOND_GAMMA, PC_PRECOND_LAPLACIAN = 0, 1
 PC_PREC_FP64, PC_PREC_MIXED = 0, 1
+PC_WS_C1, PC_WS_C2 = 8, 16  # warm-start encoder channels (include/pc.h)
 PC_NOT_CONVERGED, PC_SPURIOUS = 1, 2
 
 

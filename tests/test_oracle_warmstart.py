@@ -186,3 +186,18 @@ def test_planted_backward_mistake_is_caught(monkeypatch):
         return du, dW, dout.sum(axis=(1, 2, 3))
     monkeypatch.setattr(ws, "conv_s2_backward", wrong)
     assert fd_check(small_params(), random_sample(), "W1") > 1e-3
+
+
+def test_library_initial_parameters_follow_the_reference_layout():
+    """The training driver's flat initial parameters have the library's count and the reference's layout: FiLM at
+    the identity and zero biases, so the first forward pass of both starts from the same kind of model."""
+    from paper_2503_19379_gb300 import warmstart as lws
+    flat = lws.init_params(8, seed=3)
+    ref = ws.init_params(8, 16, 8, 3)
+    assert flat.size == sum(v.size for v in ref.values())
+    off = 0
+    for k in ws.PARAM_ORDER:
+        part = flat[off:off + ref[k].size]
+        if k[0] in "bf" or k in ("Fa", "Fc"):
+            assert np.all(part == 0.0), k
+        off += ref[k].size
