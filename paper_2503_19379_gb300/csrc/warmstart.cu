@@ -53,7 +53,7 @@ Offs offsets(int nb) {
 
 // device workspace of one forward + backward pass over S samples (offsets in bytes, 256-aligned)
 struct Work {
-  size_t phi, a1, a2, z, pool, y, coarse, G, B, Cx, Cv, dX, dcoarse, dz, da2, da1, dsa, dsc, loss, gram, total;
+  size_t phi, a1, a2, z, pool, dy, coarse, G, B, Cx, Cv, dX, dcoarse, dz, da2, da1, dsa, dsc, loss, gram, total;
 };
 
 Work work_layout(int N, int nb, int S) {
@@ -71,7 +71,7 @@ Work work_layout(int N, int nb, int S) {
   w.a2 = take(sizeof(float) * (size_t)S * C2 * m3);
   w.z = take(sizeof(float) * (size_t)S * C2 * m3);
   w.pool = take(sizeof(float) * (size_t)S * C2);
-  w.y = take(sizeof(float) * (size_t)S * nb);
+  w.dy = take(sizeof(float) * (size_t)S * nb);
   w.coarse = take(sizeof(float2) * (size_t)S * nb * 3 * m3);
   w.G = take(sizeof(double2) * (size_t)S * nb * nb);
   w.B = take(sizeof(double2) * (size_t)S * nb * nb);
@@ -686,7 +686,7 @@ extern "C" int pc_ws_backward(int N, int nb, int S, const float *params, const f
   const float *dphi = reinterpret_cast<const float *>(wp(work, w.phi));
   float *a1 = reinterpret_cast<float *>(wp(work, w.a1)), *a2 = reinterpret_cast<float *>(wp(work, w.a2));
   float *z = reinterpret_cast<float *>(wp(work, w.z)), *pool = reinterpret_cast<float *>(wp(work, w.pool));
-  float *dy = reinterpret_cast<float *>(wp(work, w.y));
+  float *dy = reinterpret_cast<float *>(wp(work, w.dy));
   double2 *G = reinterpret_cast<double2 *>(wp(work, w.G)), *B = reinterpret_cast<double2 *>(wp(work, w.B));
   double2 *Cx = reinterpret_cast<double2 *>(wp(work, w.Cx)), *Cv = reinterpret_cast<double2 *>(wp(work, w.Cv));
   float2 *dX = reinterpret_cast<float2 *>(wp(work, w.dX)), *dc = reinterpret_cast<float2 *>(wp(work, w.dcoarse));
