@@ -13,7 +13,7 @@ Modules and what each one follows:
 * ``spectrum``  -- the exact discrete spectrum for a homogeneous permittivity, derived from the circulant symbols
                    (Section 5.2, eq. diag_of_circ) together with Proposition 3.1.
 * ``geometry``  -- M0 from a sphere structure: inverse permittivity at edge midpoints with the interface rule
-                   (Section 4.4).
+                   (Section 4.4); the BCC gyroid and the FCC diamond of Section 6.3.
 * ``precond``   -- the FFT preconditioner solve (Algorithm 5.1 with the 3x3 symbol of eq. penalised_marix).
 * ``eigs``      -- dense / shift-invert reference eigenpairs, an independent block LOBPCG (Section 5.1), the
                    recompute check (Algorithm 4.1) and the k = 0 treatment (Remark after eq. penalised_marix).
