@@ -179,6 +179,20 @@ int pc_eps_spheres(int N, int nsph, const double *spheres, double eps_bg, double
 int pc_eps_spheres_lattice(int N, const double *lattice, int nsph, const double *spheres, double eps_bg,
                            double *eps_out);
 
+/* a0 for the structures of Section 6.3 on a general cell (lattice as in pc_setup; eps_out host [3][N][N][N] at the
+ * Cartesian points A y of the edge midpoints y). Each runs a device kernel; synchronous.
+ * pc_eps_gyroid: the single gyroid {g > threshold} with g = sin(2 pi x/l) cos(2 pi y/l) + sin(2 pi y/l) cos(2 pi z/l)
+ *   + sin(2 pi z/l) cos(2 pi x/l) (Section 6.3: threshold 1.1, eps_in 16, in the BCC lattice of constant l); the
+ *   strict inequality decides every point.
+ * pc_eps_diamond: the FCC diamond: spheres of radius r l at (0,0,0) and (l/4)(1,1,1), and one spheroid per bond
+ *   (l/4)(1,1,1), (l/4)(1,-1,-1), (l/4)(-1,1,-1), (l/4)(-1,-1,1) from the origin with foci at the bond's ends and
+ *   minor axis of full length b l (Section 6.3: r = 0.12, b = 0.11, eps_in 13); closed sets, periodic images by the
+ *   nearest-image search of pc_eps_spheres_lattice. */
+int pc_eps_gyroid(int N, const double *lattice, double l, double threshold, double eps_in, double eps_bg,
+                  double *eps_out);
+int pc_eps_diamond(int N, const double *lattice, double l, double r, double b, double eps_in, double eps_bg,
+                   double *eps_out);
+
 /* a1: Y = Op X = A M0 A' X + gamma B'B X for nb k-points x m fields (eq. Ker_comp; stencils of Section 4.1.2,
  * of the context's order: Table 1's 2k-th order schemes).
  *   kpts: host [nb][3] (used as given, no zone reduction); gammas: host [nb].

@@ -52,6 +52,8 @@ SIGNATURES = {
     "pc_last_error": (C.c_char_p, []),
     "pc_eps_spheres": (_i, [_i, _i, _dp, _d, _dp]),
     "pc_eps_spheres_lattice": (_i, [_i, _dp, _i, _dp, _d, _dp]),
+    "pc_eps_gyroid": (_i, [_i, _dp, _d, _d, _d, _d, _dp]),
+    "pc_eps_diamond": (_i, [_i, _dp, _d, _d, _d, _d, _d, _dp]),
     "pc_apply_op": (_i, [_vp, _i, _dp, _dp, _i, _i, _vp, _vp]),
     "pc_apply_half": (_i, [_vp, _i, _dp, _i, _vp, _vp, _vp]),
     "pc_recompute_norms": (_i, [_vp, _i, _dp, _i, _vp, _vp]),
@@ -172,6 +174,25 @@ def eps_spheres_lattice(N: int, lattice, spheres, eps_bg: float) -> np.ndarray:
     out = np.empty((3, N, N, N), dtype=np.float64)
     _check(lib().pc_eps_spheres_lattice(N, _dptr(lat), sph.shape[0], _dptr(sph) if sph.size else None,
                                         float(eps_bg), _dptr(out)), "pc_eps_spheres_lattice")
+    return out
+
+
+def eps_gyroid(N: int, lattice, l: float = 1.0, threshold: float = 1.1, eps_in: float = 16.0,
+               eps_bg: float = 1.0) -> np.ndarray:
+    """Permittivity at the edge DoFs of the single gyroid (Section 6.3) on the cell A (pc_eps_gyroid)."""
+    out = np.empty((3, N, N, N), dtype=np.float64)
+    _check(lib().pc_eps_gyroid(N, _dptr(lattice_vectors(lattice)), float(l), float(threshold), float(eps_in),
+                               float(eps_bg), _dptr(out)), "pc_eps_gyroid")
+    return out
+
+
+def eps_diamond(N: int, lattice, l: float = 1.0, r: float = 0.12, b: float = 0.11, eps_in: float = 13.0,
+                eps_bg: float = 1.0) -> np.ndarray:
+    """Permittivity at the edge DoFs of the diamond of spheres and spheroids (Section 6.3) on the cell A
+    (pc_eps_diamond)."""
+    out = np.empty((3, N, N, N), dtype=np.float64)
+    _check(lib().pc_eps_diamond(N, _dptr(lattice_vectors(lattice)), float(l), float(r), float(b), float(eps_in),
+                                float(eps_bg), _dptr(out)), "pc_eps_diamond")
     return out
 
 

@@ -204,3 +204,17 @@ def test_solve_init_rejects_null_arguments_on_the_host(libpath):
     ev = np.zeros(4)
     rc = pc.lib().pc_solve_init(None, 1, pc._dptr(k), 4, 1e-6, None, 2, pc._dptr(ev), None, None, None)
     assert rc == -1 and b"null" in pc.lib().pc_last_error()
+
+
+def test_structure_entry_points_reject_bad_arguments_on_the_host(libpath):
+    import numpy as np
+
+    from paper_2503_19379_gb300 import pc
+    L = pc.lib()
+    out = np.empty((3, 8, 8, 8))
+    flat = np.array([1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 1.0, 1.0, 0.0])
+    assert L.pc_eps_gyroid(8, pc._dptr(flat), 1.0, 1.1, 16.0, 1.0, pc._dptr(out)) == -1
+    assert L.pc_eps_diamond(8, pc._dptr(flat), 1.0, 0.12, 0.11, 13.0, 1.0, pc._dptr(out)) == -1
+    eye = np.eye(3).ravel()
+    assert L.pc_eps_gyroid(8, pc._dptr(eye), -1.0, 1.1, 16.0, 1.0, pc._dptr(out)) == -1
+    assert L.pc_eps_diamond(8, pc._dptr(eye), 1.0, -0.1, 0.11, 13.0, 1.0, pc._dptr(out)) == -1
