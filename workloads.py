@@ -143,3 +143,28 @@ def workload_fcc_128(npts: int = 64) -> Workload:
     """FCC spheres eps=13, N=128, 16 bands, 64 k-points, complex64 search space with FP64 Rayleigh-Ritz."""
     return Workload("fcc-spheres-N128", fcc_spheres(), 128, kpath(FCC_PATH, FCC_POINTS, npts), 16, 1e-6, "mixed")
 
+
+
+# ------------------------------------------------------------------------------------------ the paper's own cells
+# Section 6's translation vectors (lattice constant l = 1) as the columns of A, and the timing setting of its BCC
+# and FCC tables: the first 10 eigenvalues at k = (pi, pi, pi) / l. The structures themselves (the single gyroid and
+# the diamond of spheres and spheroids) are sampled by each side's own geometry code; a workload only names them.
+SC_CELL = np.eye(3)
+FCC_CELL = 0.5 * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
+BCC_CELL = 0.5 * np.array([[-1.0, 1.0, 1.0], [1.0, -1.0, 1.0], [1.0, 1.0, -1.0]])
+
+
+def workload_bcc_gyroid(N: int = 128) -> Workload:
+    """BCC single gyroid {g > 1.1}, eps 16 in air, on the BCC primitive cell at N (power of two; the paper's timing
+    table uses N = 100, 120, 150), 10 bands at k = (pi, pi, pi), tol 1e-6."""
+    s = Structure((), 1.0, "bcc-gyroid")
+    return Workload(f"bcc-gyroid-N{N}", s, N, np.array([[PI, PI, PI]]), 10, 1e-6,
+                    extra={"lattice": BCC_CELL, "geometry": "gyroid", "threshold": 1.1, "eps_in": 16.0})
+
+
+def workload_fcc_diamond(N: int = 128) -> Workload:
+    """FCC diamond of spheres (r = 0.12) and bond spheroids (minor axis 0.11), eps 13 in air, on the FCC primitive
+    cell at N, 10 bands at k = (pi, pi, pi), tol 1e-6."""
+    s = Structure((), 1.0, "fcc-diamond")
+    return Workload(f"fcc-diamond-N{N}", s, N, np.array([[PI, PI, PI]]), 10, 1e-6,
+                    extra={"lattice": FCC_CELL, "geometry": "diamond", "r": 0.12, "b": 0.11, "eps_in": 13.0})
