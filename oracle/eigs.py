@@ -34,6 +34,19 @@ def reduce_to_first_zone(kvec, a: float = 1.0) -> np.ndarray:
     return k - g * np.round(k / g)
 
 
+def reduce_by_reciprocal_lattice(kvec, lattice) -> np.ndarray:
+    """k - 2 pi A^{-T} n with n = round(A^T k / 2 pi): the Bloch vector moved by the nearest reciprocal-lattice vector
+    of the cell A in fractional coordinates (the cube's reduction for A = a I); a k whose fractional coordinates are
+    all within 1e-12 of integers is equivalent to 0 and becomes exactly 0 (Section 2: k is taken in one zone)."""
+    k = np.asarray(kvec, dtype=np.float64)
+    A = np.asarray(lattice, dtype=np.float64)
+    f = A.T @ k / (2.0 * np.pi)
+    n = np.round(f)
+    if np.all(np.abs(f - n) <= 1e-12):
+        return np.zeros(3)
+    return k - 2.0 * np.pi * np.linalg.solve(A.T, n)
+
+
 def _herm(M):
     return 0.5 * (M + M.conj().T)
 
@@ -143,8 +156,9 @@ def spurious_columns(lam_re: np.ndarray, theta: np.ndarray, nbands: int, tol: fl
 
 def solve_kpoint(N: int, kvec, m0: np.ndarray, nbands: int, tol: float, guard: int = 2, korder: int = 1,
                  gamma: float | None = None, variant: str = "gamma", X0: np.ndarray | None = None,
-                 maxiter: int = 500, max_doublings: int = 8, seed: int = 0):
-    """Algorithm 4.1 with the LOBPCG above and the FFT preconditioner of Algorithm 5.1.
+                 maxiter: int = 500, max_doublings: int = 8, seed: int = 0, lattice=None):
+    """Algorithm 4.1 with the LOBPCG above and the FFT preconditioner of Algorithm 5.1 (on the cell ``lattice`` when
+    given: Section 4.2.2's operators and symbols, k reduced by its reciprocal lattice).
 
     Returns a dict with eigenvalues (nbands), eigenvectors, iterations, residuals, the final gamma and the number
     of gamma doublings.
@@ -152,18 +166,19 @@ def solve_kpoint(N: int, kvec, m0: np.ndarray, nbands: int, tol: float, guard: i
     from .rng import initial_block
 
     h = 1.0 / N
-    k = reduce_to_first_zone(kvec)
+    k = reduce_to_first_zone(kvec) if lattice is None else reduce_by_reciprocal_lattice(kvec, lattice)
     g = mfd.penalty_gamma(h, k) if gamma is None else float(gamma)
     m = nbands + guard
     project = constant_projector(N) if not np.any(k) else None
     if X0 is None:
         X0 = initial_block(seed, 0, 3 * N ** 3, m)
-    Ah, _ = mfd.half_operators(N, k, h, korder)
+    lat = {} if lattice is None else {"lattice": lattice}
+    Ah, _ = mfd.half_operators(N, k, h, korder, **lat)
     total_it = 0
     for doubling in range(max_doublings + 1):
-        Op = mfd.compensated_operator(N, k, h, m0, g, korder)
+        Op = mfd.compensated_operator(N, k, h, m0, g, korder, **lat)
         theta, X, it, res = lobpcg(lambda Y: Op @ Y,
-                                   lambda Y: apply_preconditioner_block(Y, N, h, k, g, korder, variant),
+                                   lambda Y: apply_preconditioner_block(Y, N, h, k, g, korder, variant, **lat),
                                    X0, nbands, tol, maxiter, project)
         total_it += it
         lam_re, spurious = recompute_check(X[:, :nbands], theta[:nbands], m0, Ah, tol)

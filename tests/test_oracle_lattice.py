@@ -227,3 +227,31 @@ def test_planted_transposed_lattice_fails_the_continuum_pin():
         w = spectrum.homogeneous_physical_spectrum(64, 1.0 / 64, K_GENERIC, 1.0, 1, A)[:12]
         err = np.max(np.abs(w - ex) / ex)
         assert (err > 0.05) if bad else (err < 0.002)
+
+
+def test_oracle_lobpcg_on_a_lattice_matches_dense():
+    """The oracle's Algorithm 4.1 + LOBPCG with the lattice operators and preconditioner reproduces LAPACK on the FCC
+    cell holding a sphere (N = 8, gamma = 64 keeps the compensation values above the 6 bands)."""
+    from oracle import eigs
+    N = 8
+    m0 = geometry.m0_from_structure(N, np.array([[0.05, 0.1, 0.0, 0.2, 13.0]]), 1.0, FCC).ravel()
+    k = np.array([0.4, 0.8, -0.2])
+    out = eigs.solve_kpoint(N, k, m0, 6, 1e-9, guard=4, gamma=64.0, lattice=FCC)
+    Op = mfd.compensated_operator(N, k, 1.0 / N, m0, 64.0, 1, FCC)
+    ref, _ = eigs.lowest_dense(Op, 6)
+    assert out["doublings"] == 0
+    assert np.max(np.abs(out["evals"] - ref) / ref) <= 1e-9
+
+
+def test_reciprocal_lattice_reduction():
+    """A reciprocal-lattice vector reduces to exactly 0; a general k moves by one, keeping every eigenvalue of the
+    continuum (|k + G|^2 over all G is unchanged); the cube's rule is the special case A = I."""
+    from oracle import eigs
+    G = 2 * np.pi * np.linalg.inv(FCC).T @ np.array([1.0, -2.0, 1.0])
+    assert np.array_equal(eigs.reduce_by_reciprocal_lattice(G, FCC), np.zeros(3))
+    k = np.array([7.0, -1.0, 3.5])
+    kr = eigs.reduce_by_reciprocal_lattice(k, FCC)
+    frac = FCC.T @ (k - kr) / (2 * np.pi)
+    assert np.allclose(frac, np.round(frac), atol=1e-12)
+    assert np.all(np.abs(FCC.T @ kr / (2 * np.pi)) <= 0.5 + 1e-12)
+    assert np.allclose(eigs.reduce_by_reciprocal_lattice(k, np.eye(3)), eigs.reduce_to_first_zone(k))
