@@ -308,14 +308,14 @@ size_t pc_ws_work_bytes(int N, int nb, int S);
 /* Forward pass for S samples.
  *   params: device float [pc_ws_param_count(nb)].
  *   m0:     device float [nstruct][3][N][N][N], M0 = 1/eps at the edge DoFs of each structure.
- *   sidx:   device int [S], the structure of each sample.
+ *   sidx:   device int [S], the structure of each sample, each in [0, nstruct) (checked on the host: PC_EINVAL).
  *   kpts:   host double [S][3], the Bloch vector of each sample.
  *   X:      device complex64 [S][nb][3][N][N][N] (out): the predicted block of each sample.
  *   y:      device float [S][nb] (out): the guesses of log lambda.
  *   work:   device buffer of pc_ws_work_bytes(N, nb, S) bytes; keeps the activations for pc_ws_backward.
  * Synchronous on stream. */
-int pc_ws_forward(int N, int nb, int S, const float *params, const float *m0, const int *sidx, const double *kpts,
-                  void *X, float *y, void *work, void *stream);
+int pc_ws_forward(int N, int nb, int S, const float *params, const float *m0, int nstruct, const int *sidx,
+                  const double *kpts, void *X, float *y, void *work, void *stream);
 
 /* Loss and gradient for the S samples of the preceding pc_ws_forward call with the same work buffer and inputs.
  *   V:     device complex64 [S][nb][3][N][N][N], orthonormal eigenvectors of each sample's converged solve.
@@ -324,9 +324,9 @@ int pc_ws_forward(int N, int nb, int S, const float *params, const float *m0, co
  *   loss:  device double [S] (out): each sample's loss (NaN where X^H X was not positive definite; that sample
  *          then adds no gradient).
  * Enqueued on stream; returns before completion. */
-int pc_ws_backward(int N, int nb, int S, const float *params, const float *m0, const int *sidx, const void *X,
-                   const float *y, const void *V, const double *lam, float w_val, float *grad, double *loss,
-                   void *work, void *stream);
+int pc_ws_backward(int N, int nb, int S, const float *params, const float *m0, int nstruct, const int *sidx,
+                   const void *X, const float *y, const void *V, const double *lam, float w_val, float *grad,
+                   double *loss, void *work, void *stream);
 
 /* One Adam step (Kingma and Ba) on P parameters in place: m, v device float [P] moments (zero before step t = 1),
  * t the 1-based step count for the bias corrections. Enqueued on stream. */

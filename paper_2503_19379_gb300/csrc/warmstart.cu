@@ -621,6 +621,16 @@ int check_dims(int N, int nb, int S) {
 
 char *wp(void *work, size_t off) { return static_cast<char *>(work) + off; }
 
+// every sample's structure index must address one of the nstruct M0 grids (read back from the device: S ints)
+int check_sidx(const int *sidx, int S, int nstruct, cudaStream_t st) {
+  std::vector<int> h(S);
+  PC_CK(cudaMemcpyAsync(h.data(), sidx, sizeof(int) * S, cudaMemcpyDeviceToHost, st));
+  PC_CK(cudaStreamSynchronize(st));
+  for (int s = 0; s < S; ++s)
+    PC_REQUIRE(h[s] >= 0 && h[s] < nstruct, "warm start: sidx[%d] = %d is outside [0, %d)", s, h[s], nstruct);
+  return PC_OK;
+}
+
 }  // namespace
 
 extern "C" long pc_ws_param_count(int nb) {
@@ -633,12 +643,15 @@ extern "C" size_t pc_ws_work_bytes(int N, int nb, int S) {
   return work_layout(N, nb, S).total;
 }
 
-extern "C" int pc_ws_forward(int N, int nb, int S, const float *params, const float *m0, const int *sidx,
-                             const double *kpts, void *X, float *y, void *work, void *stream) {
+extern "C" int pc_ws_forward(int N, int nb, int S, const float *params, const float *m0, int nstruct,
+                             const int *sidx, const double *kpts, void *X, float *y, void *work, void *stream) {
   int rc = check_dims(N, nb, S);
   if (rc) return rc;
   PC_REQUIRE(params && m0 && sidx && kpts && X && y && work, "pc_ws_forward: null argument");
+  PC_REQUIRE(nstruct >= 1, "pc_ws_forward: nstruct must be >= 1");
   cudaStream_t st = (cudaStream_t)stream;
+  rc = check_sidx(sidx, S, nstruct, st);
+  if (rc) return rc;
   const Offs of = offsets(nb);
   const Work w = work_layout(N, nb, S);
   const int logN = ilog2(N);
@@ -671,14 +684,17 @@ extern "C" int pc_ws_forward(int N, int nb, int S, const float *params, const fl
   return PC_OK;
 }
 
-extern "C" int pc_ws_backward(int N, int nb, int S, const float *params, const float *m0, const int *sidx,
-                              const void *X, const float *y, const void *V, const double *lam, float w_val,
-                              float *grad, double *loss, void *work, void *stream) {
+extern "C" int pc_ws_backward(int N, int nb, int S, const float *params, const float *m0, int nstruct,
+                              const int *sidx, const void *X, const float *y, const void *V, const double *lam,
+                              float w_val, float *grad, double *loss, void *work, void *stream) {
   int rc = check_dims(N, nb, S);
   if (rc) return rc;
   PC_REQUIRE(params && m0 && sidx && X && y && V && lam && grad && loss && work, "pc_ws_backward: null argument");
   PC_REQUIRE(w_val >= 0.0f, "pc_ws_backward: w_val must be >= 0");
+  PC_REQUIRE(nstruct >= 1, "pc_ws_backward: nstruct must be >= 1");
   cudaStream_t st = (cudaStream_t)stream;
+  rc = check_sidx(sidx, S, nstruct, st);
+  if (rc) return rc;
   const Offs of = offsets(nb);
   const Work w = work_layout(N, nb, S);
   const int logN = ilog2(N);

@@ -73,8 +73,8 @@ SIGNATURES = {
     "pc_reset_stats": (_i, [_vp]),
     "pc_ws_param_count": (_l, [_i]),
     "pc_ws_work_bytes": (C.c_size_t, [_i, _i, _i]),
-    "pc_ws_forward": (_i, [_i, _i, _i, _vp, _vp, _vp, _dp, _vp, _vp, _vp, _vp]),
-    "pc_ws_backward": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp]),
+    "pc_ws_forward": (_i, [_i, _i, _i, _vp, _vp, _i, _vp, _dp, _vp, _vp, _vp, _vp]),
+    "pc_ws_backward": (_i, [_i, _i, _i, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp, _vp]),
     "pc_ws_adam": (_i, [_l, _vp, _vp, _vp, _vp, _i, C.c_float, C.c_float, C.c_float, C.c_float, _vp]),
 }
 
@@ -423,8 +423,8 @@ class WarmStart:
         X = torch.empty((self.S, self.nb, 3, self.N, self.N, self.N), dtype=torch.complex64, device="cuda")
         y = torch.empty((self.S, self.nb), dtype=torch.float32, device="cuda")
         _check(lib().pc_ws_forward(self.N, self.nb, self.S, _dev(self.params, [torch.float32]),
-                                   _dev(m0, [torch.float32]), _dev(sidx, [torch.int32]), _dptr(k), _dev(X), _dev(y),
-                                   _dev(self.work), self._stream), "pc_ws_forward")
+                                   _dev(m0, [torch.float32]), int(m0.shape[0]), _dev(sidx, [torch.int32]), _dptr(k),
+                                   _dev(X), _dev(y), _dev(self.work), self._stream), "pc_ws_forward")
         return X, y
 
     def backward(self, m0, sidx, X, y, V, lam, w_val: float = 0.1):
@@ -433,7 +433,8 @@ class WarmStart:
         grad = torch.empty_like(self.params)
         loss = torch.empty(self.S, dtype=torch.float64, device="cuda")
         _check(lib().pc_ws_backward(self.N, self.nb, self.S, _dev(self.params, [torch.float32]),
-                                    _dev(m0, [torch.float32]), _dev(sidx, [torch.int32]), _dev(X, [torch.complex64]),
+                                    _dev(m0, [torch.float32]), int(m0.shape[0]), _dev(sidx, [torch.int32]),
+                                    _dev(X, [torch.complex64]),
                                     _dev(y, [torch.float32]), _dev(V, [torch.complex64]), _dev(lam, [torch.float64]),
                                     float(w_val), _dev(grad), _dev(loss), _dev(self.work), self._stream),
                "pc_ws_backward")

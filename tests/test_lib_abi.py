@@ -187,9 +187,9 @@ def test_warm_start_host_entry_points(libpath):
     assert L.pc_ws_param_count(0) == -1 and L.pc_ws_param_count(17) == -1
     assert L.pc_ws_work_bytes(32, 8, 4) > 0 and L.pc_ws_work_bytes(12, 8, 4) == 0
     k = np.zeros(3)
-    rc = L.pc_ws_forward(12, 8, 1, None, None, None, pc._dptr(k), None, None, None, None)
+    rc = L.pc_ws_forward(12, 8, 1, None, None, 1, None, pc._dptr(k), None, None, None, None)
     assert rc == -1 and b"power of two" in L.pc_last_error()
-    rc = L.pc_ws_forward(32, 8, 1, None, None, None, pc._dptr(k), None, None, None, None)
+    rc = L.pc_ws_forward(32, 8, 1, None, None, 1, None, pc._dptr(k), None, None, None, None)
     assert rc == -1 and b"null" in L.pc_last_error()
     rc = L.pc_ws_adam(4, None, None, None, None, 1, C.c_float(1e-3), C.c_float(0.9), C.c_float(0.999),
                       C.c_float(1e-8), None)
