@@ -104,6 +104,11 @@ def kpath(labels, points: dict, npts: int) -> np.ndarray:
 
 FCC_PATH = ("G", "X", "W", "K", "G", "L")
 SC_PATH = ("G", "L", "M", "G", "N")
+# BCC symmetry points of Section 6 (Cartesian, l = 1). The paper lists the points but its band figure, which would
+# show their order, is lost; the path below is a reading: the usual BCC circuit through all of them.
+BCC_POINTS = {"G": (0.0, 0.0, 0.0), "H": (0.0, 2 * PI, 0.0), "N": (PI, 0.0, PI), "P": (PI, PI, PI),
+              "H'": (0.0, 0.0, 2 * PI)}
+BCC_PATH = ("G", "H", "N", "G", "P", "H'")
 
 
 @dataclass
