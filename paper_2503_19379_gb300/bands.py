@@ -27,3 +27,29 @@ def largest_gap(evals):
         return 0, 0.0
     n = int(np.argmax(r))
     return n + 1, float(r[n])
+
+
+def solve_path_two_pass(solver, kpts, nbands: int, tol: float):
+    """All k-points of a path in two batched solves: the even-indexed k-points from random blocks, then the odd ones
+    from the eigenvectors of their preceding (even) neighbour (pc_solve_init). Along a path the neighbour's
+    eigenvectors are a close start: the oracle's LOBPCG needs about 30% fewer iterations from them.
+
+    Returns the dict of Solver.solve (evals, iters, resid, status) in path order."""
+    kpts = np.asarray(kpts, dtype=np.float64).reshape(-1, 3)
+    nk = kpts.shape[0]
+    even = np.arange(0, nk, 2)
+    odd = np.arange(1, nk, 2)
+    first = solver.solve(kpts[even], nbands, tol, want_vectors=odd.size > 0)
+    evals = np.zeros((nk, nbands))
+    resid = np.zeros((nk, nbands))
+    iters = np.zeros(nk, dtype=np.int32)
+    evals[even], resid[even], iters[even] = first["evals"], first["resid"], first["iters"]
+    status = first["status"]
+    if odd.size:
+        import torch
+        x0 = first["evecs"][(odd - 1) // 2].to(torch.complex64).contiguous()  # odd i starts from i - 1 = 2 ((i-1)/2)
+        del first["evecs"]
+        second = solver.solve(kpts[odd], nbands, tol, x0=x0)
+        evals[odd], resid[odd], iters[odd] = second["evals"], second["resid"], second["iters"]
+        status = max(status, second["status"])
+    return {"evals": evals, "iters": iters, "resid": resid, "status": status}
