@@ -74,6 +74,9 @@ typedef struct {
     int groups;            /* PC_PREC_MIXED: k-point groups (at most 4) iterated on separate streams so that one
                               group's latency-bound steps (Rayleigh-Ritz, host decisions) overlap the others'
                               kernels; 0 (default): 4 from 16 k-points, 2 from 8, else 1 */
+    int kchunk;            /* k-points per pass of pc_solve: a batch larger than what fits the device memory (85% of
+                              the free memory for the solve's panels) is solved in consecutive chunks; kchunk > 0
+                              caps the chunk further; 0 (default): as many as fit */
 } pc_opts;
 
 /* Fill *opts with the defaults listed above. */

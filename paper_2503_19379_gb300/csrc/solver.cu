@@ -222,6 +222,7 @@ extern "C" int pc_opts_default(pc_opts *o) {
   o->max_doublings = 8;
   o->seed = 0;
   o->groups = 0;
+  o->kchunk = 0;
   return PC_OK;
 }
 
@@ -261,6 +262,7 @@ extern "C" int pc_setup(pc_ctx **out, int N, const double *eps_edges, const doub
   PC_REQUIRE(o.precond == PC_PRECOND_GAMMA || o.precond == PC_PRECOND_LAPLACIAN, "pc_setup: bad precond");
   PC_REQUIRE(o.precision == PC_PREC_FP64 || o.precision == PC_PREC_MIXED, "pc_setup: bad precision");
   PC_REQUIRE(o.maxiter >= 1 && o.max_doublings >= 0, "pc_setup: bad maxiter/doublings");
+  PC_REQUIRE(o.kchunk >= 0, "pc_setup: kchunk must be >= 0");
   const long n = (long)N * N * N;
   for (long i = 0; i < 3 * n; ++i)
     PC_REQUIRE(eps_edges[i] > 0.0 && std::isfinite(eps_edges[i]), "pc_setup: eps_edges[%ld] must be finite and > 0", i);
@@ -354,6 +356,41 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
   const int guard = ctx->opts.guard >= 0 ? ctx->opts.guard : std::max(0, std::min(nbands / 2 + 1, 21 - nbands));
   const int m = nbands + guard;
   PC_REQUIRE(3 * m <= 64, "pc_solve: nbands + guard must be <= 21");
+  // k-points per pass that fit the device: the solve's panels take ~136 m L bytes per k-point in the mixed solve
+  // (four complex64 panels of 3m columns, two double-float blocks and a complex64 residual copy) and 192 m L in the
+  // FP64 solve (four complex128 panels); the budget is 85% of the free memory plus what this context already holds
+  // in those buffers. A batch larger than that is solved in consecutive chunks (the results are the same: the
+  // k-points are independent problems).
+  {
+    const double Lb = 3.0 * (double)ctx->n;
+    const double per_k = (ctx->opts.precision == PC_PREC_MIXED ? 136.0 : 192.0) * m * Lb;
+    size_t freeb = 0, totalb = 0;
+    PC_CK(cudaMemGetInfo(&freeb, &totalb));
+    double held = 0.0;
+    for (int i = 0; i < 2; ++i) held += (double)ctx->S[i].bytes + (double)ctx->AS[i].bytes + (double)ctx->X64[i].bytes;
+    held += (double)ctx->R32.bytes;
+    const double budget = 0.85 * ((double)freeb + held);
+    int chunk = (int)std::max(1.0, std::min(std::floor(budget / per_k), (double)nk));
+    if (ctx->opts.kchunk > 0) chunk = std::min(chunk, ctx->opts.kchunk);
+    if (chunk < nk) {
+      int status = PC_OK;
+      const void *x0 = ctx->x0;  // a caller's initial block (pc_solve_init) covers all nk k-points
+      for (int b0 = 0; b0 < nk; b0 += chunk) {
+        const int nc = std::min(chunk, nk - b0);
+        if (x0)
+          ctx->x0 = static_cast<const char *>(x0) + sizeof(float2) * (size_t)b0 * ctx->x0n * (size_t)(3 * ctx->n);
+        void *ev = evecs ? static_cast<void *>(static_cast<char *>(evecs) + sizeof(double2) * (size_t)b0 * nbands *
+                                                                                 (size_t)(3 * ctx->n))
+                         : nullptr;
+        const int rc = pc_solve(ctx, nc, kpts + 3 * (size_t)b0, nbands, tol, evals + (size_t)b0 * nbands, ev,
+                                iters ? iters + b0 : nullptr, resid ? resid + (size_t)b0 * nbands : nullptr);
+        ctx->x0 = x0;
+        if (rc < 0) return rc;
+        status = std::max(status, rc);
+      }
+      return status;
+    }
+  }
   cudaStream_t st = ctx->stream;
   const int nb = nk;
   const long n = ctx->n, L = 3 * n;

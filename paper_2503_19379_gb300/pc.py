@@ -35,7 +35,7 @@ class StageStat(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("order", C.c_int), ("gamma_override", C.c_double), ("precond", C.c_int), ("precision", C.c_int),
                 ("guard", C.c_int), ("maxiter", C.c_int), ("max_doublings", C.c_int), ("seed", C.c_uint64),
-                ("groups", C.c_int)]
+                ("groups", C.c_int), ("kchunk", C.c_int)]
 
 
 _LIB = None

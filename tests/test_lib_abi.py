@@ -218,3 +218,35 @@ def test_structure_entry_points_reject_bad_arguments_on_the_host(libpath):
     eye = np.eye(3).ravel()
     assert L.pc_eps_gyroid(8, pc._dptr(eye), -1.0, 1.1, 16.0, 1.0, pc._dptr(out)) == -1
     assert L.pc_eps_diamond(8, pc._dptr(eye), 1.0, -0.1, 0.11, 13.0, 1.0, pc._dptr(out)) == -1
+
+
+def test_opts_layout_matches_the_header(tmp_path):
+    """The binding's Opts mirrors pc_opts field by field: sizes and offsets from a C program compiled against
+    include/pc.h equal ctypes' (a drift here would shift every option after it)."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_2503_19379_gb300 import pc
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    names = [f[0] for f in pc.Opts._fields_]
+    body = "".join(f'printf("%zu ", offsetof(pc_opts, {n}));' for n in names)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "pc.h"\nint main(void){' + body +
+                   'printf("%zu\\n", sizeof(pc_opts)); return 0;}\n')
+    exe = tmp_path / "layout"
+    res = subprocess.run([cc, "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    want = [getattr(pc.Opts, n).offset for n in names] + [ctypes.sizeof(pc.Opts)]
+    assert got == want
+
+
+def test_kchunk_option_validated_on_the_host(libpath):
+    from paper_2503_19379_gb300 import pc
+    rc, msg = _setup_rc(8, kchunk=-1)
+    assert rc == -1 and "kchunk" in msg
+    assert pc.default_opts().kchunk == 0
