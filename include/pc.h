@@ -89,10 +89,10 @@ int pc_opts_default(pc_opts *opts);
  *              M0 = diag(1/eps_edges).
  *   lattice:   host double[9] or NULL (identity): the lattice vectors a1, a2, a3 one after the other
  *              (lattice[3 n + c] = component c of a_{n+1}), finite and linearly independent (else PC_EINVAL). The
- *              identity runs the cubic cell's kernels; any other cell runs the general-lattice stencils at every
- *              order and the FP64 / complex64 paths only (PC_PREC_MIXED with a non-identity lattice ->
- *              PC_EUNSUPPORTED; the double-float stencil likewise). eps_edges then holds the permittivity at the
- *              Cartesian points A y of the edge midpoints y (pc_eps_spheres_lattice).
+ *              identity runs the cubic cell's kernels; any other cell runs the general-lattice stencils (every
+ *              order in FP64 and complex64; second order in double-float, which the mixed solve uses). eps_edges
+ *              then holds the permittivity at the Cartesian points A y of the edge midpoints y
+ *              (pc_eps_spheres_lattice).
  *   opts:      options (NULL -> defaults).
  *   stream:    cudaStream_t to use for all work of this context (NULL -> the legacy default stream).
  * Uploads M0 and the FFT tables once (one host-to-device copy). */

@@ -370,9 +370,137 @@ static int launch_opz_df_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, v
   return PC_OK;
 }
 
+// ---------------------------------------------------------------- general lattice (Section 4.2.2)
+// D_hat_a f = sum_j (b_ja / h)(f_{r+e_j} - f_r) + i kh_a (f_r + f_{r+e_a}) and its adjoint
+// D_hat_a' g = sum_j (b_ja / h)(g_{r-e_j} - g_r) - i kh_a (g_{r-e_a} + g_r), second order, in double-float; the
+// weights b_ja / h are double-float pairs. Two passes through a per-stream scratch block (e = M0 A' v, c = B v as
+// double-float pairs, then y = A e + gamma B' c), the second with the residual epilogue of the cubic kernels.
+struct LatDF {
+  df bh[9];  // bh[3 j + a] = b_ja N
+};
+
+__device__ __forceinline__ long lat_nb(long i, int axis, int off, int logN) {
+  const int N = 1 << logN, mask = N - 1;
+  int x = (int)(i & mask), y = (int)((i >> logN) & mask), z = (int)(i >> (2 * logN));
+  if (axis == 0) x = (x + off) & mask;
+  else if (axis == 1) y = (y + off) & mask;
+  else z = (z + off) & mask;
+  return ((long)z << (2 * logN)) + ((long)y << logN) + x;
+}
+
+// D_hat_a (adj = false) or D_hat_a' (adj = true) of field f at point i; f[...] read through ld_cdf
+template <typename S>
+__device__ __forceinline__ cdf dlat_df(const S *__restrict__ f, long i, int a, bool adj, int logN, const LatDF &lt,
+                                       df kh) {
+  const cdf f0 = ld_cdf(f + i);
+  cdf acc = cdf{df{0.f, 0.f}, df{0.f, 0.f}}, sm = acc;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const cdf fj = ld_cdf(f + lat_nb(i, j, adj ? -1 : 1, logN));
+    acc = cdf_add(acc, cdf_scale(cdf_sub(fj, f0), lt.bh[3 * j + a]));
+    if (j == a) sm = cdf_add(fj, f0);
+  }
+  // acc + i kh sm (forward) or acc - i kh sm (adjoint)
+  const df sr = df_mul(kh, sm.re), si = df_mul(kh, sm.im);
+  return adj ? cdf{df_add(acc.re, si), df_sub(acc.im, sr)} : cdf{df_sub(acc.re, si), df_add(acc.im, sr)};
+}
+
+// pass 1: E (3 fields) and Cc (1 field) of column j of k-point act[bz], double-float pairs. grid (n / 256, m, nb)
+template <typename XS>
+__global__ void __launch_bounds__(256) lat_df_half_kernel(const XS *__restrict__ X, long sx, float4 *__restrict__ E,
+                                                          const float2 *__restrict__ m0, const KParam *__restrict__ kp,
+                                                          const int *__restrict__ act, int logN, const LatDF lt) {
+  const long n = 1L << (3 * logN);
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int bz = blockIdx.z, j = blockIdx.y, m = gridDim.y;
+  const int b = act ? act[bz] : bz;
+  const KParam &p = kp[b];
+  const df kh0 = kp_df(p.khf[0], p.khl[0]), kh1 = kp_df(p.khf[1], p.khl[1]), kh2 = kp_df(p.khf[2], p.khl[2]);
+  const XS *v1 = X + (long)b * sx + (long)j * 3 * n, *v2 = v1 + n, *v3 = v2 + n;
+  const cdf e1 = cdf_scale(cdf_sub(dlat_df(v2, i, 2, true, logN, lt, kh2), dlat_df(v3, i, 1, true, logN, lt, kh1)),
+                           ld_m0(m0 + i));
+  const cdf e2 = cdf_scale(cdf_sub(dlat_df(v3, i, 0, true, logN, lt, kh0), dlat_df(v1, i, 2, true, logN, lt, kh2)),
+                           ld_m0(m0 + n + i));
+  const cdf e3 = cdf_scale(cdf_sub(dlat_df(v1, i, 1, true, logN, lt, kh1), dlat_df(v2, i, 0, true, logN, lt, kh0)),
+                           ld_m0(m0 + 2 * n + i));
+  const cdf c = cdf_add(cdf_add(dlat_df(v1, i, 0, false, logN, lt, kh0), dlat_df(v2, i, 1, false, logN, lt, kh1)),
+                        dlat_df(v3, i, 2, false, logN, lt, kh2));
+  float4 *eb = E + ((long)bz * m + j) * 4 * n;
+  st_cdf(eb + i, e1);
+  st_cdf(eb + n + i, e2);
+  st_cdf(eb + 2 * n + i, e3);
+  st_cdf(eb + 3 * n + i, c);
+}
+
+// pass 2: y = A e + gamma B' c, stored (RES = false) or reduced to the residual epilogue (RES = true; every thread
+// of the block takes part in its block sum). grid (n / 256, m, nb), 256 threads
+template <bool RES>
+__global__ void __launch_bounds__(256) lat_df_full_kernel(const float4 *__restrict__ E, const df_store_t<RES> *__restrict__ X,
+                                                          long sx, df_store_t<RES> *__restrict__ Y, long sy,
+                                                          const KParam *__restrict__ kp, const int *__restrict__ act,
+                                                          int logN, const LatDF lt, const ResidArgs ra) {
+  const long n = 1L << (3 * logN);
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int bz = blockIdx.z, j = blockIdx.y, m = gridDim.y;
+  const int b = act ? act[bz] : bz;
+  const KParam &p = kp[b];
+  float sr = 0.f, sxx = 0.f;
+  if (i < n) {
+    const df kh0 = kp_df(p.khf[0], p.khl[0]), kh1 = kp_df(p.khf[1], p.khl[1]), kh2 = kp_df(p.khf[2], p.khl[2]);
+    const df gam = kp_df(p.gammaf, p.gammal);
+    const float4 *e1 = E + ((long)bz * m + j) * 4 * n, *e2 = e1 + n, *e3 = e2 + n, *c = e3 + n;
+    cdf y1 = cdf_sub(dlat_df(e3, i, 1, false, logN, lt, kh1), dlat_df(e2, i, 2, false, logN, lt, kh2));
+    y1 = cdf_add(y1, cdf_scale(dlat_df(c, i, 0, true, logN, lt, kh0), gam));
+    cdf y2 = cdf_sub(dlat_df(e1, i, 2, false, logN, lt, kh2), dlat_df(e3, i, 0, false, logN, lt, kh0));
+    y2 = cdf_add(y2, cdf_scale(dlat_df(c, i, 1, true, logN, lt, kh1), gam));
+    cdf y3 = cdf_sub(dlat_df(e2, i, 0, false, logN, lt, kh0), dlat_df(e1, i, 1, false, logN, lt, kh1));
+    y3 = cdf_add(y3, cdf_scale(dlat_df(c, i, 2, true, logN, lt, kh2), gam));
+    if constexpr (RES) {
+      const df_store_t<RES> *xb = X + (long)b * sx + (long)j * 3 * n;
+      const cdf yv[3] = {y1, y2, y3}, xv[3] = {ld_cdf(xb + i), ld_cdf(xb + n + i), ld_cdf(xb + 2 * n + i)};
+      const df th = df_from(ra.theta[(long)b * ra.m + j]);
+      resid_point(ra, b, j, n, i, th, yv, xv, sr, sxx);
+    } else {
+      df_store_t<RES> *yb = Y + (long)b * sy + (long)j * 3 * n;
+      st_cdf(yb + i, y1);
+      st_cdf(yb + n + i, y2);
+      st_cdf(yb + 2 * n + i, y3);
+    }
+  }
+  if constexpr (RES) resid_block_sum(ra, sr, sxx);
+}
+
+template <bool RES>
+int launch_op_df_lat(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act,
+                     const ResidArgs &ra, int *nchunk) {
+  const long n = ctx->n;
+  const dim3 grid((unsigned)((n + 255) / 256), m, nb);
+  *nchunk = (int)grid.x;
+  if (RES && ra.part == nullptr) return PC_OK;  // sizing call
+  LatDF lt;
+  for (int q = 0; q < 9; ++q) {
+    const double v = ctx->binv[q] * (double)ctx->N;
+    lt.bh[q].hi = (float)v;
+    lt.bh[q].lo = (float)(v - (double)lt.bh[q].hi);
+  }
+  DevBuf &ks = kscratch_for(ctx);
+  PC_CK(ks.reserve(sizeof(float4) * 4 * (size_t)n * m * nb));
+  float4 *E = ks.as<float4>();
+  using XS = df_store_t<RES>;
+  lat_df_half_kernel<XS><<<grid, 256, 0, ctx->stream>>>(static_cast<const XS *>(X), sx, E, ctx->m0p.as<float2>(),
+                                                         ctx->kparam.as<KParam>(), act, ctx->logN, lt);
+  PC_CK_LAUNCH();
+  lat_df_full_kernel<RES><<<grid, 256, 0, ctx->stream>>>(E, static_cast<const XS *>(X), sx, static_cast<XS *>(Y), sy,
+                                                          ctx->kparam.as<KParam>(), act, ctx->logN, lt, ra);
+  PC_CK_LAUNCH();
+  return PC_OK;
+}
+
 template <bool RES>
 static int op_df_dispatch(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act,
                           const ResidArgs &ra, int *nchunk) {
+  if (ctx->lat) return launch_op_df_lat<RES>(ctx, nb, m, X, sx, Y, sy, act, ra, nchunk);
   const int N = ctx->N;
   if (N >= 32) return launch_opz_df_t<32, 8, RES>(ctx, nb, m, X, sx, Y, sy, act, ra, nchunk);
   if (N == 16) return launch_op_df_t<16, 4, 4, RES>(ctx, nb, m, X, sx, Y, sy, act, ra, nchunk);
@@ -381,8 +509,8 @@ static int op_df_dispatch(pc_ctx *ctx, int nb, int m, const void *X, long sx, vo
 
 int launch_apply_op_df(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act) {
   if (nb == 0 || m == 0) return PC_OK;
-  if (ctx->opts.order != 1 || ctx->lat) {
-    set_error("double-float stencil: second order (order 1) on the cubic cell only");
+  if (ctx->opts.order != 1) {
+    set_error("double-float stencil: second order (order 1) only");
     return PC_EUNSUPPORTED;
   }
   int nchunk = 0;

@@ -124,7 +124,8 @@ struct pc_ctx {
   double amat[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   pc::DevBuf m0d, m0f;      // M0 diagonal, double and float copies, [3][N^3]
   pc::DevBuf m0p;           // M0 diagonal as double-float pairs (hi, lo) float2 [3][N^3]
-  pc::DevBuf kscratch;      // higher-order stencils: e = M0 A' v (3 fields) and c = B v (1 field) per column
+  pc::DevBuf kscratch;      // two-pass stencils: e = M0 A' v (3 fields) and c = B v (1 field) per column
+  pc::DevBuf kscratch_x[3]; // the same for k-point groups 1.. of the mixed solve (their own streams, concurrent)
   pc::DevBuf twd, twf;      // FFT twiddles exp(-2 pi i t / N), t < N/2
   pc::DevBuf kparam;        // KParam [nb]
   pc::DevBuf symd;          // per-k axis symbols d_i(m) complex128 [nb][3][N]; general lattice: [nb][3][3][N]
@@ -168,6 +169,14 @@ struct pc_ctx {
 };
 
 namespace pc {
+// The two-pass stencils' scratch for the stream the context currently issues on: the mixed solve's k-point groups
+// run concurrently on their own streams, each with its own buffer; every other caller uses ctx->kscratch.
+static_assert(sizeof(pc_ctx::kscratch_x) / sizeof(DevBuf) == pc_ctx::kMaxGroups - 1, "one scratch per extra group");
+inline DevBuf &kscratch_for(pc_ctx *ctx) {
+  for (int i = 0; i < pc_ctx::kMaxGroups - 1; ++i)
+    if (ctx->xstream[i] && ctx->stream == ctx->xstream[i]) return ctx->kscratch_x[i];
+  return ctx->kscratch;
+}
 // Runs one stage invocation: counts it, adds its algorithmic work, and brackets it with events when timing is on.
 template <typename F> int run_stage(pc_ctx *ctx, int stage, int kernels, double flops, double bytes, F &&launch);
 // Accumulates the elapsed times of finished event pairs; pairs still in flight stay pending.

@@ -247,10 +247,6 @@ extern "C" int pc_setup(pc_ctx **out, int N, const double *eps_edges, const doub
   pc_opts o;
   pc_opts_default(&o);
   if (opts) o = *opts;
-  if (general && o.precision == PC_PREC_MIXED) {
-    set_error("pc_setup: the mixed-precision solve implements the cubic cell only (lattice = identity)");
-    return PC_EUNSUPPORTED;
-  }
   if (o.order < 1 || o.order > 4) {
     set_error("pc_setup: stencil order %d: Table 1 orders 1..4 (2nd to 8th order) are implemented", o.order);
     return PC_EUNSUPPORTED;

@@ -349,8 +349,9 @@ template <typename T, int K, bool LAT>
 int apply_op_k_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act) {
   using C = cplx<T>;
   const long n = ctx->n;
-  PC_CK(ctx->kscratch.reserve(sizeof(C) * 4 * (size_t)n * m * nb));
-  C *E = ctx->kscratch.as<C>(), *Cc = E + 3 * n * (long)m * nb;
+  DevBuf &ks = kscratch_for(ctx);
+  PC_CK(ks.reserve(sizeof(C) * 4 * (size_t)n * m * nb));
+  C *E = ks.as<C>(), *Cc = E + 3 * n * (long)m * nb;
   const Coef<T> cf = coef_for<T>(K);
   const Lat<T> lt = lat_for<T>(ctx);
   const T *m0 = std::is_same<T, double>::value ? ctx->m0d.as<T>() : ctx->m0f.as<T>();

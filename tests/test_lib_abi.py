@@ -128,8 +128,8 @@ def test_setup_rejects_bad_arguments_on_the_host(libpath):
     import numpy as np
     rc, msg = _setup_rc(12)
     assert rc == -1 and "power of two" in msg
-    rc, msg = _setup_rc(8, lattice=np.diag([1.0, 1.0, 2.0]), precision=1)
-    assert rc == -2 and "cubic" in msg and "mixed" in msg
+    rc, msg = _setup_rc(8, lattice=np.diag([1.0, 1.0, 2.0]), order=2, precision=1)
+    assert rc == -2 and "mixed" in msg
     rc, msg = _setup_rc(8, lattice=[0.0, 0.5, 0.5, 0.5, 0.0, 0.5, 0.5, 0.5, 0.0 * np.nan])
     assert rc == -1 and "finite" in msg
     rc, msg = _setup_rc(8, lattice=[1.0, 2.0, 3.0, 2.0, 4.0, 6.0, 0.0, 0.0, 1.0])
