@@ -53,3 +53,39 @@ def solve_path_two_pass(solver, kpts, nbands: int, tol: float):
         evals[odd], resid[odd], iters[odd] = second["evals"], second["resid"], second["iters"]
         status = max(status, second["status"])
     return {"evals": evals, "iters": iters, "resid": resid, "status": status}
+
+
+def structure_eps(workload) -> np.ndarray:
+    """Edge permittivity of a workload of the paper's own cells (workloads.workload_bcc_gyroid / _fcc_diamond, whose
+    `extra` names the geometry), or of a sphere workload on the cube."""
+    from . import pc
+    ex = getattr(workload, "extra", {}) or {}
+    geom = ex.get("geometry")
+    if geom == "gyroid":
+        return pc.eps_gyroid(workload.N, ex["lattice"], 1.0, ex["threshold"], ex["eps_in"], 1.0)
+    if geom == "diamond":
+        return pc.eps_diamond(workload.N, ex["lattice"], 1.0, ex["r"], ex["b"], ex["eps_in"], 1.0)
+    s = workload.structure
+    return pc.eps_spheres(workload.N, s.as_array(), s.eps_bg)
+
+
+def timed_solve(workload, precision: int, repeats: int = 1):
+    """Seconds per solve of the workload's k-points (CUDA events around pc_solve, after one untimed solve), with the
+    eigenvalues and iteration counts: the paper's timing setting (first 10 eigenvalues at k = (pi, pi, pi) / l)."""
+    from . import pc
+    torch = pc._torch()
+    ex = getattr(workload, "extra", {}) or {}
+    solver = pc.Solver(workload.N, structure_eps(workload), lattice=ex.get("lattice"), precision=precision)
+    try:
+        solver.solve(workload.kpts, workload.nbands, workload.tol)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(repeats):
+            out = solver.solve(workload.kpts, workload.nbands, workload.tol)
+        b.record()
+        torch.cuda.synchronize()
+    finally:
+        solver.close()
+    return {"seconds": a.elapsed_time(b) / 1e3 / repeats, "evals": out["evals"], "iters": out["iters"],
+            "status": out["status"]}
