@@ -289,7 +289,6 @@ extern "C" int pc_setup(pc_ctx **out, int N, const double *eps_edges, const doub
     twf[t].x = (float)tw[t].x;
     twf[t].y = (float)tw[t].y;
   }
-  int rc = PC_OK;
   auto fail = [&](int code) {
     delete ctx;
     return code;
@@ -306,7 +305,6 @@ extern "C" int pc_setup(pc_ctx **out, int N, const double *eps_edges, const doub
       (e = cudaMemcpy(ctx->twd.p, tw.data(), sizeof(double2) * (N / 2), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(ctx->twf.p, twf.data(), sizeof(float2) * (N / 2), cudaMemcpyHostToDevice)) != cudaSuccess)
     return fail(cuda_fail(e, "upload", __FILE__, __LINE__));
-  (void)rc;
   *out = ctx;
   return PC_OK;
 }
