@@ -254,7 +254,11 @@ int pc_gram_pair_coupled(int nb, long L, int p, int q, const void *S, long ss, c
  * library image, so every GPU that loads the library holds those 4 MiB until the process exits.
  * This entry point has no counterpart in the paper; it is an interface convenience.
  *   Limit: 2 * 16 * nb * p * p <= 4 MiB, i.e. nb * p * p <= 131072 (for example 32 k-points of 64 columns);
- *   larger requests return PC_EINVAL with a message. Arguments, layout and results are those of pc_gram_pair.
+ *   larger requests return PC_EINVAL with a message. Arguments and layout are those of pc_gram_pair. Results agree
+ *   with pc_gram_pair within rounding, but not bit for bit: complex64 panels are always summed on the CUDA cores
+ *   (FP32 products and partial sums over row chunks, chunks added in FP64), never on the tensor-core path that
+ *   pc_gram_pair takes for them. The call is asynchronous: it returns once the work is enqueued on `stream`
+ *   (pc_gram_pair waits for its stream), so G and H are valid only after the caller synchronises with `stream`.
  *   The first call on each device looks up the array's device address (cudaGetSymbolAddress) with that device
  *   current; make that first call before any stream capture. Every call reuses the same array and only reads
  *   entries it has written itself, so no state carries over between calls, but calls whose work overlaps on the

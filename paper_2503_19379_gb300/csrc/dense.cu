@@ -147,7 +147,7 @@ __global__ void gram_reduce_kernel(const double2 *__restrict__ part, int nchunk,
 }
 
 static int gram_chunks(int nb, long L) {
-  long want = std::max<long>(1, (4L * 152 + nb - 1) / std::max(nb, 1));
+  long want = std::max<long>(1, (4L * sm_count() + nb - 1) / std::max(nb, 1));
   long maxc = std::max<long>(1, L / 512);
   return (int)std::min<long>(std::min(want, maxc), 256);
 }

@@ -493,6 +493,10 @@ int launch_precond(pc_ctx *ctx, int nb, int m, int dtype, const void *R, long sr
                    const int *act) {
   if (nb == 0 || m == 0) return PC_OK;
   if (dtype == PC_C128) return launch_precond_t<double>(ctx, nb, m, R, sr, W, sw, act);
+  {
+    const int rc = launch_precond_c64(ctx, nb, m, R, sr, W, sw, act);  // fft_c64.cu: N <= 64, cube and lattice
+    if (rc != PC_EUNSUPPORTED) return rc;
+  }
   // the register path's symbols are per axis; a general lattice takes the shared-memory path
   if (ctx->lat) return launch_precond_t<float>(ctx, nb, m, R, sr, W, sw, act);
   const float2 *Rf = static_cast<const float2 *>(R);

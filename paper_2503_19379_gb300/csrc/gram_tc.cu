@@ -439,16 +439,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a, 
   if (threadIdx.x == 0 && *abort) atomicExch(&g_gram_tc_error, 1);
 }
 
-int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-      n = 152;
-  }
-  return n;
-}
-
 constexpr int TC_SMEM_MAX = 232448;  // opt-in shared memory per block
 
 size_t tc_smem(int PB, int QB, int ns) {

@@ -359,7 +359,7 @@ static int launch_opz_df_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, v
   const int N = ctx->N;
   const long tiles = (long)(N / TX) * (N / TY) * m * nb;
   int ZC = N;
-  while (ZC > 4 && tiles * (N / ZC) < 4L * 152 * 4) ZC >>= 1;
+  while (ZC > 4 && tiles * (N / ZC) < 16L * sm_count()) ZC >>= 1;
   dim3 grid((N / TX) * (N / TY) * (N / ZC), m, nb);
   *nchunk = (int)grid.x;
   if (RES && ra.part == nullptr) return PC_OK;  // sizing call
@@ -659,7 +659,7 @@ __global__ void gram_df_reduce_kernel(const double2 *__restrict__ part, int nchu
 }
 
 static int df_chunks(int nb, long L) {
-  long want = std::max<long>(1, (8L * 152 + nb - 1) / std::max(nb, 1));
+  long want = std::max<long>(1, (8L * sm_count() + nb - 1) / std::max(nb, 1));
   return (int)std::min<long>(std::min<long>(want, std::max<long>(1, L / 512)), 128);
 }
 

@@ -78,6 +78,20 @@ inline int ilog2(int n) {
 }
 inline bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
+// Streaming multiprocessors of the current device (queried once per device): grids and chunk counts are sized in
+// multiples of it. Falls back to 1 if the query fails, so that sizes stay valid.
+inline int sm_count() {
+  static int count[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (count[dev] <= 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    count[dev] = n;
+  }
+  return count[dev];
+}
+
 // ---------------------------------------------------------------- device buffer that frees itself
 struct DevBuf {
   void *p = nullptr;
@@ -120,6 +134,9 @@ struct pc_ctx {
   // caller-provided initial block of pc_solve_init: device complex64 [nk][x0n][3][N][N][N], or null
   const void *x0 = nullptr;
   int x0n = 0;
+  // index of the batch's first k-point within the caller's list: a chunked pc_solve passes each chunk's offset, so
+  // that every k-point draws the initial columns of its own index (the same block as in an unchunked solve)
+  int kidx0 = 0;
   double binv[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   double amat[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   pc::DevBuf m0d, m0f;      // M0 diagonal, double and float copies, [3][N^3]
@@ -191,6 +208,8 @@ int launch_apply_op(pc_ctx *ctx, int nb, int m, int dtype, const void *X, long s
                     const int *act);
 int launch_precond(pc_ctx *ctx, int nb, int m, int dtype, const void *R, long sr, void *W, long sw,
                    const int *act);
+// complex64 preconditioner in three natural-order passes (fft_c64.cu); PC_EUNSUPPORTED for sizes it does not take
+int launch_precond_c64(pc_ctx *ctx, int nb, int m, const void *R, long sr, void *W, long sw, const int *act);
 // nb_alloc: k-points in the panel arrays (the act list indexes them); <= 0 means nb.
 // sg: batch stride of the output matrices in elements; <= 0 means packed (p q, or p p for the pair).
 int launch_gram(int nb, long L, int p, int q, int dtype, const void *A, long sa, const void *B, long sb, void *G,

@@ -352,25 +352,33 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
   PC_REQUIRE(3 * m <= 64, "pc_solve: nbands + guard must be <= 21");
   // k-points per pass that fit the device: the solve's panels take ~136 m L bytes per k-point in the mixed solve
   // (four complex64 panels of 3m columns, two double-float blocks and a complex64 residual copy) and 192 m L in the
-  // FP64 solve (four complex128 panels); the budget is 85% of the free memory plus what this context already holds
-  // in those buffers. A batch larger than that is solved in consecutive chunks (the results are the same: the
-  // k-points are independent problems).
+  // FP64 solve (four complex128 panels); the two-pass stencils (general cell, orders above 1) add their scratch of
+  // 4 n entries of 16 bytes per column (64 n m); the chunked reductions' partial sums add a few percent. The budget
+  // is 85% of the free memory plus what this context already holds in those buffers. A batch larger than that is
+  // solved in consecutive chunks; each chunk passes its offset in the caller's list, so that every k-point starts
+  // from the initial block of its own index, as in an unchunked solve (the results agree to the tolerance: the
+  // chunked reductions' summation order depends on the batch size).
   {
     const double Lb = 3.0 * (double)ctx->n;
-    const double per_k = (ctx->opts.precision == PC_PREC_MIXED ? 136.0 : 192.0) * m * Lb;
+    const bool two_pass = ctx->lat || ctx->opts.order > 1;
+    const double per_k = 1.05 * ((ctx->opts.precision == PC_PREC_MIXED ? 136.0 : 192.0) * m * Lb +
+                                 (two_pass ? 64.0 * (double)ctx->n * m : 0.0));
     size_t freeb = 0, totalb = 0;
     PC_CK(cudaMemGetInfo(&freeb, &totalb));
     double held = 0.0;
     for (int i = 0; i < 2; ++i) held += (double)ctx->S[i].bytes + (double)ctx->AS[i].bytes + (double)ctx->X64[i].bytes;
-    held += (double)ctx->R32.bytes;
+    held += (double)ctx->R32.bytes + (double)ctx->kscratch.bytes;
+    for (const auto &kb : ctx->kscratch_x) held += (double)kb.bytes;
     const double budget = 0.85 * ((double)freeb + held);
     int chunk = (int)std::max(1.0, std::min(std::floor(budget / per_k), (double)nk));
     if (ctx->opts.kchunk > 0) chunk = std::min(chunk, ctx->opts.kchunk);
     if (chunk < nk) {
       int status = PC_OK;
       const void *x0 = ctx->x0;  // a caller's initial block (pc_solve_init) covers all nk k-points
+      const int kidx_base = ctx->kidx0;
       for (int b0 = 0; b0 < nk; b0 += chunk) {
         const int nc = std::min(chunk, nk - b0);
+        ctx->kidx0 = kidx_base + b0;
         if (x0)
           ctx->x0 = static_cast<const char *>(x0) + sizeof(float2) * (size_t)b0 * ctx->x0n * (size_t)(3 * ctx->n);
         void *ev = evecs ? static_cast<void *>(static_cast<char *>(evecs) + sizeof(double2) * (size_t)b0 * nbands *
@@ -379,6 +387,7 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
         const int rc = pc_solve(ctx, nc, kpts + 3 * (size_t)b0, nbands, tol, evals + (size_t)b0 * nbands, ev,
                                 iters ? iters + b0 : nullptr, resid ? resid + (size_t)b0 * nbands : nullptr);
         ctx->x0 = x0;
+        ctx->kidx0 = kidx_base;
         if (rc < 0) return rc;
         status = std::max(status, rc);
       }
@@ -499,7 +508,7 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
   int cur = 0;
   const int na0 = (int)act.size();
   RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, Ld * cb * m * nb,
-                [&] { return launch_init_block(nb, L, m, ctx->opts.seed, 0, S[0], sS, st); }));
+                [&] { return launch_init_block(nb, L, m, ctx->opts.seed, ctx->kidx0, S[0], sS, st); }));
   if (ctx->x0) RUN(launch_copy_x0(ctx, 0, nb, PC_C128, S[0], sS, st));
   if (any_zero) RUN(DEFL(na0, S[0]));
   RUN(OP(na0, S[0], AS[0]));

@@ -72,7 +72,7 @@ struct MixedShared {
   void *evecs;
   int status = PC_OK;
   double Ld, nd, fft_flops;
-  bool verbose = false;  // host-side trace of the iteration (stderr), PC_VERBOSE set
+  int verbose = 0;  // host-side trace of the iteration (stderr): PC_VERBOSE = 1 (largest residual), 2 (every column)
 };
 
 struct Group {
@@ -162,7 +162,7 @@ class MixedSolve {
     for (int b = g.b0; b < g.b1; ++b) g.act.push_back(b);
     RUN(set_act(g.act));
     RUN(run_stage(ctx, PC_STAGE_OTHER, 1, 0.0, S.Ld * 8.0 * m * na, [&] {
-      return launch_init_block(na, L, m, ctx->opts.seed, 0, S.F[0], sF, g.st, nullptr, g.d_act, PC_C64);
+      return launch_init_block(na, L, m, ctx->opts.seed, ctx->kidx0, S.F[0], sF, g.st, nullptr, g.d_act, PC_C64);
     }));
     if (ctx->x0) RUN(launch_copy_x0(ctx, g.b0, na, PC_C64, S.F[0], sF, g.st));
     RUN(DEFL(g.act, S.F[0], sF, PC_C64));
@@ -225,14 +225,21 @@ class MixedSolve {
       for (int b : g.act) {
         double mx = 0;
         for (int j = 0; j < nbands; ++j) mx = std::max(mx, relres(b, j));
-        std::fprintf(stderr, "[pc-mixed] it %d k %d phase %d maxres %.3e\n", it, b, S.phase[b], mx);
+        std::fprintf(stderr, "[pc-mixed] it %d k %d phase %d maxres %.3e", it, b, S.phase[b], mx);
+        if (S.verbose > 1)
+          for (int j = 0; j < S.m; ++j) std::fprintf(stderr, " %.2e", relres(b, j));
+        std::fprintf(stderr, "\n");
       }
     // ---- phase 1 -> 2 once the complex64 residual stops falling, at its floor. The floor is eps32 times the stencil's
-    // magnitude over lambda: ~3e-3 for most k-points here, but ~6e-2 near Gamma where the penalty gamma = 2 / |k|^2
-    // is large, so a stall is accepted at any level below 0.25 (the early iterations, whose residual plateaus near 1
-    // while the search space builds up, are not a floor). Stalled: the best residual of the last 5 iterations is not
-    // 30% below the best of the 5 before. The history holds one entry per iteration: a decision pass that repeats an
-    // iteration (phase switch, gamma doubling) does not add one. Also switch below 3e-3, or after 150 iterations.
+    // magnitude (~gamma / h^2) over lambda: ~3e-3 for most k-points of a path at N = 32 and ~3e-2 at N = 64, but
+    // near Gamma, where the lowest bands have small lambda (~|k|^2 / eps), it reaches 1 and above. A short stall is
+    // accepted below 0.25 (the early iterations, whose residual plateaus near 1 while the search space builds up,
+    // are not a floor): the best residual of the last 5 iterations is not 30% below the best of the 5 before. A
+    // long stall is accepted at any level: the best of the last 10 iterations is not 30% below the best of the 10
+    // before (near Gamma at N = 64 the complex64 residual sits at ~2 from iteration ~20 on; without this rule those
+    // k-points waited for the 150-iteration cap). The history holds one entry per iteration: a decision pass that
+    // repeats an iteration (phase switch, gamma doubling) does not add one. Also switch below 3e-3, or after 150
+    // iterations.
     std::vector<int> sw;
     for (int b : act1) {
       double mx = 0;
@@ -241,13 +248,13 @@ class MixedSolve {
       auto &h = S.hist[b];
       if (h.empty() || h.back().first != it) h.push_back({it, mx});
       const int k1 = (int)h.size();
-      bool stalled = false;
-      if (k1 >= 10 && mx < S.p1_stall) {
+      auto stall = [&](int w) {  // best of the last w entries not 30% below the best of the w before
         double recent = 1e300, before = 1e300;
-        for (int q = k1 - 5; q < k1; ++q) recent = std::min(recent, h[q].second);
-        for (int q = k1 - 10; q < k1 - 5; ++q) before = std::min(before, h[q].second);
-        stalled = recent > 0.7 * before;
-      }
+        for (int q = k1 - w; q < k1; ++q) recent = std::min(recent, h[q].second);
+        for (int q = k1 - 2 * w; q < k1 - w; ++q) before = std::min(before, h[q].second);
+        return recent > 0.7 * before;
+      };
+      const bool stalled = (k1 >= 10 && mx < S.p1_stall && stall(5)) || (k1 >= 20 && stall(10));
       if (stalled || mx < S.p1_floor || it - S.p1_start[b] >= 150) sw.push_back(b);
     }
     // ---- phase 2: convergence on FP64 residuals, then Algorithm 4.1
@@ -533,7 +540,7 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
   S.Ld = (double)L;
   S.nd = (double)n;
   S.fft_flops = 3.0 * 2.0 * 5.0 * S.nd * std::log2(S.nd) + 60.0 * S.nd;
-  S.verbose = std::getenv("PC_VERBOSE") != nullptr;
+  S.verbose = std::getenv("PC_VERBOSE") ? std::max(1, std::atoi(std::getenv("PC_VERBOSE"))) : 0;
 
   cudaStream_t st0 = ctx->stream;
   PC_CK(cudaMemcpyAsync(S.d_zero, zero.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st0));

@@ -412,7 +412,7 @@ static int launch_opz_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, void
   // z chunk: enough blocks to fill the GPU several times over, at least 4 planes per chunk
   const long tiles = (long)(N / TX) * (N / TY) * m * nb;
   int ZC = N;
-  while (ZC > 4 && tiles * (N / ZC) < 4L * 152 * 4) ZC >>= 1;
+  while (ZC > 4 && tiles * (N / ZC) < 16L * sm_count()) ZC >>= 1;
   dim3 grid((N / TX) * (N / TY) * (N / ZC), m, nb);
   const T *m0 = std::is_same<T, double>::value ? ctx->m0d.as<T>() : ctx->m0f.as<T>();
   opz_kernel<T, TX, TY><<<grid, TX * TY, smem, ctx->stream>>>(static_cast<const cplx<T> *>(X), sx,

@@ -189,3 +189,51 @@ def test_solve_sphere_fcc_matches_dense(pcmod):
     ref, _ = eigs.lowest_dense(Op, 6)
     assert ref[-1] < 64.0 * float(np.dot(k, k))
     assert np.max(np.abs(out["evals"][0] - ref) / ref) <= 1e-9
+
+
+@pytest.mark.parametrize("name,N", [("triclinic", 8), ("fcc", 16), ("bcc", 16)])
+def test_apply_op_lattice_double_float(pcmod, name, N):
+    """The mixed solve's phase-2 stencil on a general cell: a complex128 block evaluated in double-float arithmetic
+    (PC_C128_DF, ~2^-44 relative rounding per operation) against the oracle's lattice operator, 1e-11 relative to
+    the largest output."""
+    A = LATTICES[name]
+    m0 = lattice_m0(N, A)
+    S = pcmod.Solver(N, 1.0 / m0, lattice=A)
+    g = np.random.default_rng(41 + N)
+    kpts = np.vstack([g.uniform(-3.5, 3.5, (2, 3)), np.zeros((1, 3))])
+    gammas = np.array([2.0 * N, 9.5, 2.0 * N])
+    X = rand_block(N + 13, (3, 2, 3 * N ** 3))
+    Y = S.apply_op(kpts, gammas, to_dev(X.reshape(3, 2, 3, N, N, N)), double_float=True).cpu().numpy()
+    Y = Y.reshape(3, 2, -1)
+    for b in range(3):
+        ref = (mfd.compensated_operator(N, kpts[b], 1.0 / N, m0, gammas[b], 1, A) @ X[b].T).T
+        assert np.max(np.abs(Y[b] - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("name", ["fcc", "triclinic"])
+def test_mixed_solve_lattice_matches_fp64(pcmod, name):
+    """The mixed-precision solve on a general cell (two k-point groups on their own streams, each with its own
+    two-pass stencil scratch) against the FP64 solve of the same cell: eigenvalues within 1e-6 relative, and every
+    returned eigenvector's residual, recomputed with the oracle's lattice operator, at most twice the tolerance
+    (the oracle's operator takes the penalty of eq. pnt_number; the physical eigenvectors do not depend on it up to
+    their divergence, which is of the order of the tolerance). One k-point is a reciprocal-lattice vector (k = 0)."""
+    N, nb, tol = 16, 6, 1e-6
+    A = LATTICES[name]
+    eps = geometry.eps_edges(N, SPHERES, 1.0, A)
+    m0 = 1.0 / eps
+    G = 2.0 * np.pi * np.linalg.inv(A).T @ np.array([0.0, 1.0, 0.0])
+    kpts = np.array([[0.4, 0.8, -0.2], [1.0, -0.3, 0.6], [2.0, 1.0, 0.5], G])
+    o64 = pcmod.Solver(N, eps, lattice=A).solve(kpts, nb, tol)
+    sm = pcmod.Solver(N, eps, lattice=A, precision=pcmod.pc.PC_PREC_MIXED, groups=2)
+    om = sm.solve(kpts, nb, tol, want_vectors=True)
+    assert o64["status"] == 0 and om["status"] == 0
+    assert np.max(np.abs(om["evals"] - o64["evals"]) / o64["evals"]) <= 1e-6
+    assert np.max(om["resid"]) <= tol
+    V = om["evecs"].cpu().numpy().reshape(len(kpts), nb, -1)
+    for b, k in enumerate(kpts):
+        kr = eigs.reduce_by_reciprocal_lattice(k, A)
+        Op = mfd.compensated_operator(N, kr, 1.0 / N, m0, mfd.penalty_gamma(1.0 / N, kr), 1, A)
+        X = V[b].T
+        R = Op @ X - X * om["evals"][b][None, :]
+        rel = np.linalg.norm(R, axis=0) / (om["evals"][b] * np.linalg.norm(X, axis=0))
+        assert np.max(rel) <= 2.0 * tol, (b, rel)

@@ -1,9 +1,13 @@
-"""pc_gram_pair_noalloc, the allocation-free Gram pair, agrees with pc_gram_pair.
+"""pc_gram_pair_noalloc, the allocation-free Gram pair, agrees with pc_gram_pair and with numpy's own products.
 
 Some callers cannot allocate device memory (a fixed memory budget, an application allocator that must own every
 allocation, or a loop where cudaMalloc/cudaFree would synchronise the device); this entry point serves them from a
 fixed array inside the library. The test calls both entry points through the C ABI on the same inputs, twice in a
-row with different data, so that any state left in the shared array by the first call would show up in the second.
+row with different data, so that any state left in the shared array by the first call would show up in the second,
+and checks both against S^H S and S^H AS formed by numpy in complex128 from the same (rounded) inputs.
+
+Tolerances: complex128, 1e-13 sqrt(L) times the largest entry; complex64 (FP32 products, partial sums in FP32 over
+row chunks), 4e-6 |s_i| |a_j| per entry, the FP32 accuracy bound of the library's Gram products.
 """
 import ctypes
 
@@ -31,6 +35,13 @@ def panel(seed, nb, p, L, dtype):
     return (torch.from_numpy(S).to(dtype).cuda().contiguous(), torch.from_numpy(AS).to(dtype).cuda().contiguous())
 
 
+def numpy_pair(S, AS):
+    """G = S^H S and H = S^H AS per k-point, complex128, from the device inputs' own values."""
+    s = S.cpu().numpy().astype(np.complex128)
+    a = AS.cpu().numpy().astype(np.complex128)
+    return s.conj() @ s.transpose(0, 2, 1), s.conj() @ a.transpose(0, 2, 1)
+
+
 def call(pcmod, name, S, AS):
     lib = pcmod.lib()
     nb, p, L = S.shape
@@ -51,10 +62,18 @@ def test_noalloc_gram_pair_matches_allocating_entry(pcmod, dtype):
         S, AS = panel(seed, nb, p, L, dtype)
         G0, H0 = call(pcmod, "pc_gram_pair", S, AS)
         G1, H1 = call(pcmod, "pc_gram_pair_noalloc", S, AS)
-        scale = np.max(np.abs(G0))
-        tol = (1e-13 if dtype == torch.complex128 else 1e-5) * np.sqrt(L) * scale
-        assert np.max(np.abs(G1 - G0)) <= tol
-        assert np.max(np.abs(H1 - H0)) <= tol * 2.0
+        Gr, Hr = numpy_pair(S, AS)
+        if dtype == torch.complex128:
+            tolG = 1e-13 * np.sqrt(L) * np.max(np.abs(Gr))
+            tolH = 1e-13 * np.sqrt(L) * np.max(np.abs(Hr))
+        else:
+            ns = np.linalg.norm(S.cpu().numpy().astype(np.complex128), axis=2)
+            na = np.linalg.norm(AS.cpu().numpy().astype(np.complex128), axis=2)
+            tolG = 4e-6 * ns[:, :, None] * ns[:, None, :]
+            tolH = 4e-6 * ns[:, :, None] * na[:, None, :]
+        for G, H in ((G1, H1), (G0, H0)):
+            assert np.all(np.abs(G - Gr) <= tolG)
+            assert np.all(np.abs(H - Hr) <= tolH)
 
 
 def test_noalloc_rejects_oversized_request(pcmod):
