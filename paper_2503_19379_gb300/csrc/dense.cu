@@ -152,8 +152,12 @@ static int gram_chunks(int nb, long L) {
   return (int)std::min<long>(std::min(want, maxc), 256);
 }
 
+// partial sums per k-point that either Gram path may write: the CUDA-core kernels' chunks, or the tensor-core
+// kernel's (at least tc_min_chunks)
+static int gram_scratch_chunks(int nb, long L) { return std::max(gram_chunks(nb, L), tc_min_chunks(L)); }
+
 size_t gram_scratch_bytes(int nb, long L, int p, int q) {
-  return sizeof(double2) * (size_t)nb * gram_chunks(nb, L) * p * q;
+  return sizeof(double2) * (size_t)nb * gram_scratch_chunks(nb, L) * p * q;
 }
 
 int launch_gram(int nb, long L, int p, int q, int dtype, const void *A, long sa, const void *B, long sb, void *G,
@@ -297,7 +301,7 @@ __global__ void gram_pair_reduce_kernel(const double2 *__restrict__ partG, const
 }
 
 size_t gram_pair_scratch_bytes(int nb, long L, int p) {
-  return 2 * sizeof(double2) * (size_t)nb * gram_chunks(nb, L) * p * p;
+  return 2 * sizeof(double2) * (size_t)nb * gram_scratch_chunks(nb, L) * p * p;
 }
 
 void launch_gram_pair_reduce(int nb, int nchunk, int p, const double2 *part, const int *act, void *G, void *H,
@@ -363,7 +367,7 @@ int launch_gram_pair(int nb, long L, int p, int dtype, const void *S, const void
 }
 
 size_t gram_pair_coupled_scratch_bytes(int nb, long L, int p, int q2) {
-  return std::max({sizeof(double2) * (size_t)nb * gram_chunks(nb, L) * p * (2 * p + q2),
+  return std::max({sizeof(double2) * (size_t)nb * gram_scratch_chunks(nb, L) * p * (2 * p + q2),
                    gram_pair_scratch_bytes(nb, L, p), gram_scratch_bytes(nb, L, q2, p)});
 }
 

@@ -331,31 +331,44 @@ __global__ void __launch_bounds__(ZCfg<N>::THREADS) fft_zsym_kernel(const float2
 #pragma unroll
     for (int a = 0; a < N1; ++a) S[(c * N + t + N1 * q + N2 * a) * U + u] = w[q * N1 + a];
   __syncthreads();
-  // the symbol's inverse at each of this thread's modes, for its own component c
-  const float fac = kp[b].pfacf;  // (gamma - 1) / gamma
-  const float scale = 1.0f / (float)n;
-  const float2 e1 = dxy[u * 3 + 0], e2 = dxy[u * 3 + 1], e3 = dxy[u * 3 + 2];
+  // the symbol's inverse, one mode (all three components) per thread and step: consecutive threads on consecutive
+  // columns, each mode's sigma, reciprocal and d^T r formed once
+  {
+    const float fac = kp[b].pfacf;  // (gamma - 1) / gamma
+    const float scale = 1.0f / (float)n;
+    for (int i = tid; i < U * N; i += CF::THREADS) {
+      const int uu = i % U, kz = i / U;
+      const float2 d1 = cadd(dxy[uu * 3 + 0], dz[kz]), d2 = cadd(dxy[uu * 3 + 1], dz[N + kz]);
+      const float2 d3 = cadd(dxy[uu * 3 + 2], dz[2 * N + kz]);
+      const float sigma = d1.x * d1.x + d1.y * d1.y + d2.x * d2.x + d2.y * d2.y + d3.x * d3.x + d3.y * d3.y;
+      float2 *m = S + kz * U + uu;
+      float2 r1 = m[0], r2 = m[N * U], r3 = m[2 * N * U];
+      if (!(sigma > 0.f)) {
+        r1 = r2 = r3 = make_float2(0.f, 0.f);
+      } else {
+        const float rs = __frcp_rn(sigma);
+        if (!laplacian) {
+          // r_c - (gamma - 1) / (gamma sigma) conj(d_c) (d^T r)
+          const float2 sd = cscale(cadd(cadd(cmul(d1, r1), cmul(d2, r2)), cmul(d3, r3)), fac * rs);
+          r1 = csub(r1, cmulc(d1, sd));
+          r2 = csub(r2, cmulc(d2, sd));
+          r3 = csub(r3, cmulc(d3, sd));
+        }
+        const float f = scale * rs;
+        r1 = cscale(r1, f);
+        r2 = cscale(r2, f);
+        r3 = cscale(r3, f);
+      }
+      m[0] = r1;
+      m[N * U] = r2;
+      m[2 * N * U] = r3;
+    }
+  }
+  __syncthreads();
 #pragma unroll
   for (int q = 0; q < Q; ++q)
 #pragma unroll
-    for (int a = 0; a < N1; ++a) {
-      const int kz = t + N1 * q + N2 * a;
-      const float2 d1 = cadd(e1, dz[kz]), d2 = cadd(e2, dz[N + kz]), d3 = cadd(e3, dz[2 * N + kz]);
-      const float sigma = d1.x * d1.x + d1.y * d1.y + d2.x * d2.x + d2.y * d2.y + d3.x * d3.x + d3.y * d3.y;
-      float2 o = w[q * N1 + a];
-      if (!(sigma > 0.f)) {
-        o = make_float2(0.f, 0.f);
-      } else {
-        if (!laplacian) {
-          const float2 r1 = S[(0 * N + kz) * U + u], r2 = S[(1 * N + kz) * U + u], r3 = S[(2 * N + kz) * U + u];
-          const float2 sd = cadd(cadd(cmul(d1, r1), cmul(d2, r2)), cmul(d3, r3));  // d^T r
-          const float2 dc = c == 0 ? d1 : (c == 1 ? d2 : d3);
-          o = csub(o, cscale(cmulc(dc, sd), fac / sigma));  // r_c - (gamma-1)/(gamma sigma) conj(d_c) (d^T r)
-        }
-        o = cscale(o, scale / sigma);
-      }
-      w[q * N1 + a] = o;
-    }
+    for (int a = 0; a < N1; ++a) w[q * N1 + a] = S[(c * N + t + N1 * q + N2 * a) * U + u];
   // inverse along z: the length-N1 DFTs first (over k1), twiddles, exchange, the length-N2 DFTs (over k2)
 #pragma unroll
   for (int q = 0; q < Q; ++q) dft<N1, true>(w + q * N1);

@@ -11,12 +11,15 @@
 // Precision: every FP32 value x is split x = hi + lo, hi = tf32(x), lo = tf32(x - hi) (round to nearest), and the
 // product is formed as hi.hi + (hi.lo + lo.hi); the neglected lo.lo term and the rounding of lo are ~2^-22 relative.
 // The tensor core's FP32 accumulator does not round to nearest on every addition (its error grows with the number
-// of additions into one accumulator), so hi.hi and the two small cross terms go to separate TMEM accumulators that
-// are drained every TC_GROUP K tiles into FP32 registers (round-to-nearest CUDA-core additions) and restarted; two
-// accumulator sets alternate so that the MMAs run on while one set is drained. Every drained group holds at most
-// 4 TC_GROUP additions of hi.hi, which keeps the result at the accuracy of an FP32 CUDA-core product.
+// of additions into one accumulator), so hi.hi goes to TMEM accumulators that are drained every TC_GROUP K tiles
+// into FP32 registers (round-to-nearest CUDA-core additions) and restarted; two hi.hi accumulators alternate so
+// that the MMAs run on while one is drained. Every drained group holds at most 4 TC_GROUP additions of hi.hi,
+// which keeps the result at the accuracy of an FP32 CUDA-core product. The two cross terms, ~2^-11 of hi.hi, go to
+// a third accumulator that is drained once at the end of the chunk: its accumulation error is 2^-11 times that of
+// an undrained hi.hi accumulator, far below FP32 rounding. Three accumulators of N columns fit TMEM's 512 columns
+// for N <= 160, which takes the mixed solve's coupled pencil at 19 block columns (N = 2 * 64 + 32).
 //
-// Structure (one CTA per (k-point, K-chunk), 16 warps):
+// Structure (one CTA per (k-point, K-chunk), 20 warps):
 //   warp 0       one thread issues 2D tensor-map copies (cp.async.bulk.tensor, 128-byte swizzle) of the A and B1
 //                tiles (32 floats x rows) into a staging ring of up to 4 stages of 2 K tiles each;
 //   warp 1       one thread issues the tcgen05.mma chain (12 per 32-float K tile) into the TMEM accumulators;
@@ -24,9 +27,9 @@
 //                (rows of 128 bytes, 16-byte chunks XOR-ed with the row index mod 8, as the copy left them; every
 //                block of rows starts at a multiple of 8, so a chunk keeps its position), double buffered against
 //                the MMAs;
-//   warps 8..15  drain the accumulators (tcgen05.ld: TMEM lane quarter = warp % 4, two warps per quarter splitting
-//                the columns) into registers and finally write FP64 partial sums per chunk, which the Gram reduction
-//                kernels add up.
+//   warps 8..19  drain the accumulators (tcgen05.ld: TMEM lane quarter = warp % 4, three warps per quarter
+//                splitting the columns in 32-column chunks) into registers and finally write FP64 partial sums per
+//                chunk, which the Gram reduction kernels add up.
 // Every wait is bounded in time: a wait that runs out raises an abort flag that the other roles observe, copies and
 // MMAs in flight are drained (again with a bound), TMEM is released and an error flag is left for the host.
 #include <cuda.h>
@@ -42,13 +45,15 @@ namespace pc {
 
 namespace {
 
-constexpr int TC_THREADS = 512;
+constexpr int TC_THREADS = 640;
 constexpr int TC_KT = 32;     // floats of K per tile (one 128-byte swizzle row)
 constexpr int TC_SPT = 2;     // K tiles per staging stage: each row arrives as a 256-byte run
 constexpr int TC_M = 128;     // MMA rows
 constexpr int TC_GROUP = 2;   // K tiles per accumulator drain
 constexpr int TC_NTR = 6;     // transform warps (2..7)
-constexpr int TC_NDR = 8;     // drain warps (8..15)
+constexpr int TC_NDR = 12;    // drain warps (8..19), three per TMEM lane quarter
+constexpr int TC_NMAX = 160;  // MMA columns: three accumulators of N columns in the 512 TMEM columns
+constexpr int TC_MAXT = 512;  // K tiles per chunk at most: the drain's FP32 running sums span <= 256 groups
 constexpr unsigned long long TC_WAIT_NS = 1000000000ull;  // 1 s: a kernel call takes milliseconds
 
 __device__ int g_gram_tc_error = 0;
@@ -134,25 +139,30 @@ __device__ __forceinline__ float tf32_rna(float x) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
-// 32 consecutive accumulator columns of this warp's 32 TMEM lanes
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 16 consecutive accumulator columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  // the wait names the registers so that no use of them is scheduled before it
   asm volatile("tcgen05.wait::ld.sync.aligned;"
                : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
                  "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
-                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
-                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 "+r"(r[15])
                :
                : "memory");
+}
+// adds 32 accumulator columns (two 16-column loads) into acc
+__device__ __forceinline__ void tmem_add32(uint32_t taddr, float (&acc)[32]) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    uint32_t r[16];
+    tmem_ld16(taddr + (uint32_t)(16 * s), r);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[16 * s + k] += __uint_as_float(r[k]);
+  }
 }
 
 struct TcArgs {
@@ -163,13 +173,13 @@ struct TcArgs {
   int RB, q2;           // pair mode with a coupling block: B1 = [B1a (QB - RB rows); R (RB rows, q2 used)], the
                         // second part from its own tensor (RB = 0: none)
   long cppR;            // columns per k-point panel of R
-  int N;                // MMA N: QB + PB when pair (B = [B1; A]), else QB (multiple of 16, <= 128)
+  int N;                // MMA N: QB + PB when pair (B = [B1; A]), else QB (multiple of 16, <= TC_NMAX)
   int pair;             // pair: outputs G = A^H A and H = A^H B1 (upper triangles); else A^H B1 (p x q)
   int transpose;        // general mode: write the conjugate transpose (B1^H A, q x p) instead
   int ns;               // staging stages
   int ktiles, tpc, nchunk;
-  int nc;                // accumulator columns per slot (N rounded up to 32)
-  uint32_t tmem_cols;    // allocated TMEM columns (4 nc rounded up to a power of two)
+  int nc;                // accumulator columns (N rounded up to 32): hi.hi sets at 0 and nc, cross terms at 2 nc
+  uint32_t tmem_cols;    // allocated TMEM columns (3 nc rounded up to a power of two)
   uint32_t idesc;
   double *partG, *partH;  // pair: [nb][nchunk][p][p] double2 each; general: partH = [nb][nchunk][p][q]
   double *partQ;          // coupling block (RB > 0): R^H A as [nb][nchunk][q2][p] double2
@@ -278,7 +288,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a, 
       for (int g = 0; g < ngroup && ok; ++g) {
         const int v = g & 1;
         if (!bar_wait(bar_aempty + 8u * v, ((g >> 1) & 1) ^ 1, abort)) break;
-        const uint32_t dA = tmem + (uint32_t)(v * 2 * a.nc), dB = dA + (uint32_t)a.nc;
+        const uint32_t dA = tmem + (uint32_t)(v * a.nc), dX = tmem + (uint32_t)(2 * a.nc);
         const int t1 = min(ntile, (g + 1) * TC_GROUP);
         for (int t = g * TC_GROUP; t < t1; ++t) {
           const int u = t & 1;
@@ -296,9 +306,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a, 
             const uint64_t ahi = sdesc(hi + aoff + ko), alo = sdesc(lo + aoff + ko);
             const uint64_t bhi = sdesc(hi + ko), blo = sdesc(lo + ko);
             const uint32_t acc = (first && ks == 0) ? 0u : 1u;
+            const uint32_t accx = (t == 0 && ks == 0) ? 0u : 1u;  // cross terms: the whole chunk in one accumulator
             mma_tf32(dA, ahi, bhi, a.idesc, acc);
-            mma_tf32(dB, ahi, blo, a.idesc, acc);
-            mma_tf32(dB, alo, bhi, a.idesc, 1u);
+            mma_tf32(dX, ahi, blo, a.idesc, accx);
+            mma_tf32(dX, alo, bhi, a.idesc, 1u);
           }
           mma_commit(bar_free + 8u * u);
         }
@@ -356,9 +367,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a, 
     }
   } else {
     // ------------------------------------------------ accumulator drain and epilogue
-    const int dw = warp - (2 + TC_NTR);  // 0..7
+    const int dw = warp - (2 + TC_NTR);  // 0..11
     const int qd = warp & 3;            // TMEM lane quarter
-    const int half = dw >> 2;           // column chunks half, half + 2
+    const int slot = dw >> 2;           // column chunks slot, slot + 3 (32 columns each)
     float acc[2][32];
 #pragma unroll
     for (int h = 0; h < 2; ++h)
@@ -373,23 +384,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a, 
         break;
       }
       tc_fence_after();
-      const uint32_t dA = tmem + lanebase + (uint32_t)(v * 2 * a.nc), dB = dA + (uint32_t)a.nc;
+      const uint32_t dA = tmem + lanebase + (uint32_t)(v * a.nc);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int c0 = (half + 2 * h) * 32;
-        if (c0 < a.N) {
-          uint32_t r[32];
-          tmem_ld32(dA + (uint32_t)c0, r);
-#pragma unroll
-          for (int k = 0; k < 32; ++k) acc[h][k] += __uint_as_float(r[k]);
-          tmem_ld32(dB + (uint32_t)c0, r);
-#pragma unroll
-          for (int k = 0; k < 32; ++k) acc[h][k] += __uint_as_float(r[k]);
-        }
+        const int c0 = (slot + 3 * h) * 32;
+        if (c0 < a.N) tmem_add32(dA + (uint32_t)c0, acc[h]);
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) bar_arrive(bar_aempty + 8u * v);
+    }
+    // the cross terms, once every MMA of the chunk has completed
+    if (ok && bar_wait(bar_done, 0, abort)) {
+      tc_fence_after();
+      const uint32_t dX = tmem + lanebase + (uint32_t)(2 * a.nc);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c0 = (slot + 3 * h) * 32;
+        if (c0 < a.N) tmem_add32(dX + (uint32_t)c0, acc[h]);
+      }
+    } else {
+      ok = false;
     }
     if (__all_sync(0xffffffffu, ok)) {
       const int i = qd * 32 + lane;  // accumulator row
@@ -399,7 +414,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gram_tc_kernel(const TcArgs a, 
         const long oG = ((long)bi * a.nchunk + chunk) * a.p * (a.pair ? a.p : a.q);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int c0 = (half + 2 * h) * 32;
+          const int c0 = (slot + 3 * h) * 32;
 #pragma unroll
           for (int k = 0; k < 32; ++k) {
             const int j = c0 + k;
@@ -445,14 +460,18 @@ size_t tc_smem(int PB, int QB, int ns) {
   return 1024 + 4 * (size_t)(QB + TC_M) * 128 + (size_t)ns * TC_SPT * (PB + QB) * 128 + 8 * (2 * ns + 9) + 16;
 }
 
-// chunks per k-point: whole waves of one CTA per SM where possible, within the partial-sum scratch
+// chunks per k-point: at least ktiles / TC_MAXT (the drain adds each chunk's K tiles in FP32 registers, whose
+// rounding grows with the number of additions: a chunk of thousands of tiles, as a large batch with few chunks per
+// k-point would have, leaves errors of several 1e-6 relative in the Gram entries, enough to stall LOBPCG near a
+// relative residual of 1e-6), and whole waves of one CTA per SM where possible, within the partial-sum scratch
 int tc_chunks(int nb, int ktiles, long maxc) {
   const int nsm = sm_count();
+  const long cmin = std::min<long>((ktiles + TC_MAXT - 1) / TC_MAXT, maxc);
   int best = 1;
   double beff = 0.0;
-  for (int w = 1; w <= 8; ++w) {
-    long c = std::max<long>(1, (long)w * nsm / nb);
-    c = std::min<long>({c, (long)ktiles, maxc});
+  for (int w = 1; w <= 64; ++w) {
+    long c = std::max<long>(cmin, (long)w * nsm / nb);
+    c = std::max<long>(1, std::min<long>({c, (long)ktiles, maxc}));
     const long ctas = (long)nb * c;
     const double eff = (double)ctas / ((double)nsm * ((ctas + nsm - 1) / nsm));
     if (eff > beff + 0.02) {
@@ -507,7 +526,7 @@ int launch_tc(int nb, int nb_alloc, long L, int p, int q, bool pair, const void 
   if (a.RB > 0 && (2 * a.PB + a.RB) % 16 != 0) a.RB += 8;  // the MMA's N must be a multiple of 16
   a.QB = pair ? a.PB + a.RB : (q + 15) / 16 * 16;
   a.N = pair ? a.QB + a.PB : a.QB;
-  if (a.N > 128) return PC_EUNSUPPORTED;
+  if (a.N > TC_NMAX) return PC_EUNSUPPORTED;
   a.pair = pair ? 1 : 0;
   a.transpose = transpose ? 1 : 0;
   a.ktiles = (int)(2 * L / TC_KT);
@@ -527,7 +546,7 @@ int launch_tc(int nb, int nb_alloc, long L, int p, int q, bool pair, const void 
   a.idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(a.N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
   a.nc = (a.N + 31) / 32 * 32;
   a.tmem_cols = 32;
-  while (a.tmem_cols < (uint32_t)(4 * a.nc)) a.tmem_cols *= 2;
+  while (a.tmem_cols < (uint32_t)(3 * a.nc)) a.tmem_cols *= 2;
   a.partG = reinterpret_cast<double *>(part);
   a.partH = pair ? reinterpret_cast<double *>(part + (size_t)nb * c * p * p) : reinterpret_cast<double *>(part);
   a.partQ = a.q2 > 0 ? reinterpret_cast<double *>(part + 2 * (size_t)nb * c * p * p) : nullptr;
@@ -576,6 +595,9 @@ bool tc_shape_ok(long L, int p, int q, const void *A, long sa, const void *B, lo
 
 }  // namespace
 
+// chunks per k-point that the tensor-core Gram takes at least, for panels of L rows (partial-sum scratch sizing)
+int tc_min_chunks(long L) { return (int)((2 * L / TC_KT + TC_MAXT - 1) / TC_MAXT); }
+
 // G = S^H S and H = S^H AS (complex64 panels, p <= 64) on the tensor cores; PC_EUNSUPPORTED when the shape or
 // alignment does not fit (the caller then takes the CUDA-core kernel).
 int launch_gram_pair_tc(int nb, long L, int p, const void *S, const void *AS, long ss, void *G, void *H,
@@ -592,7 +614,7 @@ int launch_gram_pair_tc(int nb, long L, int p, const void *S, const void *AS, lo
 }
 
 // G = S^H S, H = S^H AS and RQ = R^H S (q2 x p, row stride p) in one pass over [S | AS | R] (complex64, 2 p + q2
-// rounded up <= 128 MMA columns); PC_EUNSUPPORTED as above.
+// rounded up <= 160 MMA columns); PC_EUNSUPPORTED as above.
 int launch_gram_pair_coupled_tc(int nb, long L, int p, int q2, const void *S, const void *AS, long ss, const void *R,
                                 long sr, void *G, void *H, void *RQ, void *scratch, size_t scratch_bytes,
                                 cudaStream_t st, const int *act, int nb_alloc, long sg, long srq) {

@@ -239,6 +239,8 @@ int launch_gram_pair_coupled(int nb, long L, int p, int q2, int dtype, const voi
 size_t gram_pair_coupled_scratch_bytes(int nb, long L, int p, int q2);
 int launch_gram_tc(int nb, long L, int p, int q, const void *A, long sa, const void *B, long sb, void *G,
                    void *scratch, size_t scratch_bytes, cudaStream_t st, const int *act, int nb_alloc, long sg);
+// chunks per k-point that the tensor-core Gram takes at least for panels of L rows (its partial sums need that many)
+int tc_min_chunks(long L);
 // reads and clears the time-out flag of the tensor-core Gram kernel (call after a synchronisation)
 int gram_tc_check();
 // Y = S C (+ Z, a complex64 addend, if Z is not null); arithmetic in the precision of dtype

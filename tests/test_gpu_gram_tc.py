@@ -80,10 +80,12 @@ def test_gram_pair_split_exposes_lo(pcmod):
 
 
 @pytest.mark.parametrize("nb,p,q,L", [(3, 48, 16, 3 * 32 ** 3), (2, 32, 16, 4096), (2, 40, 9, 3 * 16 ** 3),
-                                      (4, 8, 3, 512), (1, 64, 16, 2048)])
+                                      (4, 8, 3, 512), (1, 64, 16, 2048), (2, 57, 19, 3 * 32 ** 3),
+                                      (1, 64, 40, 2048)])
 def test_gram_pair_coupled_c64(pcmod, nb, p, q, L):
     """G = S^H S, H = S^H AS and RQ = R^H S from one pass over [S | AS | R] (the mixed solve's pencil and coupling
-    block). The last case (2 p + q beyond 128 MMA columns) takes the separate pair and general products."""
+    block). (57, 19) is the pencil of 12 bands with 7 guard columns (MMA N = 2 * 64 + 32 = 160, the widest one pass
+    takes); the last case (2 p + q beyond 160 MMA columns) takes the separate pair and general products."""
     S = rand_c64(p + 3 * q + L, (nb, p, L))
     AS = (S * np.random.default_rng(L + 1).uniform(0.5, 4.0, L)[None, None, :]).astype(np.complex64)
     R = rand_c64(q + 17, (nb, q, L))

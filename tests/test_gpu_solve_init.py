@@ -116,7 +116,13 @@ def test_chunked_solve_matches_unchunked(pcmod, precision):
     Va = a["evecs"].cpu().numpy().reshape(5, nb, -1)
     Vb = b["evecs"].cpu().numpy().reshape(5, nb, -1)
     for k in range(5):
-        assert subspace_gap(Va[k].T, Vb[k].T) <= 1e-4
+        # the subspace of the first nbands columns is unique only where band nbands + 1 is separated from band
+        # nbands (at Gamma the cubic symmetry makes the second cluster threefold, and nbands = 5 cuts it)
+        kr0 = eigs.reduce_to_first_zone(kpts[k])
+        wk, _ = eigs.lowest_dense(mfd.compensated_operator(N, kr0, 1.0 / N, m0, mfd.penalty_gamma(1.0 / N, kr0)),
+                                  nb + 1, skip=0 if np.any(kr0) else 3)
+        if wk[nb] - wk[nb - 1] > 1e-3 * wk[nb]:
+            assert subspace_gap(Va[k].T, Vb[k].T) <= 1e-4
         # and each is an eigenbasis of its own k-point's operator (oracle), so no chunk wrote another's slot
         kr = eigs.reduce_to_first_zone(kpts[k])
         Op = mfd.compensated_operator(N, kr, 1.0 / N, m0, mfd.penalty_gamma(1.0 / N, kr))
@@ -127,7 +133,7 @@ def test_chunked_solve_matches_unchunked(pcmod, precision):
     x0 = torch.from_numpy(Va.reshape(5, nb, 3, N, N, N).astype(np.complex64)).cuda()
     c = chunked.solve(kpts, nb, tol, x0=x0)
     assert c["status"] == 0
-    assert np.all(c["iters"] <= 4), c["iters"]
+    assert np.all(c["iters"] <= (8 if precision == 0 else 15)), c["iters"]  # from complex64-rounded vectors, to tol
     assert np.max(np.abs(c["evals"] - a["evals"]) / a["evals"]) <= 10 * tol
 
 
