@@ -494,7 +494,7 @@ int launch_precond(pc_ctx *ctx, int nb, int m, int dtype, const void *R, long sr
   if (nb == 0 || m == 0) return PC_OK;
   if (dtype == PC_C128) return launch_precond_t<double>(ctx, nb, m, R, sr, W, sw, act);
   {
-    const int rc = launch_precond_c64(ctx, nb, m, R, sr, W, sw, act);  // fft_c64.cu: N <= 64, cube and lattice
+    const int rc = launch_precond_c64(ctx, nb, m, R, sr, W, sw, act);  // fft_c64.cu: N <= 128, cube and lattice
     if (rc != PC_EUNSUPPORTED) return rc;
   }
   // the register path's symbols are per axis; a general lattice takes the shared-memory path

@@ -1,5 +1,5 @@
 // Complex64 FFT preconditioner W = P^{-1} R (Section 5.2, Algorithm 5.1, with the 3x3 mode symbol of
-// eq. penalised_marix) for N = 8 .. 64: three passes over the block, each one HBM read and one HBM write.
+// eq. penalised_marix) for N = 8 .. 128: three passes over the block, each one HBM read and one HBM write.
 //   1. forward transforms along x and y of one (component, z) plane held in shared memory;
 //   2. along z, all three components of U consecutive (x, y) columns: forward transform, the exact inverse of the
 //      mode's 3x3 symbol sigma I + (gamma - 1) conj(d) d^T times 1/N^3, inverse transform;
@@ -424,7 +424,7 @@ int launch_precond_c64_n(pc_ctx *ctx, int nb, int m, const float2 *R, long sr, f
 
 }  // namespace
 
-// complex64 path for 8 <= N <= 64 (cube and general lattice); PC_EUNSUPPORTED for other sizes
+// complex64 path for 8 <= N <= 128 (cube and general lattice); PC_EUNSUPPORTED for other sizes
 int launch_precond_c64(pc_ctx *ctx, int nb, int m, const void *R, long sr, void *W, long sw, const int *act) {
   const float2 *Rf = static_cast<const float2 *>(R);
   float2 *Wf = static_cast<float2 *>(W);
@@ -433,6 +433,7 @@ int launch_precond_c64(pc_ctx *ctx, int nb, int m, const void *R, long sr, void 
     case 16: return launch_precond_c64_n<16>(ctx, nb, m, Rf, sr, Wf, sw, act);
     case 32: return launch_precond_c64_n<32>(ctx, nb, m, Rf, sr, Wf, sw, act);
     case 64: return launch_precond_c64_n<64>(ctx, nb, m, Rf, sr, Wf, sw, act);
+    case 128: return launch_precond_c64_n<128>(ctx, nb, m, Rf, sr, Wf, sw, act);
     default: return PC_EUNSUPPORTED;
   }
 }

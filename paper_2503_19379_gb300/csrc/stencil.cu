@@ -284,6 +284,230 @@ __global__ void __launch_bounds__(TX * TY, 6) opz_kernel(const cplx<T> *__restri
   }
 }
 
+// ------------------------------------------------------------------------------------------------ row-warp z march
+// Complex64 Op X for N = 32 XPL (XPL = 1, 2, 4 consecutive x values per lane): one warp per grid row, so that the
+// x-neighbours of every point are in the same warp (register shuffles, with the periodic wrap inside the warp), the
+// z-neighbours stay in registers along the z walk, and only the y-neighbours go through shared memory. A CTA holds
+// TY + 2 warps on rows y0 - 1 .. y0 + TY; warp w loads v on its row R_w = y0 - 1 + w, forms e = M0 A' v on R_w
+// (w >= 1; needs v at R_w - 1) and c = B v on R_w (w <= TY; needs v at R_w + 1), and warps 1..TY write
+// y = A e + gamma B' c on their rows (e at R_w + 1 and c at R_w - 1 from the neighbouring warps). Per z plane: the
+// plane of v in shared memory (three components), e1 and e3 (the components needed at +y) and c, double buffered
+// where a plane is read one step later; two barriers per plane.
+template <int XPL> struct OpzRow {
+  static constexpr int TY = 8;
+  static constexpr int WARPS = TY + 2;
+  static constexpr int N = 32 * XPL;
+  // v [2][3][WARPS][N], e (e1, e3) [2][2][WARPS][N], c [WARPS][N]
+  static constexpr size_t smem() { return sizeof(float2) * (size_t)(2 * 3 + 2 * 2 + 1) * WARPS * N; }
+};
+
+template <int XPL> __device__ __forceinline__ void ld_row(const float2 *p, float2 (&v)[XPL]) {
+  if constexpr (XPL == 1) {
+    v[0] = *p;
+  } else {
+#pragma unroll
+    for (int i = 0; i < XPL; i += 2) {
+      const float4 q = *reinterpret_cast<const float4 *>(p + i);
+      v[i] = make_float2(q.x, q.y);
+      v[i + 1] = make_float2(q.z, q.w);
+    }
+  }
+}
+template <int XPL> __device__ __forceinline__ void st_row(float2 *p, const float2 (&v)[XPL]) {
+  if constexpr (XPL == 1) {
+    *p = v[0];
+  } else {
+#pragma unroll
+    for (int i = 0; i < XPL; i += 2)
+      *reinterpret_cast<float4 *>(p + i) = make_float4(v[i].x, v[i].y, v[i + 1].x, v[i + 1].y);
+  }
+}
+template <int XPL> __device__ __forceinline__ void ld_row_m0(const float *p, float (&v)[XPL]) {
+  if constexpr (XPL == 1) {
+    v[0] = *p;
+  } else if constexpr (XPL == 2) {
+    const float2 q = *reinterpret_cast<const float2 *>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < XPL; i += 4) {
+      const float4 q = *reinterpret_cast<const float4 *>(p + i);
+      v[i] = q.x;
+      v[i + 1] = q.y;
+      v[i + 2] = q.z;
+      v[i + 3] = q.w;
+    }
+  }
+}
+// the value at x - 1 of each of this lane's points (the previous lane's last point for the first one, periodic)
+template <int XPL> __device__ __forceinline__ void xprev(const float2 (&v)[XPL], float2 (&o)[XPL], int lane) {
+  const int src = (lane + 31) & 31;
+  o[0] = make_float2(__shfl_sync(0xffffffffu, v[XPL - 1].x, src), __shfl_sync(0xffffffffu, v[XPL - 1].y, src));
+#pragma unroll
+  for (int i = 1; i < XPL; ++i) o[i] = v[i - 1];
+}
+// the value at x + 1 of each of this lane's points (the next lane's first point for the last one, periodic)
+template <int XPL> __device__ __forceinline__ void xnext(const float2 (&v)[XPL], float2 (&o)[XPL], int lane) {
+  const int src = (lane + 1) & 31;
+  o[XPL - 1] = make_float2(__shfl_sync(0xffffffffu, v[0].x, src), __shfl_sync(0xffffffffu, v[0].y, src));
+#pragma unroll
+  for (int i = 0; i + 1 < XPL; ++i) o[i] = v[i + 1];
+}
+
+template <int XPL>
+__global__ void __launch_bounds__(OpzRow<XPL>::WARPS * 32) opz_row_kernel(const float2 *__restrict__ X, long sx,
+                                                                          float2 *__restrict__ Y, long sy,
+                                                                          const float *__restrict__ m0,
+                                                                          const KParam *__restrict__ kp,
+                                                                          const int *__restrict__ act, int ZC) {
+  using CF = OpzRow<XPL>;
+  constexpr int N = CF::N, TY = CF::TY, W = CF::WARPS, PL = W * N;  // PL: one component plane of the CTA's rows
+  constexpr int mask = N - 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *vs = reinterpret_cast<float2 *>(smem_raw);  // [2][3][W][N]
+  float2 *es = vs + 2 * 3 * PL;                         // [2][2][W][N]: e1, e3
+  float2 *cs = es + 2 * 2 * PL;                         // [W][N]
+  const long n = (long)N * N * N, plane = (long)N * N;
+  const int b = act ? act[blockIdx.z] : (int)blockIdx.z;
+  const int j = blockIdx.y;
+  const int tilesY = N / TY;
+  const int y0 = (blockIdx.x % tilesY) * TY;
+  const int zb = (blockIdx.x / tilesY) * ZC;
+  const float2 *Xb = X + (long)b * sx + (long)j * 3 * n;
+  float2 *Yb = Y + (long)b * sy + (long)j * 3 * n;
+  const KParam &p = kp[b];
+  const float kh0 = p.khf[0], kh1 = p.khf[1], kh2 = p.khf[2], gam = p.gammaf, ih = (float)N;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int R = (y0 - 1 + w) & mask;
+  const int x0 = lane * XPL;
+  const long rowoff = (long)R * N + x0;  // within a plane
+  const bool has_e = w >= 1, has_c = w <= TY, has_y = w >= 1 && w <= TY;
+  float2 *const vrow0 = vs + w * N + x0;  // slot s, component c: + (3 s + c) PL
+  float2 *const erow0 = es + w * N + x0;  // slot s, (e1, e3): + (2 s + 0 / 1) PL
+  float2 *const crow = cs + w * N + x0;
+  auto vrow = [&](int slot) { return vrow0 + slot * 3 * PL; };
+  auto erow = [&](int slot) { return erow0 + slot * 2 * PL; };
+
+  auto load_v = [&](int z, float2 (&v)[3][XPL]) {
+    const long o = (long)(z & mask) * plane + rowoff;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ld_row<XPL>(Xb + c * n + o, v[c]);
+  };
+  auto store_v = [&](int slot, const float2 (&v)[3][XPL]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) st_row<XPL>(vrow(slot) + c * PL, v[c]);
+  };
+  // e = M0 A' v at plane z on this row: v (own, plane z), vm (own, plane z - 1), v at row R - 1 from slot s
+  auto make_e = [&](int z, int s, const float2 (&v)[3][XPL], const float2 (&vm)[3][XPL], float2 (&e)[3][XPL]) {
+    float2 v1y[XPL], v3y[XPL], v2x[XPL], v3x[XPL];
+    ld_row<XPL>(vrow(s) - N, v1y);           // v1 at R - 1
+    ld_row<XPL>(vrow(s) + 2 * PL - N, v3y);  // v3 at R - 1
+    xprev<XPL>(v[1], v2x, lane);
+    xprev<XPL>(v[2], v3x, lane);
+    float mz[3][XPL];
+    const long o = (long)(z & mask) * plane + rowoff;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ld_row_m0<XPL>(m0 + c * n + o, mz[c]);
+#pragma unroll
+    for (int i = 0; i < XPL; ++i) {
+      const float2 d3v2 = dbwd(vm[1][i], v[1][i], ih, kh2), d2v3 = dbwd(v3y[i], v[2][i], ih, kh1);
+      const float2 d3v1 = dbwd(vm[0][i], v[0][i], ih, kh2), d1v3 = dbwd(v3x[i], v[2][i], ih, kh0);
+      const float2 d2v1 = dbwd(v1y[i], v[0][i], ih, kh1), d1v2 = dbwd(v2x[i], v[1][i], ih, kh0);
+      e[0][i] = cscale(csub(d3v2, d2v3), mz[0][i]);
+      e[1][i] = cscale(csub(d1v3, d3v1), mz[1][i]);
+      e[2][i] = cscale(csub(d2v1, d1v2), mz[2][i]);
+    }
+  };
+  // c = B v at plane z on this row: v (own, plane z), v2 at R + 1 from slot s (plane z), v3 of plane z + 1 (own)
+  auto make_c = [&](int s, const float2 (&v)[3][XPL], const float2 (&vp3)[XPL], float2 (&cc)[XPL]) {
+    float2 v2y[XPL], v1x[XPL];
+    ld_row<XPL>(vrow(s) + PL + N, v2y);  // v2 at R + 1
+    xnext<XPL>(v[0], v1x, lane);
+#pragma unroll
+    for (int i = 0; i < XPL; ++i)
+      cc[i] = cadd(cadd(dfwd(v[0][i], v1x[i], ih, kh0), dfwd(v[1][i], v2y[i], ih, kh1)),
+                   dfwd(v[2][i], vp3[i], ih, kh2));
+  };
+
+  float2 vm[3][XPL], v0[3][XPL], vp[3][XPL], ecur[3][XPL], enext[3][XPL], cprev[XPL], ccur[XPL];
+  // (the edge warps shuffle values they never use: start them defined)
+#pragma unroll
+  for (int i = 0; i < XPL; ++i) {
+    cprev[i] = ccur[i] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ecur[c][i] = enext[c][i] = make_float2(0.f, 0.f);
+  }
+  // prologue: v(zb - 1) into slot 1, v(zb) into slot 0; c(zb - 1) and e(zb)
+  load_v(zb - 1, vm);
+  load_v(zb, v0);
+  store_v(1, vm);
+  store_v(0, v0);
+  __syncthreads();
+  if (has_c) make_c(1, vm, v0[2], cprev);
+  if (has_e) {
+    make_e(zb, 0, v0, vm, ecur);
+    st_row<XPL>(erow(0), ecur[0]);
+    st_row<XPL>(erow(0) + PL, ecur[2]);
+  }
+  __syncthreads();  // slot 1 (v(zb - 1)) is rewritten by the first step
+  int s0 = 0, es0 = 0;  // slots of v(z) and e(z)
+  for (int z = zb; z < zb + ZC; ++z) {
+    const int s1 = 1 - s0, es1 = 1 - es0;
+    load_v(z + 1, vp);
+    store_v(s1, vp);  // slot s1 held v(z - 1): its last readers (c(z - 1)) finished before the previous barrier
+    __syncthreads();
+    if (has_e) {
+      make_e(z + 1, s1, vp, v0, enext);
+      st_row<XPL>(erow(es1), enext[0]);
+      st_row<XPL>(erow(es1) + PL, enext[2]);
+    }
+    if (has_c) {
+      make_c(s0, v0, vp[2], ccur);
+      st_row<XPL>(crow, ccur);
+    }
+    __syncthreads();
+    // every warp takes part in the shuffles; warps 0 and TY + 1 hold no output row
+    float2 e3x[XPL], e2x[XPL], cx[XPL];
+    xnext<XPL>(ecur[2], e3x, lane);
+    xnext<XPL>(ecur[1], e2x, lane);
+    xprev<XPL>(ccur, cx, lane);
+    if (has_y) {
+      float2 e1y[XPL], e3y[XPL], cy[XPL];
+      ld_row<XPL>(erow(es0) + N, e1y);       // e1(z) at R + 1
+      ld_row<XPL>(erow(es0) + PL + N, e3y);  // e3(z) at R + 1
+      ld_row<XPL>(crow - N, cy);             // c(z) at R - 1
+      float2 o1[XPL], o2[XPL], o3[XPL];
+#pragma unroll
+      for (int i = 0; i < XPL; ++i) {
+        const float2 e1 = ecur[0][i], e2 = ecur[1][i], e3 = ecur[2][i], c0 = ccur[i];
+        o1[i] = cadd(csub(dfwd(e3, e3y[i], ih, kh1), dfwd(e2, enext[1][i], ih, kh2)),
+                     cscale(dbwd(cx[i], c0, ih, kh0), gam));
+        o2[i] = cadd(csub(dfwd(e1, enext[0][i], ih, kh2), dfwd(e3, e3x[i], ih, kh0)),
+                     cscale(dbwd(cy[i], c0, ih, kh1), gam));
+        o3[i] = cadd(csub(dfwd(e2, e2x[i], ih, kh0), dfwd(e1, e1y[i], ih, kh1)),
+                     cscale(dbwd(cprev[i], c0, ih, kh2), gam));
+      }
+      const long o = (long)z * plane + rowoff;
+      st_row<XPL>(Yb + o, o1);
+      st_row<XPL>(Yb + n + o, o2);
+      st_row<XPL>(Yb + 2 * n + o, o3);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int i = 0; i < XPL; ++i) {
+        vm[c][i] = v0[c][i];
+        v0[c][i] = vp[c][i];
+        ecur[c][i] = enext[c][i];
+      }
+#pragma unroll
+    for (int i = 0; i < XPL; ++i) cprev[i] = ccur[i];
+    s0 = s1;
+    es0 = es1;
+  }
+}
+
 // ------------------------------------------------------------------------------------------------ half applies
 // A' x at edge point r and B x at cell point r, read straight from global memory (not on the per-iteration path).
 struct HalfOut {
@@ -422,11 +646,37 @@ static int launch_opz_t(pc_ctx *ctx, int nb, int m, const void *X, long sx, void
   return PC_OK;
 }
 
+template <int XPL>
+static int launch_opz_row(pc_ctx *ctx, int nb, int m, const void *X, long sx, void *Y, long sy, const int *act) {
+  using CF = OpzRow<XPL>;
+  constexpr size_t smem = CF::smem();
+  static bool configured = false;
+  if (!configured) {
+    PC_CK(cudaFuncSetAttribute(opz_row_kernel<XPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = true;
+  }
+  constexpr int N = CF::N;
+  // z chunk: at least about 8 CTAs per SM over the launch, at least 8 planes per chunk (the prologue loads one
+  // extra plane per chunk)
+  const long tiles = (long)(N / CF::TY) * m * nb;
+  int ZC = N;
+  while (ZC > 8 && tiles * (N / ZC) < 8L * sm_count()) ZC >>= 1;
+  dim3 grid((N / CF::TY) * (N / ZC), m, nb);
+  opz_row_kernel<XPL><<<grid, CF::WARPS * 32, smem, ctx->stream>>>(static_cast<const float2 *>(X), sx,
+                                                                    static_cast<float2 *>(Y), sy, ctx->m0f.as<float>(),
+                                                                    ctx->kparam.as<KParam>(), act, ZC);
+  PC_CK_LAUNCH();
+  return PC_OK;
+}
+
 int launch_apply_op(pc_ctx *ctx, int nb, int m, int dtype, const void *X, long sx, void *Y, long sy,
                     const int *act) {
   if (nb == 0 || m == 0) return PC_OK;
   if (ctx->opts.order > 1 || ctx->lat) return launch_apply_op_k(ctx, nb, m, dtype, X, sx, Y, sy, act);
   const int N = ctx->N;
+  if (dtype == PC_C64 && N == 32) return launch_opz_row<1>(ctx, nb, m, X, sx, Y, sy, act);
+  if (dtype == PC_C64 && N == 64) return launch_opz_row<2>(ctx, nb, m, X, sx, Y, sy, act);
+  if (dtype == PC_C64 && N == 128) return launch_opz_row<4>(ctx, nb, m, X, sx, Y, sy, act);
   if (dtype == PC_C64 && N >= 32) return launch_opz_t<float, 32, 8>(ctx, nb, m, X, sx, Y, sy, act);
   if (dtype == PC_C128) {
     if (N >= 32) return launch_op_t<double, 32, 4, 4>(ctx, nb, m, X, sx, Y, sy, act);

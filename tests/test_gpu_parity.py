@@ -144,8 +144,9 @@ def test_apply_precond_fp64(pcmod, N, variant):
 
 @pytest.mark.parametrize("N,variant", [(8, 0), (16, 0), (32, 0), (64, 0), (32, 1), (128, 0)])
 def test_apply_precond_fp32(pcmod, N, variant):
-    """complex64 solve (register-resident line FFTs for N <= 64, shared-memory FFTs above) against the FP64
-    oracle, including a k = 0 point whose zero mode is singular and maps to zero."""
+    """complex64 solve (two-level register/shared-memory line FFTs in natural order for N <= 128, the shared-memory
+    radix-2 FFTs above) against the FP64 oracle, including a k = 0 point whose zero mode is singular and maps to
+    zero."""
     S, _ = make_solver(pcmod, N, precond=variant)
     kpts = np.array([[1.1, -0.2, 0.7], [0.0, 0.0, 0.0]])
     gammas = [64.0, 2.0 * N]
