@@ -748,22 +748,27 @@ int launch_pairs_to_c128(int nb, long L, int m, const void *X, long sx, void *Y,
 
 // ------------------------------------------------------------------------------------------------ k = 0 projection
 // Removes the mean of each component of each column for k-points with flags[b] != 0 (the constant kernel fields).
-// One block per (column, component) and k-point: FP64 sums over the component (strided, then a block tree), then
-// the subtraction in a second pass over the same entries (L2-resident). Blocks of k-points without the flag return
-// at once, so the launch can cover a whole active list. S: the element storage, float2 (complex64), double2
-// (complex128) or float4 (double-float pairs).
+// Two launches, DEFL_SPLIT blocks per (column, component) each: partial sums over a slice of the component (FP64,
+// from FP32 per-thread sums for complex64 data), then every block adds the slices' partial sums and subtracts the
+// mean from its own slice. Blocks of k-points without the flag return at once, so a launch can cover a whole active
+// list. S: the element storage, float2 (complex64), double2 (complex128) or float4 (double-float pairs). Scratch:
+// [nb][3 m][DEFL_SPLIT] double2.
+constexpr int DEFL_SPLIT = 16;
+
 template <typename S>
-__global__ void __launch_bounds__(256) deflate_kernel(S *__restrict__ X, long sx, long n, const int *__restrict__ flags,
-                                                     const int *__restrict__ act) {
-  const int bi = blockIdx.y, col = blockIdx.x;  // col = j * 3 + comp
+__global__ void __launch_bounds__(256) deflate_sum_kernel(const S *__restrict__ X, long sx, long n,
+                                                         const int *__restrict__ flags, const int *__restrict__ act,
+                                                         double2 *__restrict__ part) {
+  const int bi = blockIdx.y, col = blockIdx.x / DEFL_SPLIT, sl = blockIdx.x % DEFL_SPLIT;  // col = j * 3 + comp
   const int b = act ? act[bi] : bi;
   if (!flags[b]) return;
-  S *x = X + (long)b * sx + (long)col * n;
+  const long len = (n + DEFL_SPLIT - 1) / DEFL_SPLIT, l0 = sl * len, l1 = min(n, l0 + len);
+  const S *x = X + (long)b * sx + (long)col * n;
   double sr = 0.0, si = 0.0;
   if constexpr (std::is_same<S, float2>::value) {
     // complex64 data: per-thread sums in FP32 (their rounding is that of the data), FP64 from the warp sums on
     float fr = 0.f, fi = 0.f;
-    for (long l = threadIdx.x; l < n; l += blockDim.x) {
+    for (long l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
       const float2 v = x[l];
       fr += v.x;
       fi += v.y;
@@ -771,7 +776,7 @@ __global__ void __launch_bounds__(256) deflate_kernel(S *__restrict__ X, long sx
     sr = fr;
     si = fi;
   } else {
-    for (long l = threadIdx.x; l < n; l += blockDim.x) {
+    for (long l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
       const double2 v = ld_c128(x + l);
       sr += v.x;
       si += v.y;
@@ -789,16 +794,36 @@ __global__ void __launch_bounds__(256) deflate_kernel(S *__restrict__ X, long sx
     red[1][w] = si;
   }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    double mr = 0.0, mi = 0.0;
+    for (int i = 0; i < nw; ++i) {
+      mr += red[0][i];
+      mi += red[1][i];
+    }
+    part[((long)bi * gridDim.x + blockIdx.x)] = make_double2(mr, mi);
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) deflate_sub_kernel(S *__restrict__ X, long sx, long n,
+                                                         const int *__restrict__ flags, const int *__restrict__ act,
+                                                         const double2 *__restrict__ part) {
+  const int bi = blockIdx.y, col = blockIdx.x / DEFL_SPLIT, sl = blockIdx.x % DEFL_SPLIT;
+  const int b = act ? act[bi] : bi;
+  if (!flags[b]) return;
   double mr = 0.0, mi = 0.0;
-  for (int i = 0; i < nw; ++i) {
-    mr += red[0][i];
-    mi += red[1][i];
+  const double2 *pc = part + (long)bi * gridDim.x + (long)col * DEFL_SPLIT;
+  for (int i = 0; i < DEFL_SPLIT; ++i) {
+    mr += pc[i].x;
+    mi += pc[i].y;
   }
   mr /= (double)n;
   mi /= (double)n;
+  const long len = (n + DEFL_SPLIT - 1) / DEFL_SPLIT, l0 = sl * len, l1 = min(n, l0 + len);
+  S *x = X + (long)b * sx + (long)col * n;
   if constexpr (std::is_same<S, float4>::value) {
     const df dr = df_from(mr), di = df_from(mi);
-    for (long l = threadIdx.x; l < n; l += blockDim.x) {
+    for (long l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
       cdf v = ld_cdf(x + l);
       v.re = df_sub(v.re, dr);
       v.im = df_sub(v.im, di);
@@ -807,24 +832,33 @@ __global__ void __launch_bounds__(256) deflate_kernel(S *__restrict__ X, long sx
   } else {
     using T = decltype(S{}.x);
     const T tr = (T)mr, ti = (T)mi;
-    for (long l = threadIdx.x; l < n; l += blockDim.x) {
+    for (long l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
       x[l].x -= tr;
       x[l].y -= ti;
     }
   }
 }
 
+template <typename S>
+static void deflate_t(int nb, long n, int m, S *X, long sx, const int *flags, double2 *part, cudaStream_t st,
+                      const int *act) {
+  const dim3 grid(3 * m * DEFL_SPLIT, nb);
+  deflate_sum_kernel<S><<<grid, 256, 0, st>>>(X, sx, n, flags, act, part);
+  deflate_sub_kernel<S><<<grid, 256, 0, st>>>(X, sx, n, flags, act, part);
+}
+
+size_t deflate_scratch_bytes(int nb, int m) { return sizeof(double2) * (size_t)nb * 3 * m * DEFL_SPLIT; }
+
 int launch_deflate(int nb, long n, int m, void *X, long sx, const int *flags, void *scratch, cudaStream_t st,
                    const int *act, int dtype) {
-  (void)scratch;
   if (nb == 0 || m == 0) return PC_OK;
-  const dim3 grid(3 * m, nb);
+  double2 *part = static_cast<double2 *>(scratch);
   if (dtype == PC_C128)
-    deflate_kernel<double2><<<grid, 256, 0, st>>>(static_cast<double2 *>(X), sx, n, flags, act);
+    deflate_t<double2>(nb, n, m, static_cast<double2 *>(X), sx, flags, part, st, act);
   else if (dtype == PC_DFS)
-    deflate_kernel<float4><<<grid, 256, 0, st>>>(static_cast<float4 *>(X), sx, n, flags, act);
+    deflate_t<float4>(nb, n, m, static_cast<float4 *>(X), sx, flags, part, st, act);
   else
-    deflate_kernel<float2><<<grid, 256, 0, st>>>(static_cast<float2 *>(X), sx, n, flags, act);
+    deflate_t<float2>(nb, n, m, static_cast<float2 *>(X), sx, flags, part, st, act);
   PC_CK_LAUNCH();
   return PC_OK;
 }

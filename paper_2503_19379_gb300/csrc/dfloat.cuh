@@ -90,6 +90,35 @@ __device__ __forceinline__ void cdf_mac(cdf &s, cdf a, cdf b) {
   df_mac(s.im, a.im, b.re);
 }
 __device__ __forceinline__ cdf cdf_scale2(cdf a, float s) { return cdf{df_scale2(a.re, s), df_scale2(a.im, s)}; }
+
+// A double-float sum built term by term without renormalising after every term: s is the FP32 running sum of the
+// leading products, e collects every rounding error exactly captured on the way (two_sum of the running sum, the
+// fma residual of each leading product) plus the small cross terms hi*lo + lo*hi. One term costs 12 FP32 operations
+// (df_mac: 15), and the value is quick_two_sum(s, e) at the end; e stays ~2^-24 |s|, so its own rounding is ~2^-48
+// of the sum, like the renormalised form.
+struct dfsum {
+  float s, e;
+};
+// a += x c
+__device__ __forceinline__ void dfsum_mac(dfsum &a, df x, df c) {
+  const float p = x.hi * c.hi;
+  const float ep = fmaf(x.hi, c.hi, -p);
+  const float t = a.s + p;
+  const float bb = t - a.s;
+  const float es = (a.s - (t - bb)) + (p - bb);
+  a.s = t;
+  a.e += es + ep;
+  a.e = fmaf(x.hi, c.lo, a.e);
+  a.e = fmaf(x.lo, c.hi, a.e);
+}
+// a += f for an FP32 f
+__device__ __forceinline__ void dfsum_addf(dfsum &a, float f) {
+  const float t = a.s + f;
+  const float bb = t - a.s;
+  a.e += (a.s - (t - bb)) + (f - bb);
+  a.s = t;
+}
+__device__ __forceinline__ df dfsum_value(dfsum a) { return quick_two_sum(a.s, a.e); }
 // x + f for a double-float x and an FP32 f
 __device__ __forceinline__ df df_addf(df x, float f) {
   const df s = two_sum(x.hi, f);

@@ -542,55 +542,77 @@ int launch_op_df_resid(pc_ctx *ctx, int nb, int m, const void *X, long sx, const
 }
 
 // ---------------------------------------------------------------- block update Y = X C + Z
-constexpr int DF_QB = 8;
-
+// One row per thread, QB output columns per block row of the grid (QB from the column count so that few columns
+// are computed for nothing: 19 columns take two blocks of 10, not three of 8). Coefficients in shared memory as
+// double-float (re, im, -im); each term is a dfsum multiply-add (12 FP32 operations per real term).
+template <int QB>
 __global__ void __launch_bounds__(256) update_df_kernel(const float4 *__restrict__ X, long sx,
                                                        const double2 *__restrict__ Cm, long sc,
                                                        float4 *__restrict__ Y, long sy,
                                                        const float2 *__restrict__ Z, long sz, long L, int p, int q,
                                                        const int *__restrict__ act) {
-  __shared__ cdf Cs[64][DF_QB];
+  __shared__ df Cs[64][QB][3];  // (re, im, -im) of C[i][j0 + c]
   const int b = act ? act[blockIdx.z] : (int)blockIdx.z;
-  const int j0 = blockIdx.y * DF_QB;
+  const int j0 = blockIdx.y * QB;
   const double2 *Cb = Cm + (long)b * sc;
-  for (int i = threadIdx.x; i < p * DF_QB; i += blockDim.x) {
-    const int r = i / DF_QB, c = i - r * DF_QB;
-    Cs[r][c] = cdf_from((j0 + c < q) ? Cb[r * q + j0 + c] : make_double2(0.0, 0.0));
+  for (int i = threadIdx.x; i < p * QB; i += blockDim.x) {
+    const int r = i / QB, c = i - r * QB;
+    const double2 v = (j0 + c < q) ? Cb[r * q + j0 + c] : make_double2(0.0, 0.0);
+    Cs[r][c][0] = df_from(v.x);
+    Cs[r][c][1] = df_from(v.y);
+    Cs[r][c][2] = df_from(-v.y);
   }
   __syncthreads();
   const long l = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= L) return;
   const float4 *Xb = X + (long)b * sx;
-  cdf acc[DF_QB];
+  dfsum re[QB], im[QB];
 #pragma unroll
-  for (int c = 0; c < DF_QB; ++c) acc[c] = cdf{df{0.f, 0.f}, df{0.f, 0.f}};
+  for (int c = 0; c < QB; ++c) re[c] = im[c] = dfsum{0.f, 0.f};
   for (int i = 0; i < p; ++i) {
     const cdf xv = ld_cdf(Xb + (long)i * L + l);
 #pragma unroll
-    for (int c = 0; c < DF_QB; ++c) cdf_mac(acc[c], xv, Cs[i][c]);
+    for (int c = 0; c < QB; ++c) {
+      // (xr + i xi)(cr + i ci) = (xr cr - xi ci) + i (xr ci + xi cr)
+      dfsum_mac(re[c], xv.re, Cs[i][c][0]);
+      dfsum_mac(re[c], xv.im, Cs[i][c][2]);
+      dfsum_mac(im[c], xv.re, Cs[i][c][1]);
+      dfsum_mac(im[c], xv.im, Cs[i][c][0]);
+    }
   }
   float4 *Yb = Y + (long)b * sy;
   const float2 *Zb = Z ? Z + (long)b * sz : nullptr;
 #pragma unroll
-  for (int c = 0; c < DF_QB; ++c)
+  for (int c = 0; c < QB; ++c)
     if (j0 + c < q) {
-      cdf v = acc[c];
       if (Zb) {
         const float2 z = Zb[(long)(j0 + c) * L + l];
-        v.re = df_addf(v.re, z.x);
-        v.im = df_addf(v.im, z.y);
+        dfsum_addf(re[c], z.x);
+        dfsum_addf(im[c], z.y);
       }
-      st_cdf(Yb + (long)(j0 + c) * L + l, v);
+      st_cdf(Yb + (long)(j0 + c) * L + l, cdf{dfsum_value(re[c]), dfsum_value(im[c])});
     }
 }
 
 int launch_update_df(int nb, long L, int p, int q, const void *X, long sx, const void *C, long sc, void *Y, long sy,
                      const void *Z, long sz, cudaStream_t st, const int *act) {
   if (nb == 0 || q == 0) return PC_OK;
-  dim3 grid((unsigned)((L + 255) / 256), (q + DF_QB - 1) / DF_QB, nb);
-  update_df_kernel<<<grid, 256, 0, st>>>(static_cast<const float4 *>(X), sx, static_cast<const double2 *>(C), sc,
-                                         static_cast<float4 *>(Y), sy, static_cast<const float2 *>(Z), sz, L, p, q,
-                                         act);
+  if (p > 64) {
+    set_error("update_df: at most 64 input columns");
+    return PC_EINVAL;
+  }
+  // blocks of columns: 8 wide unless 10 wastes fewer (q = 19: 2 x 10 instead of 3 x 8)
+  const int nb8 = (q + 7) / 8, nb10 = (q + 9) / 10;
+  const bool wide = nb10 * 10 < nb8 * 8;
+  const unsigned gx = (unsigned)((L + 255) / 256);
+  if (wide)
+    update_df_kernel<10><<<dim3(gx, nb10, nb), 256, 0, st>>>(static_cast<const float4 *>(X), sx,
+                                                             static_cast<const double2 *>(C), sc, static_cast<float4 *>(Y),
+                                                             sy, static_cast<const float2 *>(Z), sz, L, p, q, act);
+  else
+    update_df_kernel<8><<<dim3(gx, nb8, nb), 256, 0, st>>>(static_cast<const float4 *>(X), sx,
+                                                           static_cast<const double2 *>(C), sc, static_cast<float4 *>(Y),
+                                                           sy, static_cast<const float2 *>(Z), sz, L, p, q, act);
   PC_CK_LAUNCH();
   return PC_OK;
 }
@@ -619,7 +641,7 @@ __global__ void __launch_bounds__(528) gram_df_kernel(const float4 *__restrict__
   }
   __syncthreads();
   const int i = pi[tid], j = pj[tid];
-  df re{0.f, 0.f}, im{0.f, 0.f};
+  dfsum re{0.f, 0.f}, im{0.f, 0.f};
   const long beg = (long)blockIdx.x * chunk, end = min(L, beg + chunk);
   for (long l0 = beg; l0 < end; l0 += DF_TL) {
     for (int e = tid; e < p * DF_TL; e += nthr) {
@@ -631,15 +653,16 @@ __global__ void __launch_bounds__(528) gram_df_kernel(const float4 *__restrict__
 #pragma unroll 4
     for (int t = 0; t < DF_TL; ++t) {
       const cdf a = Xs[i][t], c = Xs[j][t];
-      // conj(a) c
-      df_mac(re, a.re, c.re);
-      df_mac(re, a.im, c.im);
-      df_mac(im, a.re, c.im);
-      df_mac(im, df_neg(a.im), c.re);
+      // conj(a) c = (ar cr + ai ci) + i (ar ci - ai cr)
+      dfsum_mac(re, a.re, c.re);
+      dfsum_mac(re, a.im, c.im);
+      dfsum_mac(im, a.re, c.im);
+      dfsum_mac(im, df_neg(a.im), c.re);
     }
     __syncthreads();
   }
-  part[((long)bi * gridDim.x + blockIdx.x) * p * p + i * p + j] = make_double2(df_to(re), df_to(im));
+  part[((long)bi * gridDim.x + blockIdx.x) * p * p + i * p + j] =
+      make_double2(df_to(dfsum_value(re)), df_to(dfsum_value(im)));
 }
 
 // chunk sums of the upper triangle in FP64, mirrored

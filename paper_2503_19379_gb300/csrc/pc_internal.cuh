@@ -262,6 +262,7 @@ int launch_recompute(pc_ctx *ctx, int nb, int m, const void *X, long sx, double 
 size_t recompute_scratch_bytes(long n, int nb, int m);
 int launch_deflate(int nb, long n, int m, void *X, long sx, const int *flags, void *scratch, cudaStream_t st,
                    const int *act, int dtype = PC_C128);
+size_t deflate_scratch_bytes(int nb, int m);
 int launch_residual_mixed(int nb, long L, int m, int dtype_x, const void *X, long sx, const void *AX, long sax,
                           const double *theta, void *R1, long sr1, void *R2, long sr2, void *X32, long sx32,
                           void *AX32, long sax32, double *norms, void *scratch, size_t scratch_bytes,

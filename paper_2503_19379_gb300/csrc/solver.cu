@@ -439,7 +439,7 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
   size_t scr = 16;
   for (int na = 1; na <= nb; ++na)
     scr = std::max({scr, gram_pair_scratch_bytes(na, L, nmax), residual_scratch_bytes(na, L, m),
-                    sizeof(double2) * (size_t)na * 3 * m * 16, sizeof(double) * 3 * (size_t)na * m * 64});
+                    deflate_scratch_bytes(na, m), sizeof(double) * 3 * (size_t)na * m * 64});
   PC_CK(ctx->scratch.reserve(scr));
   int *d_act = ctx->rank.as<int>() + nb;
   int *d_zero = ctx->flag.as<int>();

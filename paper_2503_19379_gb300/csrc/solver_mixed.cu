@@ -470,7 +470,7 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
                     gram_df_scratch_bytes(na, L, m),
                     gram_scratch_bytes(na, L, m, nmax), residual_scratch_bytes(na, L, m),
                     recompute_scratch_bytes(n, na, m), op_df_resid_scratch_bytes(ctx, na, m),
-                    sizeof(double2) * (size_t)na * 3 * m * 16});
+                    deflate_scratch_bytes(na, m)});
   scr = (scr + 255) / 256 * 256;
   PC_CK(ctx->scratch.reserve(scr * ngroups));
   const size_t npin = (size_t)nb * m * 6;
