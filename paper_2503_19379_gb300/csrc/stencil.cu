@@ -398,17 +398,20 @@ __global__ void __launch_bounds__(OpzRow<XPL>::WARPS * 32) opz_row_kernel(const 
 #pragma unroll
     for (int c = 0; c < 3; ++c) st_row<XPL>(vrow(slot) + c * PL, v[c]);
   };
-  // e = M0 A' v at plane z on this row: v (own, plane z), vm (own, plane z - 1), v at row R - 1 from slot s
-  auto make_e = [&](int z, int s, const float2 (&v)[3][XPL], const float2 (&vm)[3][XPL], float2 (&e)[3][XPL]) {
+  auto load_m0 = [&](int z, float (&mz)[3][XPL]) {
+    const long o = (long)(z & mask) * plane + rowoff;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ld_row_m0<XPL>(m0 + c * n + o, mz[c]);
+  };
+  // e = M0 A' v at plane z on this row: v (own, plane z), vm (own, plane z - 1), v at row R - 1 from slot s, mz the
+  // M0 entries of the row at plane z
+  auto make_e = [&](const float (&mz)[3][XPL], int s, const float2 (&v)[3][XPL], const float2 (&vm)[3][XPL],
+                    float2 (&e)[3][XPL]) {
     float2 v1y[XPL], v3y[XPL], v2x[XPL], v3x[XPL];
     ld_row<XPL>(vrow(s) - N, v1y);           // v1 at R - 1
     ld_row<XPL>(vrow(s) + 2 * PL - N, v3y);  // v3 at R - 1
     xprev<XPL>(v[1], v2x, lane);
     xprev<XPL>(v[2], v3x, lane);
-    float mz[3][XPL];
-    const long o = (long)(z & mask) * plane + rowoff;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) ld_row_m0<XPL>(m0 + c * n + o, mz[c]);
 #pragma unroll
     for (int i = 0; i < XPL; ++i) {
       const float2 d3v2 = dbwd(vm[1][i], v[1][i], ih, kh2), d2v3 = dbwd(v3y[i], v[2][i], ih, kh1);
@@ -446,19 +449,36 @@ __global__ void __launch_bounds__(OpzRow<XPL>::WARPS * 32) opz_row_kernel(const 
   __syncthreads();
   if (has_c) make_c(1, vm, v0[2], cprev);
   if (has_e) {
-    make_e(zb, 0, v0, vm, ecur);
+    float mz0[3][XPL];
+    load_m0(zb, mz0);
+    make_e(mz0, 0, v0, vm, ecur);
     st_row<XPL>(erow(0), ecur[0]);
     st_row<XPL>(erow(0) + PL, ecur[2]);
   }
   __syncthreads();  // slot 1 (v(zb - 1)) is rewritten by the first step
   int s0 = 0, es0 = 0;  // slots of v(z) and e(z)
+  // v of the next plane is loaded one step ahead (vn), so that its latency overlaps a whole step
+  float2 vn[3][XPL];
+  float mn[3][XPL], mz[3][XPL];
+  load_v(zb + 1, vn);
+  load_m0(zb + 1, mn);
   for (int z = zb; z < zb + ZC; ++z) {
     const int s1 = 1 - s0, es1 = 1 - es0;
-    load_v(z + 1, vp);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int i = 0; i < XPL; ++i) {
+        vp[c][i] = vn[c][i];
+        mz[c][i] = mn[c][i];
+      }
+    if (z + 1 < zb + ZC) {
+      load_v(z + 2, vn);
+      load_m0(z + 2, mn);
+    }
     store_v(s1, vp);  // slot s1 held v(z - 1): its last readers (c(z - 1)) finished before the previous barrier
     __syncthreads();
     if (has_e) {
-      make_e(z + 1, s1, vp, v0, enext);
+      make_e(mz, s1, vp, v0, enext);
       st_row<XPL>(erow(es1), enext[0]);
       st_row<XPL>(erow(es1) + PL, enext[2]);
     }
