@@ -386,24 +386,25 @@ int launch_gram_pair_coupled(int nb, long L, int p, int q2, int dtype, const voi
 }
 
 // ------------------------------------------------------------------------------------------------ block update
-// Y_b[:, j] = sum_i S_b[:, i] C_b[i, j] (+ Z_b[:, j] when Z is given); grid (ceil(L/256), ceil(q/16), nb); one row
-// per thread, 16 outputs. Products and sums run in the precision T of S and Y; Z is a complex64 addend (the
-// complex64 correction added to the FP64 block in the mixed-precision update).
-constexpr int UPD_QB = 16;
+// Y_b[:, j] = sum_i S_b[:, i] C_b[i, j] (+ Z_b[:, j] when Z is given); grid (ceil(L/256), ceil(q/QB), nb); one row
+// per thread, QB outputs. Products and sums run in the precision T of S and Y; Z is a complex64 addend (the
+// complex64 correction added to the FP64 block in the mixed-precision update). Each column group re-reads S, so
+// the launcher takes the width that covers q in the fewest groups with the fewest idle columns (complex64: one
+// group of up to 24 columns, 48 accumulator registers; complex128: 16).
+constexpr int UPD_PMAX = 64;
 
-template <typename T>
-__global__ void __launch_bounds__(256) block_update_kernel(const cplx<T> *__restrict__ S, long ss,
-                                                          const double2 *__restrict__ Cm, long sc,
-                                                          cplx<T> *__restrict__ Y, long sy,
-                                                          const float2 *__restrict__ Z, long sz, long L, int p,
-                                                          int q, const int *__restrict__ act) {
+template <typename T, int QB>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+    block_update_kernel(const cplx<T> *__restrict__ S, long ss, const double2 *__restrict__ Cm, long sc,
+                        cplx<T> *__restrict__ Y, long sy, const float2 *__restrict__ Z, long sz, long L, int p, int q,
+                        const int *__restrict__ act) {
   using C = cplx<T>;
-  __shared__ C Cs[64][UPD_QB];
+  __shared__ C Cs[UPD_PMAX][QB];
   const int b = act ? act[blockIdx.z] : (int)blockIdx.z;
-  const int j0 = blockIdx.y * UPD_QB;
+  const int j0 = blockIdx.y * QB;
   const double2 *Cb = Cm + (long)b * sc;
-  for (int i = threadIdx.x; i < p * UPD_QB; i += blockDim.x) {
-    const int r = i / UPD_QB, c = i - r * UPD_QB;
+  for (int i = threadIdx.x; i < p * QB; i += blockDim.x) {
+    const int r = i / QB, c = i - r * QB;
     const double2 v = (j0 + c < q) ? Cb[r * q + j0 + c] : cmake<double2>(0.0, 0.0);
     Cs[r][c] = cmake<C>((T)v.x, (T)v.y);
   }
@@ -411,13 +412,13 @@ __global__ void __launch_bounds__(256) block_update_kernel(const cplx<T> *__rest
   const long l = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= L) return;
   const C *Sb = S + (long)b * ss;
-  C acc[UPD_QB];
+  C acc[QB];
 #pragma unroll
-  for (int c = 0; c < UPD_QB; ++c) acc[c] = cmake<C>((T)0, (T)0);
+  for (int c = 0; c < QB; ++c) acc[c] = cmake<C>((T)0, (T)0);
   for (int i = 0; i < p; ++i) {
     const C sv = Sb[(long)i * L + l];
 #pragma unroll
-    for (int c = 0; c < UPD_QB; ++c) {
+    for (int c = 0; c < QB; ++c) {
       const C cv = Cs[i][c];
       acc[c].x = fma(sv.x, cv.x, fma(-sv.y, cv.y, acc[c].x));
       acc[c].y = fma(sv.x, cv.y, fma(sv.y, cv.x, acc[c].y));
@@ -426,7 +427,7 @@ __global__ void __launch_bounds__(256) block_update_kernel(const cplx<T> *__rest
   C *Yb = Y + (long)b * sy;
   const float2 *Zb = Z ? Z + (long)b * sz : nullptr;
 #pragma unroll
-  for (int c = 0; c < UPD_QB; ++c)
+  for (int c = 0; c < QB; ++c)
     if (j0 + c < q) {
       C v = acc[c];
       if (Zb) {
@@ -438,18 +439,51 @@ __global__ void __launch_bounds__(256) block_update_kernel(const cplx<T> *__rest
     }
 }
 
+template <typename T, int QB>
+static void block_update_t(int nb, long L, int p, int q, const void *S, long ss, const void *C, long sc, void *Y,
+                           long sy, cudaStream_t st, const int *act, const void *Z, long sz) {
+  const dim3 grid((unsigned)((L + 255) / 256), (unsigned)((q + QB - 1) / QB), nb);
+  block_update_kernel<T, QB><<<grid, 256, 0, st>>>(static_cast<const cplx<T> *>(S), ss,
+                                                   static_cast<const double2 *>(C), sc, static_cast<cplx<T> *>(Y), sy,
+                                                   static_cast<const float2 *>(Z), sz, L, p, q, act);
+}
+
+// the column-group width for q outputs among `widths`: fewest idle columns, then fewest groups
+static int update_width(int q, std::initializer_list<int> widths) {
+  int best = 0;
+  for (int w : widths) {
+    if (best == 0) {
+      best = w;
+      continue;
+    }
+    const int idle = (q + w - 1) / w * w - q, best_idle = (q + best - 1) / best * best - q;
+    if (idle < best_idle || (idle == best_idle && (q + w - 1) / w < (q + best - 1) / best)) best = w;
+  }
+  return best;
+}
+
 int launch_block_update(int nb, long L, int p, int q, int dtype, const void *S, long ss, const void *C, long sc,
                         void *Y, long sy, cudaStream_t st, const int *act, const void *Z, long sz) {
   if (nb == 0 || q == 0) return PC_OK;
-  dim3 grid((unsigned)((L + 255) / 256), (q + UPD_QB - 1) / UPD_QB, nb);
-  if (dtype == PC_C128)
-    block_update_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double2 *>(S), ss,
-                                                      static_cast<const double2 *>(C), sc, static_cast<double2 *>(Y),
-                                                      sy, static_cast<const float2 *>(Z), sz, L, p, q, act);
-  else
-    block_update_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float2 *>(S), ss,
-                                                     static_cast<const double2 *>(C), sc, static_cast<float2 *>(Y), sy,
-                                                     static_cast<const float2 *>(Z), sz, L, p, q, act);
+  if (p > UPD_PMAX) {
+    set_error("block_update: at most 64 input columns");
+    return PC_EINVAL;
+  }
+  if (dtype == PC_C128) {
+    if (update_width(q, {8, 16}) == 8)
+      block_update_t<double, 8>(nb, L, p, q, S, ss, C, sc, Y, sy, st, act, Z, sz);
+    else
+      block_update_t<double, 16>(nb, L, p, q, S, ss, C, sc, Y, sy, st, act, Z, sz);
+  } else {
+    switch (update_width(q, {8, 10, 12, 16, 20, 24})) {
+      case 8: block_update_t<float, 8>(nb, L, p, q, S, ss, C, sc, Y, sy, st, act, Z, sz); break;
+      case 10: block_update_t<float, 10>(nb, L, p, q, S, ss, C, sc, Y, sy, st, act, Z, sz); break;
+      case 12: block_update_t<float, 12>(nb, L, p, q, S, ss, C, sc, Y, sy, st, act, Z, sz); break;
+      case 16: block_update_t<float, 16>(nb, L, p, q, S, ss, C, sc, Y, sy, st, act, Z, sz); break;
+      case 20: block_update_t<float, 20>(nb, L, p, q, S, ss, C, sc, Y, sy, st, act, Z, sz); break;
+      default: block_update_t<float, 24>(nb, L, p, q, S, ss, C, sc, Y, sy, st, act, Z, sz); break;
+    }
+  }
   PC_CK_LAUNCH();
   return PC_OK;
 }

@@ -210,6 +210,21 @@ def test_block_update(pcmod, p, q, L):
     assert np.max(np.abs(Y - ref)) <= 1e-14 * np.max(np.abs(ref)) * p
 
 
+@pytest.mark.parametrize("q", [5, 10, 12, 16, 19, 21, 24, 33])
+def test_block_update_complex64(pcmod, q):
+    # every column-group width of the complex64 kernel (8, 10, 12, 16, 20, 24; 33 = two groups) and a ragged tail
+    p, L = 38, 70001
+    Sb = rand_block(3, (2, p, L))
+    Cm = rand_block(4, (2, p, q))
+    S32 = to_dev(Sb, torch.complex64)
+    Y = pcmod.block_update(S32, to_dev(Cm)).cpu().numpy()
+    # reference from the complex64-rounded inputs in FP64; FP32 products and sums: error ~eps32 sqrt(p) |S| |C|
+    ref = np.einsum("bil,biq->bql", S32.cpu().numpy().astype(np.complex128), Cm)
+    bound = 8 * np.finfo(np.float32).eps * np.sqrt(p) * np.max(np.abs(Sb)) * np.max(np.abs(Cm)) * 2
+    assert Y.dtype == np.complex64 and Y.shape == (2, q, L)
+    assert np.max(np.abs(Y - ref)) <= bound
+
+
 # ------------------------------------------------------------------------------------------- a4 small dense
 @pytest.mark.parametrize("n", [1, 2, 13, 36, 64])
 def test_eigh_batched(pcmod, n):
