@@ -530,6 +530,7 @@ def main():
                        "kpoint_groups": args.groups if args.groups > 0 else "library default (4 from 16 k-points)",
                        "mean_lobpcg_iterations": mean_iters, "max_lobpcg_iterations": max_iters,
                        "lobpcg_iterations_per_kpoint": [int(x) for x in iters[-1]],
+                       "fp64_finish_kpoints": [int(b) for b in np.nonzero(out["fp64_finish"])[0]],
                        "status": max(statuses),
                        "cache": (f"inputs larger than L2 (search blocks "
                                  f"{(192 if args.precision == 'fp64' else 136) * (w.nbands + min(w.nbands // 2 + 1, 21 - w.nbands)) * 3 * w.N ** 3 * nk / 1e9:.0f} GB per GPU), no flush")},

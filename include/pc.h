@@ -112,11 +112,17 @@ int pc_setup(pc_ctx **out, int N, const double *eps_edges, const double *lattice
  *   resid:  host [nk][nbands] final relative residuals, or NULL.
  * All k-points are solved together (batched kernels). Returns PC_NOT_CONVERGED if some k-point hit maxiter and
  * PC_SPURIOUS if Algorithm 4.1 still saw a spurious eigenvalue after max_doublings (results are filled in both
- * cases). Synchronises the context stream before returning. */
+ * cases). With PC_PREC_MIXED, a k-point whose FP64-accurate phase stops converging or reaches maxiter is solved
+ * again by the FP64 solve, started from its current block (pc_get_fp64_finish tells which; its iteration count is
+ * the sum of both). Synchronises the context stream before returning. */
 int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, double tol, double *evals, void *evecs,
              int *iters, double *resid);
 
-/* Release a context and its device memory (never caller memory). NULL is allowed. */
+/* pc_get_fp64_finish -- flags[b] = 1 for each k-point b of the last pc_solve / pc_solve_init on this context that
+ * the mixed solve handed to the FP64 solve, 0 otherwise (all 0 after an FP64 solve).
+ *   nk: the k-point count of that solve (PC_EINVAL otherwise); flags: host [nk]. No device work. */
+int pc_get_fp64_finish(pc_ctx *ctx, int nk, int *flags);
+
 /* pc_solve_init -- pc_solve from a caller-provided initial block: the first n0 columns of each k-point's starting
  * block are X0 (the learned warm start's prediction, or the eigenvectors of a neighbouring k-point), the remaining
  * columns are the counter-based random fields of pc_solve. At k = 0 the constant fields are projected out of X0 as
@@ -125,6 +131,7 @@ int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, double tol, do
 int pc_solve_init(pc_ctx *ctx, int nk, const double *kpts, int nbands, double tol, const void *X0, int n0,
                   double *evals, void *evecs, int *iters, double *resid);
 
+/* Release a context and its device memory (never caller memory). NULL is allowed. */
 void pc_destroy(pc_ctx *ctx);
 
 /* Thread-local description of the last error ("" if none). */

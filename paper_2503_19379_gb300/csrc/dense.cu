@@ -502,6 +502,17 @@ __global__ void __launch_bounds__(256) copy_x0_kernel(const float2 *__restrict__
 int launch_copy_x0(const pc_ctx *ctx, int b0, int nbk, int dtype, void *X, long sx, cudaStream_t st) {
   if (!ctx->x0 || nbk == 0 || ctx->x0n == 0) return PC_OK;
   const long qL = (long)ctx->x0n * 3 * ctx->n;
+  if (ctx->x0_c128) {
+    // complex128 blocks (the FP64 finish) into complex128 panels only
+    if (dtype != PC_C128) {
+      set_error("copy_x0: a complex128 initial block needs complex128 panels");
+      return PC_EINVAL;
+    }
+    const double2 *src = static_cast<const double2 *>(ctx->x0);
+    PC_CK(cudaMemcpy2DAsync(static_cast<double2 *>(X) + (long)b0 * sx, sizeof(double2) * sx, src + (long)b0 * qL,
+                            sizeof(double2) * qL, sizeof(double2) * qL, nbk, cudaMemcpyDeviceToDevice, st));
+    return PC_OK;
+  }
   const float2 *src = static_cast<const float2 *>(ctx->x0);
   if (dtype == PC_C64) {
     // one strided copy: nbk rows of qL complex64 entries, source pitch qL, destination pitch sx

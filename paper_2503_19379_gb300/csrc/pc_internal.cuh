@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <string>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "pc.h"
@@ -131,9 +132,14 @@ struct pc_ctx {
   // general lattice (Section 2's coordinate change x = A y, Section 4.2.2): lat is set when A is not the identity;
   // binv = A^{-1} row-major (binv[3 * i + j] = b_ij), amat = A row-major (amat[3 * i + j] = a_j component i)
   bool lat = false;
-  // caller-provided initial block of pc_solve_init: device complex64 [nk][x0n][3][N][N][N], or null
+  // caller-provided initial block of pc_solve_init: device complex64 [nk][x0n][3][N][N][N], or null; complex128
+  // when x0_c128 is set (the mixed solve's FP64 finish hands its double-float blocks to the FP64 solve that way)
   const void *x0 = nullptr;
   int x0n = 0;
+  bool x0_c128 = false;
+  // per k-point of the last pc_solve: 1 where the mixed solve handed the k-point to the FP64 solve (FP64 finish)
+  std::vector<int> fp64_finish;
+  pc::DevBuf finbuf;  // FP64 finish: the handed-over blocks (complex128) and the finished eigenvectors
   // index of the batch's first k-point within the caller's list: a chunked pc_solve passes each chunk's offset, so
   // that every k-point draws the initial columns of its own index (the same block as in an unchunked solve)
   int kidx0 = 0;
@@ -301,12 +307,16 @@ int launch_gram_df(int nb, long L, int p, const void *X, long sx, void *G, void 
                    cudaStream_t st, const int *act);
 size_t gram_df_scratch_bytes(int nb, long L, int p);
 // the mixed-precision LOBPCG driver (solver_mixed.cu); k-points already reduced, gammas per k-point
+// k-points whose phase 2 stalled or reached maxiter are not finished: their indices and the buffer (0 or 1 of
+// ctx->X64) that holds their double-float block are appended to `handover`, for the FP64 finish of pc_solve
 int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam, const std::vector<int> &zero,
-                int nbands, int m, double tol, double *evals, void *evecs, int *iters, double *resid);
+                int nbands, int m, double tol, double *evals, void *evecs, int *iters, double *resid,
+                std::vector<std::pair<int, int>> *handover);
 // counter-based initial columns; with mask (int [nb][m]) only the flagged columns of the act k-points are written
 // X: dtype PC_C128, PC_DFS (the same FP64 values stored as double-float pairs) or PC_C64 (the same uniforms, the
 // normal deviates formed in FP32)
-// the caller's initial block (ctx->x0, complex64) into the first ctx->x0n columns of the panels of k-points
+// the caller's initial block (ctx->x0, complex64 or, with ctx->x0_c128, complex128) into the first ctx->x0n
+// columns of the panels of k-points
 // b0 .. b0 + nbk - 1 at X + b * sx (dtype PC_C128 or PC_C64 panels; sx in elements)
 int launch_copy_x0(const pc_ctx *ctx, int b0, int nbk, int dtype, void *X, long sx, cudaStream_t st);
 int launch_init_block(int nb, long L, int m, uint64_t seed, int kidx0, void *X, long sx, cudaStream_t st,

@@ -340,6 +340,61 @@ void reduce_lattice(const pc_ctx *ctx, const double *k, double *out) {
 
 }  // namespace
 
+// FP64 finish of the mixed solve: the k-points it handed over (phase 2 stalled or capped) are solved again by the
+// FP64 solve, started from their double-float blocks (all m columns, converted to complex128), with the same bands,
+// guard columns and tolerance. Their eigenvalues, residuals and eigenvectors replace the mixed solve's; their
+// iteration counts add up; ctx->fp64_finish flags them.
+static int fp64_finish(pc_ctx *ctx, const double *kpts, int nbands, int m, double tol, double *evals, void *evecs,
+                       int *iters, double *resid, const std::vector<std::pair<int, int>> &handover, int status) {
+  const int ns = (int)handover.size(), nb = (int)ctx->fp64_finish.size();
+  const long L = 3 * ctx->n;
+  const size_t xcount = (size_t)ns * m * L, ecount = evecs ? (size_t)ns * nbands * L : 0;
+  PC_CK(ctx->finbuf.reserve(sizeof(double2) * (xcount + ecount)));
+  double2 *x0 = ctx->finbuf.as<double2>();
+  double2 *ev = evecs ? x0 + xcount : nullptr;
+  std::vector<double> ks(3 * (size_t)ns);
+  for (int i = 0; i < ns; ++i) {
+    const int b = handover[i].first, buf = handover[i].second;
+    for (int d = 0; d < 3; ++d) ks[3 * i + d] = kpts[3 * b + d];
+    const int rc = launch_pairs_to_c128(1, L, m, ctx->X64[buf].as<float4>() + (size_t)b * m * L, (long)m * L,
+                                        x0 + (size_t)i * m * L, (long)m * L, ctx->stream, nullptr);
+    if (rc) return rc;
+  }
+  std::vector<double> ev_s((size_t)ns * nbands), res_s((size_t)ns * nbands);
+  std::vector<int> it_s(ns, 0);
+  const pc_opts saved = ctx->opts;
+  const void *saved_x0 = ctx->x0;
+  const int saved_x0n = ctx->x0n, saved_kidx0 = ctx->kidx0;
+  const bool saved_c128 = ctx->x0_c128;
+  ctx->opts.precision = PC_PREC_FP64;
+  ctx->opts.guard = m - nbands;
+  ctx->x0 = x0;
+  ctx->x0n = m;
+  ctx->x0_c128 = true;
+  const int rc = pc_solve(ctx, ns, ks.data(), nbands, tol, ev_s.data(), ev, it_s.data(), res_s.data());
+  ctx->opts = saved;
+  ctx->x0 = saved_x0;
+  ctx->x0n = saved_x0n;
+  ctx->kidx0 = saved_kidx0;
+  ctx->x0_c128 = saved_c128;
+  ctx->fp64_finish.assign(nb, 0);
+  if (rc < 0) return rc;
+  for (int i = 0; i < ns; ++i) {
+    const int b = handover[i].first;
+    for (int j = 0; j < nbands; ++j) {
+      evals[(size_t)b * nbands + j] = ev_s[(size_t)i * nbands + j];
+      if (resid) resid[(size_t)b * nbands + j] = res_s[(size_t)i * nbands + j];
+    }
+    if (iters) iters[b] += it_s[i];
+    if (evecs)
+      PC_CK(cudaMemcpyAsync(static_cast<double2 *>(evecs) + (size_t)b * nbands * L, ev + (size_t)i * nbands * L,
+                            sizeof(double2) * (size_t)nbands * L, cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->fp64_finish[b] = 1;
+  }
+  PC_CK(cudaStreamSynchronize(ctx->stream));
+  return std::max(status, rc);
+}
+
 extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, double tol, double *evals, void *evecs,
                         int *iters, double *resid) {
   PC_REQUIRE(ctx && kpts && evals, "pc_solve: null argument");
@@ -376,11 +431,13 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
       int status = PC_OK;
       const void *x0 = ctx->x0;  // a caller's initial block (pc_solve_init) covers all nk k-points
       const int kidx_base = ctx->kidx0;
+      const size_t x0_elem = ctx->x0_c128 ? sizeof(double2) : sizeof(float2);
+      std::vector<int> finish(nk, 0);
       for (int b0 = 0; b0 < nk; b0 += chunk) {
         const int nc = std::min(chunk, nk - b0);
         ctx->kidx0 = kidx_base + b0;
         if (x0)
-          ctx->x0 = static_cast<const char *>(x0) + sizeof(float2) * (size_t)b0 * ctx->x0n * (size_t)(3 * ctx->n);
+          ctx->x0 = static_cast<const char *>(x0) + x0_elem * (size_t)b0 * ctx->x0n * (size_t)(3 * ctx->n);
         void *ev = evecs ? static_cast<void *>(static_cast<char *>(evecs) + sizeof(double2) * (size_t)b0 * nbands *
                                                                                  (size_t)(3 * ctx->n))
                          : nullptr;
@@ -390,7 +447,9 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
         ctx->kidx0 = kidx_base;
         if (rc < 0) return rc;
         status = std::max(status, rc);
+        for (int i = 0; i < nc && i < (int)ctx->fp64_finish.size(); ++i) finish[b0 + i] = ctx->fp64_finish[i];
       }
+      ctx->fp64_finish = finish;
       return status;
     }
   }
@@ -412,12 +471,16 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
     gam[b] = ctx->opts.gamma_override > 0 ? ctx->opts.gamma_override
                                           : (k2 == 0.0 ? 2.0 / h : 2.0 * std::max(1.0 / h, 1.0 / k2));
   }
+  ctx->fp64_finish.assign(nb, 0);
   int rc = upload_kpoints(ctx, nb, kr.data(), gam.data());
   if (rc) return rc;
   if (ctx->opts.precision == PC_PREC_MIXED) {
-    rc = solve_mixed(ctx, nb, kr.data(), gam, zero, nbands, m, tol, evals, evecs, iters, resid);
+    std::vector<std::pair<int, int>> handover;
+    rc = solve_mixed(ctx, nb, kr.data(), gam, zero, nbands, m, tol, evals, evecs, iters, resid, &handover);
     const int tc = gram_tc_check();  // a time-out inside the tensor-core Gram kernel voids the result
-    return tc ? tc : rc;
+    if (tc) return tc;
+    if (rc < 0 || handover.empty()) return rc;
+    return fp64_finish(ctx, kpts, nbands, m, tol, evals, evecs, iters, resid, handover, rc);
   }
 
   const long sS = 3L * m * L;  // panel stride per k-point (elements)
@@ -662,6 +725,13 @@ extern "C" int pc_solve(pc_ctx *ctx, int nk, const double *kpts, int nbands, dou
   if (iters)
     for (int b = 0; b < nb; ++b) iters[b] = itcount[b];
   return status;
+}
+
+extern "C" int pc_get_fp64_finish(pc_ctx *ctx, int nk, int *flags) {
+  PC_REQUIRE(ctx && flags, "pc_get_fp64_finish: null argument");
+  PC_REQUIRE(nk == (int)ctx->fp64_finish.size(), "pc_get_fp64_finish: nk differs from the last solve's");
+  for (int b = 0; b < nk; ++b) flags[b] = ctx->fp64_finish[b];
+  return PC_OK;
 }
 
 extern "C" int pc_solve_init(pc_ctx *ctx, int nk, const double *kpts, int nbands, double tol, const void *X0, int n0,

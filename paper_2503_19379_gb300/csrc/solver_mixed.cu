@@ -16,7 +16,12 @@
 // Gram block X^H X, all three in double-float arithmetic (mixed_df.cu) on the FP32 pipe. The X-X block of the
 // projected operator is Theta X^H X + R^H X (AX = X Theta + R), with R^H X from the complex64 product R^H [X | Q]:
 // its rounding is eps32 |R| |X|, small because R is.
-// Convergence and Algorithm 4.1 are decided in phase 2 only, on FP64 residuals and FP64 norms.
+// Convergence and Algorithm 4.1 are decided in phase 2 only, on FP64 residuals and FP64 norms. A k-point whose
+// phase 2 stops converging (its largest residual below 1e-2 but not halved over 15 iterations, after at least 30)
+// or reaches maxiter is handed back unfinished: pc_solve finishes it with the FP64 solve from its double-float block.
+// (Measured at N = 128 near Gamma, where the lowest bands have lambda ~ 0.09: their phase 2 levels off at a
+// relative residual of 1e-5 to 1e-4 -- an absolute residual of ~1e-6 |x|, as for every other band there -- while
+// the FP64 solve reaches the tolerance.)
 //
 // Scheduling: the k-points are split into contiguous groups (opts.groups, up to 4; default 4 from 16 k-points, 2
 // from 8), each with its own stream, active list, scratch and pinned host copies of its residual norms. Every
@@ -66,7 +71,9 @@ struct MixedShared {
   // different iterations never overlap: G and H (nmax x nmax), R^H S (m x nmax), coefficients (nmax x m)
   long sG, sRS, sC;
   std::vector<int> phase, doublings, itcount, done, round_start, p1_start;
-  std::vector<std::vector<std::pair<int, double>>> hist;  // per k-point: (iteration, largest relative residual)
+  std::vector<std::vector<std::pair<int, double>>> hist;   // per k-point: (iteration, largest relative residual)
+  std::vector<std::vector<std::pair<int, double>>> hist2;  // the same in phase 2, since the last switch or restart
+  std::vector<std::pair<int, int>> *handover = nullptr;   // unfinished k-points and the X64 buffer of their block
   double p1_floor = 3e-3, p1_stall = 0.25;                // phase switch thresholds (see step())
   double *evals, *resid;
   void *evecs;
@@ -257,13 +264,40 @@ class MixedSolve {
       const bool stalled = (k1 >= 10 && mx < S.p1_stall && stall(5)) || (k1 >= 20 && stall(10));
       if (stalled || mx < S.p1_floor || it - S.p1_start[b] >= 150) sw.push_back(b);
     }
-    // ---- phase 2: convergence on FP64 residuals, then Algorithm 4.1
-    std::vector<int> conv;
+    // ---- phase 2: convergence on FP64 residuals, then Algorithm 4.1; a stalled or capped k-point is handed over
+    std::vector<int> conv, hand;
     for (int b : act2) {
       bool ok = true;
-      for (int j = 0; j < nbands; ++j)
-        if (!(relres(b, j) <= S.tol)) ok = false;
-      if (ok || it - S.round_start[b] >= maxiter) conv.push_back(b);
+      double mx = 0;
+      for (int j = 0; j < nbands; ++j) {
+        const double r = relres(b, j);
+        if (!(r <= S.tol)) ok = false;
+        mx = std::max(mx, r == r ? r : 1e300);
+      }
+      auto &h = S.hist2[b];
+      if (h.empty() || h.back().first != it) h.push_back({it, mx});
+      const int k2 = (int)h.size();
+      bool stalled = false;
+      if (!ok && k2 >= 30 && mx < 1e-2) {
+        double recent = 1e300, before = 1e300;
+        for (int q = k2 - 15; q < k2; ++q) recent = std::min(recent, h[q].second);
+        for (int q = k2 - 30; q < k2 - 15; ++q) before = std::min(before, h[q].second);
+        stalled = recent > 0.5 * before;
+      }
+      if (ok)
+        conv.push_back(b);
+      else if (stalled || it - S.round_start[b] >= maxiter)
+        hand.push_back(b);
+    }
+    for (int b : hand) {
+      S.done[b] = 1;
+      S.itcount[b] = it;
+      for (int j = 0; j < nbands; ++j) {
+        S.evals[(size_t)b * nbands + j] = S.h_theta[(size_t)b * m + j];
+        if (S.resid) S.resid[(size_t)b * nbands + j] = relres(b, j);
+      }
+      S.handover->push_back({b, cur});
+      if (S.verbose) std::fprintf(stderr, "[pc-mixed] it %d k %d handed to the FP64 solve\n", it, b);
     }
     std::vector<int> redo, fin;
     if (!conv.empty()) {
@@ -325,6 +359,7 @@ class MixedSolve {
         for (int b : sw) {
           S.phase[b] = 2;
           S.round_start[b] = it + 1;
+          S.hist2[b].clear();
         }
         RUN(set_act(sw));
         const int ns = (int)sw.size();
@@ -338,6 +373,7 @@ class MixedSolve {
           (*S.gam)[b] *= 2.0;
           S.doublings[b] += 1;
           S.round_start[b] = it + 1;
+          S.hist2[b].clear();
         }
         RUN(upload_kpoints(ctx, nb, S.kr, S.gam->data()));
         RUN(set_act(redo));
@@ -434,7 +470,8 @@ class MixedSolve {
 }  // namespace
 
 int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam, const std::vector<int> &zero,
-                int nbands, int m, double tol, double *evals, void *evecs, int *iters, double *resid) {
+                int nbands, int m, double tol, double *evals, void *evecs, int *iters, double *resid,
+                std::vector<std::pair<int, int>> *handover) {
   const long n = ctx->n, L = 3 * n;
   const long sF = 3L * m * L, sX = (long)m * L;
   const int nmax = 3 * m;
@@ -534,6 +571,8 @@ int solve_mixed(pc_ctx *ctx, int nb, const double *kr, std::vector<double> &gam,
   S.round_start.assign(nb, 0);
   S.p1_start.assign(nb, 0);
   S.hist.assign(nb, {});
+  S.hist2.assign(nb, {});
+  S.handover = handover;
   S.evals = evals;
   S.resid = resid;
   S.evecs = evecs;

@@ -48,6 +48,7 @@ SIGNATURES = {
     "pc_setup": (_i, [C.POINTER(_vp), _i, _dp, _dp, C.POINTER(Opts), _vp]),
     "pc_solve": (_i, [_vp, _i, _dp, _i, _d, _dp, _vp, _ip, _dp]),
     "pc_solve_init": (_i, [_vp, _i, _dp, _i, _d, _vp, _i, _dp, _vp, _ip, _dp]),
+    "pc_get_fp64_finish": (_i, [_vp, _i, _ip]),
     "pc_destroy": (None, [_vp]),
     "pc_last_error": (C.c_char_p, []),
     "pc_eps_spheres": (_i, [_i, _i, _dp, _d, _dp]),
@@ -225,7 +226,8 @@ class Solver:
 
     def solve(self, kpts, nbands: int, tol: float, want_vectors: bool = False, x0=None):
         """pc_solve (pc_solve_init when x0, a torch complex64 CUDA tensor [nk][n0][3][N][N][N], gives the first n0
-        columns of the initial block); returns dict(evals, iters, resid, status[, evecs (torch complex128)])."""
+        columns of the initial block); returns dict(evals, iters, resid, status, fp64_finish (1 where the mixed
+        solve handed the k-point to the FP64 solve)[, evecs (torch complex128)])."""
         k = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
         nk = k.shape[0]
         evals = np.zeros((nk, nbands))
@@ -246,7 +248,9 @@ class Solver:
             rc = lib().pc_solve_init(self._h, nk, _dptr(k), nbands, float(tol), _dev(x0, [torch.complex64]),
                                      int(x0.shape[1]), _dptr(evals), ev, iters.ctypes.data_as(_ip), _dptr(resid))
         _check(rc, "pc_solve", warn_ok=True)
-        out = {"evals": evals, "iters": iters, "resid": resid, "status": rc}
+        finish = np.zeros(nk, dtype=np.int32)
+        _check(lib().pc_get_fp64_finish(self._h, nk, finish.ctypes.data_as(_ip)), "pc_get_fp64_finish")
+        out = {"evals": evals, "iters": iters, "resid": resid, "status": rc, "fp64_finish": finish}
         if evecs is not None:
             out["evecs"] = evecs
         return out

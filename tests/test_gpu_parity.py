@@ -466,6 +466,32 @@ def test_mixed_groups_match_one(pcmod, groups):
     assert np.all(b["resid"] <= w.tol)
 
 
+def test_mixed_fp64_finish_of_capped_kpoints(pcmod):
+    # a phase-2 cap of 30 iterations hands most k-points of an fcc-spheres-N32 slice to the FP64 solve, which starts
+    # from their double-float blocks; the result is the plain FP64 solve's, with eigenvectors and residuals to tol
+    w = wl.workload_fcc_32()
+    eps = pcmod.eps_spheres(w.N, w.structure.as_array(), w.structure.eps_bg)
+    ks = w.kpts[[3, 11, 20, 29]]
+    mixed = pcmod.Solver(w.N, eps, precision=pcmod.pc.PC_PREC_MIXED, maxiter=30)
+    out = mixed.solve(ks, w.nbands, w.tol, want_vectors=True)
+    ref = pcmod.Solver(w.N, eps).solve(ks, w.nbands, w.tol)
+    assert out["status"] == 0 and ref["status"] == 0
+    assert out["fp64_finish"].sum() >= 1
+    assert np.all(out["resid"] <= w.tol)
+    assert np.max(np.abs(out["evals"] - ref["evals"]) / ref["evals"]) <= 10 * w.tol
+    # the handed-over k-points' eigenvectors: unit norm, Rayleigh quotients equal to their eigenvalues
+    for b in np.nonzero(out["fp64_finish"])[0]:
+        V = out["evecs"][b:b + 1]
+        kr = ks[b:b + 1] - 2 * np.pi * np.round(ks[b:b + 1] / (2 * np.pi))  # the solver's reduced k
+        gam = np.full(1, 2.0 * max(w.N, 1.0 / float(np.sum(kr * kr))))
+        AV = mixed.apply_op(kr, gam, V)
+        num = torch.sum(V.conj() * AV, dim=(2, 3, 4, 5)).real.cpu().numpy()[0]
+        nrm = torch.sum(V.conj() * V, dim=(2, 3, 4, 5)).real.cpu().numpy()[0]
+        assert np.allclose(nrm, 1.0, atol=1e-10)
+        assert np.max(np.abs(num / nrm - out["evals"][b]) / out["evals"][b]) <= 10 * w.tol
+    mixed.close()
+
+
 def test_mixed_full_benchmark_batch(pcmod):
     """The fcc-spheres-N32 configuration as a benchmark runs it: all 40 FCC k-points in one mixed solve with the
     default four k-point groups on four streams. Every residual reported within tol; at the oracle's sampled k-points
