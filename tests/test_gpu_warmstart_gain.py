@@ -19,8 +19,11 @@ import workloads as wl
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-N, NB, NK, TOL = 32, 8, 10, 1e-6
-NTRAIN, NHELD = 48, 8
+N, NB, TOL = 32, 8, 1e-6
+# the default sizes keep the test short; PC_WS_NTRAIN, PC_WS_NHELD and PC_WS_NK run the larger study
+NK = int(os.environ.get("PC_WS_NK", "10"))
+NTRAIN = int(os.environ.get("PC_WS_NTRAIN", "48"))
+NHELD = int(os.environ.get("PC_WS_NHELD", "8"))
 
 
 @pytest.fixture(scope="module")
