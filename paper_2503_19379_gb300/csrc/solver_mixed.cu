@@ -75,7 +75,7 @@ struct MixedShared {
   std::vector<std::vector<std::pair<int, double>>> hist;   // per k-point: (iteration, largest relative residual)
   std::vector<std::vector<std::pair<int, double>>> hist2;  // the same in phase 2, since the last switch or restart
   std::vector<std::pair<int, int>> *handover = nullptr;   // unfinished k-points and the X64 buffer of their block
-  double p1_floor = 3e-3, p1_stall = 0.25;                // phase switch thresholds (see step())
+  double p1_floor = 3e-3, p1_stall = 0.05;                // phase switch thresholds (see step())
   double *evals, *resid;
   void *evecs;
   int status = PC_OK;
@@ -241,8 +241,8 @@ class MixedSolve {
     // ---- phase 1 -> 2 once the complex64 residual stops falling, at its floor. The floor is eps32 times the stencil's
     // magnitude (~gamma / h^2) over lambda: ~3e-3 for most k-points of a path at N = 32 and ~3e-2 at N = 64, but
     // near Gamma, where the lowest bands have small lambda (~|k|^2 / eps), it reaches 1 and above. A short stall is
-    // accepted below 0.25 (the early iterations, whose residual plateaus near 1 while the search space builds up,
-    // are not a floor): the best residual of the last 5 iterations is not 30% below the best of the 5 before. A
+    // accepted below 0.05 (the plateaus higher up, near 1 while the search space builds up and near 0.2 later, are
+    // not a floor): the best residual of the last 5 iterations is not 30% below the best of the 5 before. A
     // long stall is accepted at any level: the best of the last 10 iterations is not 30% below the best of the 10
     // before (near Gamma at N = 64 the complex64 residual sits at ~2 from iteration ~20 on; without this rule those
     // k-points waited for the 150-iteration cap). The history holds one entry per iteration: a decision pass that
