@@ -38,6 +38,7 @@
 #include <vector>
 
 #include "pc_internal.cuh"
+#include "phase_rules.h"
 
 namespace pc {
 
@@ -72,10 +73,10 @@ struct MixedShared {
   // different iterations never overlap: G and H (nmax x nmax), R^H S (m x nmax), coefficients (nmax x m)
   long sG, sRS, sC;
   std::vector<int> phase, doublings, itcount, done, round_start, p1_start;
-  std::vector<std::vector<std::pair<int, double>>> hist;   // per k-point: (iteration, largest relative residual)
-  std::vector<std::vector<std::pair<int, double>>> hist2;  // the same in phase 2, since the last switch or restart
+  std::vector<ResidHistory> hist;   // per k-point: (iteration, largest relative residual)
+  std::vector<ResidHistory> hist2;  // the same in phase 2, since the last switch or restart
   std::vector<std::pair<int, int>> *handover = nullptr;   // unfinished k-points and the X64 buffer of their block
-  double p1_floor = 3e-3, p1_stall = 0.05;                // phase switch thresholds (see step())
+  Phase1Rule p1_rule;  // phase switch thresholds (phase_rules.h)
   double *evals, *resid;
   void *evecs;
   int status = PC_OK;
@@ -238,32 +239,18 @@ class MixedSolve {
           for (int j = 0; j < S.m; ++j) std::fprintf(stderr, " %.2e", relres(b, j));
         std::fprintf(stderr, "\n");
       }
-    // ---- phase 1 -> 2 once the complex64 residual stops falling, at its floor. The floor is eps32 times the stencil's
-    // magnitude (~gamma / h^2) over lambda: ~3e-3 for most k-points of a path at N = 32 and ~3e-2 at N = 64, but
-    // near Gamma, where the lowest bands have small lambda (~|k|^2 / eps), it reaches 1 and above. A short stall is
-    // accepted below 0.05 (the plateaus higher up, near 1 while the search space builds up and near 0.2 later, are
-    // not a floor): the best residual of the last 5 iterations is not 30% below the best of the 5 before. A
-    // long stall is accepted at any level: the best of the last 10 iterations is not 30% below the best of the 10
-    // before (near Gamma at N = 64 the complex64 residual sits at ~2 from iteration ~20 on; without this rule those
-    // k-points waited for the 150-iteration cap). The history holds one entry per iteration: a decision pass that
-    // repeats an iteration (phase switch, gamma doubling) does not add one. Also switch below 3e-3, or after 150
-    // iterations.
+    // ---- phase 1 -> 2 once the complex64 residual stops falling, at its floor (phase_rules.h). The floor is eps32
+    // times the stencil's magnitude (~gamma / h^2) over lambda: ~3e-3 for most k-points of a path at N = 32 and
+    // ~3e-2 at N = 64, but near Gamma, where the lowest bands have small lambda (~|k|^2 / eps), it reaches 1 and
+    // above (near Gamma at N = 64 the complex64 residual sits at ~2 from iteration ~20 on; without the long-stall
+    // rule those k-points waited for the 150-iteration cap).
     std::vector<int> sw;
     for (int b : act1) {
       double mx = 0;
       for (int j = 0; j < nbands; ++j) mx = std::max(mx, relres(b, j));
       if (!(mx == mx)) mx = 1e300;  // NaN guard
-      auto &h = S.hist[b];
-      if (h.empty() || h.back().first != it) h.push_back({it, mx});
-      const int k1 = (int)h.size();
-      auto stall = [&](int w) {  // best of the last w entries not 30% below the best of the w before
-        double recent = 1e300, before = 1e300;
-        for (int q = k1 - w; q < k1; ++q) recent = std::min(recent, h[q].second);
-        for (int q = k1 - 2 * w; q < k1 - w; ++q) before = std::min(before, h[q].second);
-        return recent > 0.7 * before;
-      };
-      const bool stalled = (k1 >= 10 && mx < S.p1_stall && stall(5)) || (k1 >= 20 && stall(10));
-      if (stalled || mx < S.p1_floor || it - S.p1_start[b] >= 150) sw.push_back(b);
+      record_residual(S.hist[b], it, mx);
+      if (phase1_done(S.hist[b], mx, it - S.p1_start[b], S.p1_rule)) sw.push_back(b);
     }
     // ---- phase 2: convergence on FP64 residuals, then Algorithm 4.1; a stalled or capped k-point is handed over
     std::vector<int> conv, hand, rollback;
@@ -275,29 +262,15 @@ class MixedSolve {
         if (!(r <= S.tol)) ok = false;
         mx = std::max(mx, r == r ? r : 1e300);
       }
-      auto &h = S.hist2[b];
-      double best = 1e300;  // best largest residual of the earlier phase-2 iterations
-      for (const auto &e : h)
-        if (e.first != it) best = std::min(best, e.second);
-      if (h.empty() || h.back().first != it) h.push_back({it, mx});
-      const int k2 = (int)h.size();
-      // a jump: the residual 1000 times above its best after that was below 1e-2 (a Ritz pair of a nearly dependent
-      // direction taken into X, which can blow the block up); the block of the previous iteration, still in the
-      // other buffer, is handed over. Smaller excursions (up to ~150x on the diamond-air-N64 batch) recover.
-      const bool jump = !ok && k2 >= 3 && best < 1e-2 && mx > 1000.0 * best;
-      bool stalled = false;
-      if (!ok && k2 >= 50 && mx < 1e-2) {
-        double recent = 1e300, before = 1e300;
-        for (int q = k2 - 25; q < k2; ++q) recent = std::min(recent, h[q].second);
-        for (int q = k2 - 50; q < k2 - 25; ++q) before = std::min(before, h[q].second);
-        stalled = recent > 0.8 * before;
+      // a rollback hands over the block of the previous iteration, still in the other buffer (excursions up to
+      // ~150x on the diamond-air-N64 batch recover by themselves; the rule waits for 1000x)
+      record_residual(S.hist2[b], it, mx);
+      switch (phase2_step(S.hist2[b], it, ok, mx, it - S.round_start[b] >= maxiter)) {
+        case Phase2Step::kConverged: conv.push_back(b); break;
+        case Phase2Step::kRollback: rollback.push_back(b); break;
+        case Phase2Step::kHandover: hand.push_back(b); break;
+        case Phase2Step::kContinue: break;
       }
-      if (ok)
-        conv.push_back(b);
-      else if (jump)
-        rollback.push_back(b);
-      else if (stalled || it - S.round_start[b] >= maxiter)
-        hand.push_back(b);
     }
     for (int b : rollback) hand.push_back(b);
     for (int b : hand) {
