@@ -1,5 +1,5 @@
-"""Training and evaluation of the learned warm start on the device (configuration C4 of the warm-start workload:
-seeded random structures, eigenvectors from the solver itself).
+"""Training and evaluation of the learned warm start on the device (the warm-start workload: seeded random
+structures of 1-8 spheres in a cubic cell, eigenvectors from the solver itself).
 
 Every numerical step runs in libpc: the solves (pc_solve), the network's forward and backward passes and Adam
 (pc_ws_*). This module only orders the calls and keeps the training set resident on the device: the eigenvectors
