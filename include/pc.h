@@ -57,7 +57,8 @@ extern "C" {
 
 /* Solver precision. */
 #define PC_PREC_FP64 0  /* every step in FP64 / complex128 */
-#define PC_PREC_MIXED 1 /* search directions in complex64, X, residual and Rayleigh-Ritz in FP64 */
+#define PC_PREC_MIXED 1 /* search directions in complex64; X, its residual and Gram block FP64-accurate (double-float
+                           pairs on the FP32 pipe); Rayleigh-Ritz in FP64; stalled k-points finished in FP64 */
 
 typedef struct pc_ctx pc_ctx;
 
